@@ -1,0 +1,370 @@
+"""Benchmark of the temporally-blocked stencil engine on one configuration.
+
+Default workload: Hotspot 2D (thermal), 16384 x 16384 float32 cells, 1000 time steps, seeded
+synthetic inputs (temperature U[320,340) K, power U[0,0.5), ambient 80).  One benchmark "step"
+is one full run of the hot path: stencil_run advancing the grid by 1000 time steps
+(ceil(1000/T) temporally-blocked passes).
+
+Prints one JSON line (rank 0): throughput in GCell/s (cell updates per second, the unit the
+paper's Table 4 quotes beside GB/s and GFLOP/s), the dominant kernel's roofline fraction, the
+end-to-end figure through the C ABI with host buffers, and the CPU oracle's throughput on a
+bounded sample of the same workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+
+With --gpus N > 1 (launched by torch.distributed.run) every rank advances its own grid: the
+method has no cross-grid exchange, so the job is N independent replicas (weak scaling) with a
+barrier around the timed region and the time taken as the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+# per-cell counts (Table 2): counted flops, bytes per cell per pass (field in/out, power in)
+FLOPS = {(0, 2): 9, (0, 3): 13, (1, 2): 15, (1, 3): 17}
+BYTES = {0: 8, 1: 12}
+
+WORKLOADS = {
+    "thermal2d_16384": lambda: synth.c2_thermal2d(),
+    "diffusion2d_1024": lambda: synth.c1_diffusion2d(),
+    "diffusion3d_512": lambda: synth.c3a_diffusion3d(),
+    "thermal3d_512x512x256": lambda: synth.c3b_thermal3d(),
+}
+DEFAULT = "thermal2d_16384"
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(sms: int, mhz: float) -> float:
+    """FP32 ALU peak: SMs x 128 FP32 lanes x 2 flops per fused multiply-add x clock."""
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash(ndim: int) -> str:
+    f = "tb2d_kernel.cuh" if ndim == 2 else "tb3d_kernel.cuh"
+    src = open(os.path.join(ROOT, "paper_1802_00438_gb300", "csrc", f), "rb").read()
+    return hashlib.sha1(src).hexdigest()[:12]
+
+
+def profiled_traffic(workload: str, ndim: int):
+    """DRAM bytes per launch recorded by an ncu capture of the current kernel source, if any
+    (profiles/traffic.json); None when the kernel changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(workload)
+    if not d or d.get("kernel_sha") != kernel_source_hash(ndim):
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def _oracle_sample_steps(w, budget_s: float):
+    """Time steps of the full grid that take about budget_s seconds on the host cores."""
+    import oracle
+    oracle.build()
+    cores = len(os.sched_getaffinity(0))
+    oracle.set_threads(cores)
+    t0 = time.perf_counter()
+    oracle.run(w.kind, w.u0, w.coef, 1, w.power)
+    t1 = time.perf_counter() - t0
+    return max(1, min(w.steps, int(budget_s / max(t1, 1e-4)))), cores
+
+
+def cpu_baseline(w, budget_s: float = 15.0):
+    """The oracle as it stands, on the host cores, over a bounded sample of the workload: the
+    full grid for as many time steps as fit in about `budget_s` seconds."""
+    import oracle
+    steps, cores = _oracle_sample_steps(w, budget_s)
+    t0 = time.perf_counter()
+    oracle.run(w.kind, w.u0, w.coef, steps, w.power)
+    t = time.perf_counter() - t0
+    return {"value": w.cells * steps / t / 1e9, "unit": "GCell/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"full {'x'.join(map(str, w.shape[::-1]))} grid, {steps} of {w.steps} "
+                      f"time steps ({t:.1f} s; float32 oracle, OpenMP over rows)"}
+
+
+def run_reference(args, w):
+    """Reference arm: the CPU oracle, each benchmark step a bounded sample of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    per_step = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    steps, cores = _oracle_sample_steps(w, per_step)
+    for _ in range(args.warmup):
+        oracle.run(w.kind, w.u0, w.coef, steps, w.power)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.run(w.kind, w.u0, w.coef, steps, w.power)
+    t = time.perf_counter() - t0
+    value = w.cells * steps * args.steps / t / 1e9
+    sample = (f"full {'x'.join(map(str, w.shape[::-1]))} grid, {steps} of {w.steps} time steps "
+              f"per benchmark step (float32 oracle, OpenMP over rows)")
+    line = {"impl": "reference", "metric": "stencil GCell/s & GFLOP/s vs roofline",
+            "value": value, "unit": "GCell/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name},
+            "cpu_baseline": {"value": value, "unit": "GCell/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "GCell/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
+    ap.add_argument("--T", type=int, default=0, help="force the fused step count")
+    ap.add_argument("--bx", type=int, default=0, help="force the 2D tile width")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    ap.add_argument("--nx", type=int, default=0, help="profiling: override the grid size")
+    ap.add_argument("--ny", type=int, default=0)
+    ap.add_argument("--nz", type=int, default=0)
+    ap.add_argument("--time-steps", type=int, default=0, help="profiling: override time steps")
+    args = ap.parse_args()
+
+    w = WORKLOADS[args.workload]()
+    if args.nx or args.ny or args.nz or args.time_steps:
+        w = synth.make(w.kind, w.ndim, args.nx or w.nx, args.ny or w.ny, args.nz or w.nz,
+                       steps=args.time_steps or w.steps, seed=w.seed,
+                       name=f"{w.name.split('_')[0]}_resized")
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_1802_00438_gb300 as st
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    u0 = torch.from_numpy(w.u0).to(dev)
+    pw = None if w.power is None else torch.from_numpy(w.power).to(dev)
+    out = torch.empty_like(u0)
+    plan = st.Plan(w.kind, w.ndim, w.nx, w.ny, w.nz, force_T=args.T, force_bx=args.bx,
+                   stream=stream.cuda_stream)
+    info = plan.info()
+    T = info["T"]
+    passes = -(-w.steps // T)
+
+    def step():
+        plan.run(u0, out, w.coef, w.steps, power=pw)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, device time by CUDA events on the plan's stream ----------
+    st.stencil_plan_set_timing(plan.h, True)
+    st.stencil_plan_kernel_time(plan.h, reset=True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    kern_ms, launches = st.stencil_plan_kernel_time(plan.h, reset=True)
+    st.stencil_plan_set_timing(plan.h, False)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    cells_step = w.cells * w.steps
+    value = world * cells_step * args.steps / (ms * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI with host buffers ----------------------------------
+    e2e = None
+    if not args.no_e2e:
+        h_u = torch.from_numpy(w.u0).pin_memory()
+        h_p = None if w.power is None else torch.from_numpy(w.power).pin_memory()
+        h_o = torch.empty_like(h_u).pin_memory()
+        d_u = torch.empty_like(u0)
+        d_p = None if pw is None else torch.empty_like(pw)
+        d_o = torch.empty_like(u0)
+
+        def e2e_step():
+            d_u.copy_(h_u, non_blocking=True)
+            if d_p is not None:
+                d_p.copy_(h_p, non_blocking=True)
+            st.stencil_run(plan.h, d_u, d_o, d_p, w.coef, w.nx, w.ny, w.nz, w.steps)
+            h_o.copy_(d_o, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ems = a0.elapsed_time(a1)
+        if dist:
+            t = torch.tensor([ems], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        nb = w.u0.nbytes
+        e2e = {"value": world * cells_step * args.steps / (ems * 1e-3) / 1e9, "unit": "GCell/s",
+               "h2d_bytes_per_step": nb * (2 if w.power is not None else 1),
+               "d2h_bytes_per_step": nb}
+
+    # ---- roofline of the dominant kernel ---------------------------------------------------
+    peaks, src = load_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fl = FLOPS[(w.kind, w.ndim)]
+    by = BYTES[w.kind]
+    alu_peak = fp32_peak_tflops(sms, mhz)
+    hbm_peak = float(peaks["hbm_gbs"])
+    avg_launch_ms = kern_ms / max(launches, 1)
+    # algorithmic work of one launch, averaged over the timed launches (the last pass of a
+    # run fuses the remainder of the steps)
+    flops_per_launch = w.cells * w.steps * args.steps * fl / max(launches, 1)
+    bytes_per_launch = w.cells * by
+    tflops = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12
+    gbs = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
+    cell_roof = min(alu_peak * 1e12 / fl, hbm_peak * 1e9 * T / by)      # cells/s at this T
+    alu_bound = alu_peak * 1e12 / fl <= hbm_peak * 1e9 * T / by
+    traffic = profiled_traffic(args.workload, w.ndim)
+    if alu_bound:
+        roof = {"bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": tflops / alu_peak,
+                "peak_note": f"FP32 {sms} SMs x 128 lanes x 2 x {mhz:.0f} MHz (max SM clock)"}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": gbs / hbm_peak, "peak_note": f"{src} copy bandwidth"}
+    roof["traffic"] = traffic
+    roof["algorithmic_bytes_per_launch"] = bytes_per_launch
+    roof["cell_roofline_gcells"] = cell_roof / 1e9
+    roof["frac_of_cell_roofline"] = (cells_step * args.steps / (kern_ms * 1e-3)) / cell_roof
+    roof["hbm_frac"] = gbs / hbm_peak
+    roof["kernel_ms_per_launch"] = avg_launch_ms
+
+    clocks = clk.summary()
+    if dist:
+        dist.barrier()
+    if rank == 0:
+        line = {"metric": "stencil GCell/s & GFLOP/s vs roofline",
+                "value": value, "unit": "GCell/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "gflops": value * fl, "effective_gbs": value * by,
+                "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "nz": w.nz,
+                           "time_steps": w.steps, "T": T, "tile": [info["bx"], info["by"]],
+                           "vec": info["vec"], "warps": info["warps"], "ctas": info["ctas"],
+                           "passes_per_step": passes,
+                           "l2": "inputs larger than L2 (%.0f MiB per grid)" % (w.u0.nbytes / 2**20),
+                           "parallelism": f"replicas{world}" if world > 1 else "single"},
+                "roofline": roof, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clocks}
+        if not args.no_cpu and world == 1:
+            line["cpu_baseline"] = cpu_baseline(w)
+        else:
+            line["cpu_baseline"] = None
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,140 @@
+/* stencil.h - C ABI of the GB300 temporally-blocked Jacobi stencil engine.
+ *
+ * The engine advances first-order Jacobi stencils (Table 2 of Zohouri, Podobas, Matsuoka,
+ * "Combined Spatial and Temporal Blocking for High-Performance Stencil Computation on FPGAs
+ * Using OpenCL", arXiv 1802.00438):
+ *   Diffusion 2D (5-point), Diffusion 3D (7-point), Hotspot 2D and Hotspot 3D (thermal, with a
+ *   per-cell power input and an ambient temperature),
+ * with the clamped boundary of Sec. 5.1 (an out-of-range neighbour is the boundary cell), using
+ * the combined spatial and temporal blocking of Sec. 3.1-3.2: overlapped tiles with halos of
+ * width rad * T (Eq. 2), T time steps fused per pass over device memory, redundant halo
+ * computation and masked stores (Sec. 3.2).  A run of `steps` steps is ceil(steps / T) passes
+ * (Eq. 8); when T does not divide `steps` the last pass fuses the remainder (Sec. 3.2).
+ *
+ * Layout: every grid is a dense row-major float array, x fastest:
+ *   index(x, y, z) = x + nx * (y + ny * z)
+ * Neighbours: w = x-1, e = x+1, n = y-1, s = y+1, b = z-1, a = z+1.
+ *
+ * Coefficients (host array, copied into the launch):
+ *   Diffusion 2D  [cc, cw, ce, cs, cn]                     (Table 2 row 1)
+ *   Diffusion 3D  [cc, cw, ce, cs, cn, cb, ca]             (Table 2 row 2)
+ *   Hotspot 2D    [sdc, Rx, Ry, Rz, amb]                   (Table 2 row 3: sdc, Rx_1, Ry_1,
+ *                                                          Rz_1, TEMP_AMB)
+ *   Hotspot 3D    [cc, cw, ce, cs, cn, cb, ca, sdc, amb]   (Table 2 row 4)
+ *
+ * Arithmetic is float32 (Sec. 5.1: all benchmarks are single precision).  A plan made with
+ * `exact = 1` evaluates every cell in the order Table 2 prints it, one rounding per operation,
+ * and is bit-identical to a plain sequential Jacobi loop; with `exact = 0` it contracts the
+ * same expression into fused multiply-adds.
+ *
+ * Errors: every entry point returns 0 (ST_OK) or a negative ST_ERR_* code and never throws.
+ * Launches are asynchronous on the plan's stream; a device-side failure is reported by
+ * stencil_plan_sync() or by the next call on the plan.  A plan is not thread-safe; distinct
+ * plans are independent.
+ */
+#ifndef GB300_STENCIL_H
+#define GB300_STENCIL_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ST_ABI_VERSION 1
+
+/* status codes */
+#define ST_OK                    0
+#define ST_ERR_INVALID_ARG      -1   /* null pointer, bad enum, overlapping buffers, steps < 0 */
+#define ST_ERR_DIMS_MISMATCH    -2   /* nx, ny, nz differ from the plan's */
+#define ST_ERR_UNSTABLE_COEFFS  -3   /* strict plan: coefficients break the stability bound */
+#define ST_ERR_CUDA             -4   /* a CUDA runtime call or a launch failed */
+#define ST_ERR_OOM              -5   /* device allocation failed */
+#define ST_ERR_TIMEOUT          -6   /* a bounded device-side wait gave up */
+#define ST_ERR_UNSUPPORTED      -7   /* valid request this build does not provide */
+
+/* stencil kinds (Table 2) */
+#define ST_DIFFUSION 0
+#define ST_THERMAL   1
+
+/* storage types of the grids between passes */
+#define ST_F32  0
+#define ST_BF16 1
+#define ST_F16  2
+
+typedef struct stencil_plan_s *stencil_plan;
+
+/* Problem and tuning description for stencil_plan_create. */
+typedef struct {
+    int kind;        /* ST_DIFFUSION or ST_THERMAL */
+    int ndim;        /* 2 or 3 */
+    int nx, ny, nz;  /* grid size in cells, each >= 1; nz is ignored (taken as 1) for 2D */
+    int storage;     /* ST_F32 */
+    int force_T;     /* fused steps per pass (par_time, Sec. 3.2); 0 = the plan chooses */
+    int force_bx;    /* tile width in cells incl. halos (bsize_x, Sec. 3.1); 0 = choose */
+    int force_by;    /* 3D: tile height in cells incl. halos (bsize_y); 0 = choose */
+    int force_vec;   /* cells per thread along x (par_vec, Sec. 3.1); 0 = choose */
+    int exact;       /* 1: Table 2 order, no fused multiply-add; 0: contracted */
+    int strict;      /* 1: reject coefficients that break the explicit stability bound */
+    void *stream;    /* cudaStream_t the plan launches on; NULL = the legacy default stream */
+} stencil_desc;
+
+/* What a plan chose (for reports and tests). */
+typedef struct {
+    int T;              /* fused steps per pass */
+    int bx, by;         /* tile size in cells incl. halos (by = 0 for 2D streaming) */
+    int halo;           /* halo width per side in cells (>= rad * T, Eq. 2) */
+    int vec;            /* cells per thread along x */
+    int warps;          /* warps per block */
+    int ctas;           /* blocks per launch (a multiple of the SM count where possible) */
+    int sms;            /* streaming multiprocessors on the plan's device */
+    long long scratch_bytes;   /* device scratch the plan owns */
+    int exact;          /* as requested */
+    int kernel_id;      /* internal kernel family (diagnostics) */
+} stencil_plan_info;
+
+/* Create a plan for one problem shape on the current CUDA device.  Allocates one grid-sized
+ * ping-pong scratch buffer (Sec. 2.1's second buffer) and keeps it until destroy.
+ * out: receives the plan (NULL on failure).
+ * Errors: ST_ERR_INVALID_ARG (bad desc), ST_ERR_UNSUPPORTED (e.g. a storage type or forced
+ * parameter set this build does not provide), ST_ERR_OOM, ST_ERR_CUDA. */
+int stencil_plan_create(stencil_plan *out, const stencil_desc *desc);
+
+/* Advance grid_in by `steps` Jacobi steps (Sec. 2.1) into grid_out.
+ * grid_in  : device pointer, nx*ny*nz floats, read only (never modified).
+ * grid_out : device pointer, nx*ny*nz floats; may equal grid_in (in place); any other
+ *            overlap with grid_in or power is ST_ERR_INVALID_ARG.
+ * power    : device pointer to the per-cell power map (same layout) for ST_THERMAL,
+ *            NULL for ST_DIFFUSION.
+ * coeffs   : host pointer to the coefficient array of the plan's stencil (layouts above).
+ * nx,ny,nz : must equal the plan's (ST_ERR_DIMS_MISMATCH); nz = 1 for 2D.
+ * steps    : >= 0; 0 copies grid_in to grid_out.
+ * Runs ceil(steps/T) passes on the plan's stream and returns without waiting. */
+int stencil_run(stencil_plan plan, const void *grid_in, void *grid_out, const void *power,
+                const float *coeffs, int nx, int ny, int nz, int steps);
+
+/* Wait for the plan's stream; returns the first asynchronous error seen (ST_ERR_CUDA,
+ * ST_ERR_TIMEOUT) or ST_OK. */
+int stencil_plan_sync(stencil_plan plan);
+
+/* Fill *info with the plan's chosen parameters. */
+int stencil_plan_get_info(stencil_plan plan, stencil_plan_info *info);
+
+/* Enable (1) or disable (0) per-launch timing: with it on, stencil_run brackets every kernel
+ * launch with CUDA events on the plan's stream.  stencil_plan_kernel_time then returns the
+ * summed device time in milliseconds and the number of launches since the last reset
+ * (it synchronises the plan's stream). */
+int stencil_plan_set_timing(stencil_plan plan, int enable);
+int stencil_plan_kernel_time(stencil_plan plan, double *ms, long long *launches, int reset);
+
+/* Free the plan and its scratch.  NULL is accepted. */
+int stencil_plan_destroy(stencil_plan plan);
+
+/* Static description of a status code. */
+const char *stencil_strerror(int code);
+
+/* ABI version of the loaded library (ST_ABI_VERSION it was built with). */
+int stencil_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_STENCIL_H */

@@ -1,0 +1,193 @@
+"""Python binding of the GB300 stencil engine (libstencil.so, C ABI in include/stencil.h).
+
+Argument marshalling only: every step of a sweep runs in the library's CUDA kernels.  There is
+no fallback path: importing this package loads libstencil.so and raises if it is missing
+(build it with `paper_1802_00438_gb300.build.build()` or `__graft_entry__.build()`).
+
+Functions carry the C names.  Device buffers are torch CUDA tensors (float32, contiguous) or raw
+integer device addresses; the stream defaults to torch's current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libstencil.so")
+
+ST_OK = 0
+ST_ERR_INVALID_ARG = -1
+ST_ERR_DIMS_MISMATCH = -2
+ST_ERR_UNSTABLE_COEFFS = -3
+ST_ERR_CUDA = -4
+ST_ERR_OOM = -5
+ST_ERR_TIMEOUT = -6
+ST_ERR_UNSUPPORTED = -7
+
+ST_DIFFUSION = 0
+ST_THERMAL = 1
+ST_F32, ST_BF16, ST_F16 = 0, 1, 2
+
+
+class StencilError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+class stencil_desc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("ndim", ctypes.c_int), ("nx", ctypes.c_int),
+                ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("storage", ctypes.c_int),
+                ("force_T", ctypes.c_int), ("force_bx", ctypes.c_int), ("force_by", ctypes.c_int),
+                ("force_vec", ctypes.c_int), ("exact", ctypes.c_int), ("strict", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class stencil_plan_info(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int), ("bx", ctypes.c_int), ("by", ctypes.c_int),
+                ("halo", ctypes.c_int), ("vec", ctypes.c_int), ("warps", ctypes.c_int),
+                ("ctas", ctypes.c_int), ("sms", ctypes.c_int),
+                ("scratch_bytes", ctypes.c_longlong), ("exact", ctypes.c_int),
+                ("kernel_id", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# C ABI symbols, with their argument types
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+SIGNATURES = {
+    "stencil_abi_version": ([], _I),
+    "stencil_strerror": ([_I], ctypes.c_char_p),
+    "stencil_plan_create": ([ctypes.POINTER(_P), ctypes.POINTER(stencil_desc)], _I),
+    "stencil_run": ([_P, _P, _P, _P, ctypes.POINTER(ctypes.c_float), _I, _I, _I, _I], _I),
+    "stencil_plan_sync": ([_P], _I),
+    "stencil_plan_get_info": ([_P, ctypes.POINTER(stencil_plan_info)], _I),
+    "stencil_plan_set_timing": ([_P, _I], _I),
+    "stencil_plan_kernel_time": ([_P, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_longlong), _I], _I),
+    "stencil_plan_destroy": ([_P], _I),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libstencil.so is not built ({LIB_PATH}); run the package's build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (args, res) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+lib = _load()
+
+
+def strerror(code: int) -> str:
+    return lib.stencil_strerror(int(code)).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != ST_OK:
+        raise StencilError(rc, what)
+
+
+def _addr(t):
+    """Device address of a torch tensor (float32, contiguous, on a CUDA device) or an int."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor or an integer device address")
+    if not t.is_cuda:
+        raise ValueError("grids must live on a CUDA device")
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError("grids must be contiguous float32")
+    return t.data_ptr()
+
+
+def _coef_array(coeffs):
+    vals = [float(v) for v in (coeffs.tolist() if hasattr(coeffs, "tolist") else coeffs)]
+    return (ctypes.c_float * len(vals))(*vals)
+
+
+def current_stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def stencil_plan_create(kind: int, ndim: int, nx: int, ny: int, nz: int = 1, *, storage=ST_F32,
+                        force_T=0, force_bx=0, force_by=0, force_vec=0, exact=False,
+                        strict=False, stream=None):
+    d = stencil_desc(kind, ndim, nx, ny, nz if ndim == 3 else 1, storage, force_T, force_bx,
+                     force_by, force_vec, 1 if exact else 0, 1 if strict else 0,
+                     current_stream() if stream is None else stream)
+    h = ctypes.c_void_p()
+    _check(lib.stencil_plan_create(ctypes.byref(h), ctypes.byref(d)), "stencil_plan_create")
+    return h
+
+
+def stencil_run(plan, grid_in, grid_out, power, coeffs, nx, ny, nz, steps):
+    k = _coef_array(coeffs)
+    _check(lib.stencil_run(plan, _addr(grid_in), _addr(grid_out), _addr(power), k, int(nx),
+                           int(ny), int(nz), int(steps)), "stencil_run")
+
+
+def stencil_plan_sync(plan):
+    _check(lib.stencil_plan_sync(plan), "stencil_plan_sync")
+
+
+def stencil_plan_get_info(plan) -> dict:
+    info = stencil_plan_info()
+    _check(lib.stencil_plan_get_info(plan, ctypes.byref(info)), "stencil_plan_get_info")
+    return info.as_dict()
+
+
+def stencil_plan_set_timing(plan, enable: bool):
+    _check(lib.stencil_plan_set_timing(plan, 1 if enable else 0), "stencil_plan_set_timing")
+
+
+def stencil_plan_kernel_time(plan, reset: bool = True):
+    ms = ctypes.c_double()
+    n = ctypes.c_longlong()
+    _check(lib.stencil_plan_kernel_time(plan, ctypes.byref(ms), ctypes.byref(n), 1 if reset else 0),
+           "stencil_plan_kernel_time")
+    return ms.value, n.value
+
+
+def stencil_plan_destroy(plan):
+    _check(lib.stencil_plan_destroy(plan), "stencil_plan_destroy")
+
+
+class Plan:
+    """Owning wrapper: a plan for one grid shape, destroyed with the object."""
+
+    def __init__(self, kind, ndim, nx, ny, nz=1, **kw):
+        self.kind, self.ndim, self.nx, self.ny = kind, ndim, nx, ny
+        self.nz = nz if ndim == 3 else 1
+        self.h = stencil_plan_create(kind, ndim, nx, ny, self.nz, **kw)
+
+    def run(self, grid_in, grid_out, coeffs, steps, power=None):
+        stencil_run(self.h, grid_in, grid_out, power, coeffs, self.nx, self.ny, self.nz, steps)
+        return grid_out
+
+    def sync(self):
+        stencil_plan_sync(self.h)
+
+    def info(self):
+        return stencil_plan_get_info(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            stencil_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

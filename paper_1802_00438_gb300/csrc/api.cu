@@ -1,0 +1,517 @@
+// Host runtime of the stencil engine: plans, parameter choice, pass scheduling, validation.
+//
+// A run of `steps` Jacobi steps is ceil(steps / T) passes over device memory (Eq. 8 of
+// arXiv 1802.00438), each pass one launch of a temporally-blocked kernel that fuses up to T
+// steps; the last pass fuses the remainder (Sec. 3.2).  Passes ping-pong between the caller's
+// output buffer and one plan-owned scratch grid (Sec. 2.1's second buffer), ordered so that
+// the last pass lands in the output.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/stencil.h"
+#include "internal.h"
+
+using namespace stn;
+
+namespace {
+
+struct PassCfg2D {
+    Shape2D shape;
+    int ntx = 0;
+    long long total = 0, rows_per_cta = 0;
+    int ctas = 0;
+    bool ready = false;
+};
+
+struct PassCfg3D {
+    Shape3D shape;
+    int ntx = 0, nty = 0;
+    long long cols = 0, planes_per_cta = 0;
+    int ctas = 0;
+    bool ready = false;
+};
+
+}  // namespace
+
+struct stencil_plan_s {
+    stencil_desc d;
+    cudaStream_t stream = nullptr;
+    int device = 0, sms = 0;
+    float *scratch = nullptr;
+    long long ld_scratch = 0;   // row pitch of the scratch grid (2D), floats
+    size_t scratch_bytes = 0;
+    int T = 1;
+    // 2D
+    int V = 4, W = 4;
+    std::vector<PassCfg2D> cfg2;   // indexed by kernel T
+    // 3D
+    int VY = 8, NW = 8;
+    std::vector<PassCfg3D> cfg3;
+    // timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;   // pairs, reused
+    size_t ev_used = 0;
+    double ms_acc = 0.0;
+    long long launches = 0;
+    int sticky = ST_OK;
+};
+
+namespace {
+
+const int kT2[] = {1, 2, 4, 8, 12};
+const int kT2exact[] = {1, 2, 4, 8};
+const int kT3[] = {1, 2, 3, 4};
+const int kT3exact[] = {1, 2, 4};
+
+int map_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return ST_OK;
+    if (e == cudaErrorMemoryAllocation) return ST_ERR_OOM;
+    return ST_ERR_CUDA;
+}
+
+long long cells_of(const stencil_desc &d) { return (long long)d.nx * d.ny * d.nz; }
+
+int ncoef(const stencil_desc &d)
+{
+    if (d.ndim == 2) return 5;
+    return d.kind == ST_DIFFUSION ? 7 : 9;
+}
+
+// smallest available kernel T >= want for the plan's family (or the largest available)
+int kernel_T_for(const stencil_plan_s *p, int want)
+{
+    const int *ts;
+    int n;
+    if (p->d.ndim == 2) {
+        ts = p->d.exact ? kT2exact : kT2;
+        n = p->d.exact ? 4 : 5;
+    } else {
+        ts = p->d.exact ? kT3exact : kT3;
+        n = p->d.exact ? 3 : 4;
+    }
+    for (int i = 0; i < n; i++)
+        if (ts[i] >= want) return ts[i];
+    return ts[n - 1];
+}
+
+int prepare2(stencil_plan_s *p, int Tk, PassCfg2D **out)
+{
+    if ((int)p->cfg2.size() <= Tk) p->cfg2.resize(Tk + 1);
+    PassCfg2D &c = p->cfg2[Tk];
+    if (!c.ready) {
+        c.shape = Shape2D{p->d.kind, p->d.exact ? 1 : 0, Tk, p->V, p->W};
+        if (!tb2d_available(c.shape)) return ST_ERR_UNSUPPORTED;
+        int bps = 0;
+        cudaError_t e = tb2d_prepare(c.shape, &bps);
+        if (e != cudaSuccess) return map_cuda(e);
+        if (bps < 1) return ST_ERR_UNSUPPORTED;
+        const int bx = tb2d_tile_width(c.shape), h = tb2d_halo(c.shape);
+        const int cx = bx - 2 * h;
+        c.ntx = (p->d.nx + cx - 1) / cx;
+        c.total = (long long)c.ntx * p->d.ny;
+        // each block streams at least ~8T rows so the y-halo (2T rows per segment) stays small
+        const long long min_rows = std::max(16, 8 * Tk);
+        long long ctas = std::min<long long>((long long)p->sms * bps,
+                                             std::max<long long>(1, c.total / min_rows));
+        c.rows_per_cta = (c.total + ctas - 1) / ctas;
+        c.ctas = (int)((c.total + c.rows_per_cta - 1) / c.rows_per_cta);
+        c.ready = true;
+    }
+    *out = &c;
+    return ST_OK;
+}
+
+int prepare3(stencil_plan_s *p, int Tk, PassCfg3D **out)
+{
+    if ((int)p->cfg3.size() <= Tk) p->cfg3.resize(Tk + 1);
+    PassCfg3D &c = p->cfg3[Tk];
+    if (!c.ready) {
+        c.shape = Shape3D{p->d.kind, p->d.exact ? 1 : 0, Tk, p->VY, p->NW};
+        if (!tb3d_available(c.shape)) return ST_ERR_UNSUPPORTED;
+        int bps = 0;
+        cudaError_t e = tb3d_prepare(c.shape, &bps);
+        if (e != cudaSuccess) return map_cuda(e);
+        if (bps < 1) return ST_ERR_UNSUPPORTED;
+        const int hx = (Tk + 3) / 4 * 4, hy = Tk;
+        const int cx = 64 - 2 * hx, cy = p->VY * p->NW - 2 * hy;
+        c.ntx = (p->d.nx + cx - 1) / cx;
+        c.nty = (p->d.ny + cy - 1) / cy;
+        c.cols = (long long)c.ntx * c.nty;
+        const long long total = c.cols * p->d.nz;
+        const long long min_planes = std::max(16, 8 * Tk);
+        long long ctas = std::min<long long>((long long)p->sms * bps,
+                                             std::max<long long>(1, total / min_planes));
+        c.planes_per_cta = (total + ctas - 1) / ctas;
+        c.ctas = (int)((total + c.planes_per_cta - 1) / c.planes_per_cta);
+        c.ready = true;
+    }
+    *out = &c;
+    return ST_OK;
+}
+
+bool ranges_overlap(const void *a, const void *b, size_t n)
+{
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + n && y < x + n;
+}
+
+bool stable(const stencil_desc &d, const float *k)
+{
+    const double eps = 1e-6;
+    for (int i = 0; i < ncoef(d); i++)
+        if (!std::isfinite(k[i])) return false;
+    if (d.kind == ST_DIFFUSION) {
+        double s = 0;
+        for (int i = 0; i < ncoef(d); i++) {
+            if (k[i] < 0) return false;
+            s += k[i];
+        }
+        return s <= 1.0 + eps;
+    }
+    if (d.ndim == 2) {
+        const double kdt = k[0], rx = k[1], ry = k[2], rz = k[3];
+        if (kdt < 0 || rx < 0 || ry < 0 || rz < 0) return false;
+        return kdt * (2 * rx + 2 * ry + rz) <= 1.0 + eps;
+    }
+    for (int i = 0; i < 8; i++)
+        if (k[i] < 0) return false;
+    return true;
+}
+
+cudaError_t record(stencil_plan_s *p, bool begin)
+{
+    if (!p->timing) return cudaSuccess;
+    if (begin && p->ev_used + 2 > p->ev.size()) {
+        for (int i = 0; i < 64; i++) {
+            cudaEvent_t e;
+            cudaError_t err = cudaEventCreate(&e);
+            if (err != cudaSuccess) return err;
+            p->ev.push_back(e);
+        }
+    }
+    cudaError_t err = cudaEventRecord(p->ev[p->ev_used], p->stream);
+    p->ev_used++;
+    return err;
+}
+
+int flush_timing(stencil_plan_s *p)
+{
+    if (p->ev_used == 0) return ST_OK;
+    cudaError_t e = cudaEventSynchronize(p->ev[p->ev_used - 1]);
+    if (e != cudaSuccess) return map_cuda(e);
+    for (size_t i = 0; i + 1 < p->ev_used; i += 2) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, p->ev[i], p->ev[i + 1]);
+        if (e != cudaSuccess) return map_cuda(e);
+        p->ms_acc += ms;
+        p->launches++;
+    }
+    p->ev_used = 0;
+    return ST_OK;
+}
+
+int run_pass2(stencil_plan_s *p, const float *src, long long lds, float *dst, long long ldd,
+              const float *pw, const float *k, int tsteps)
+{
+    PassCfg2D *c = nullptr;
+    int rc = prepare2(p, kernel_T_for(p, tsteps), &c);
+    if (rc != ST_OK) return rc;
+    Pass2D a;
+    a.in = src;
+    a.out = dst;
+    a.pw = pw;
+    a.ld_in = lds;
+    a.ld_out = ldd;
+    a.ld_pw = p->d.nx;
+    a.nx = p->d.nx;
+    a.ny = p->d.ny;
+    a.tsteps = tsteps;
+    a.ntx = c->ntx;
+    a.total_rows = c->total;
+    a.rows_per_cta = c->rows_per_cta;
+    a.ctas = c->ctas;
+    for (int i = 0; i < 5; i++) a.k[i] = k[i];
+    a.vec_in = ((uintptr_t)src % 16 == 0) && (lds % 4 == 0);
+    a.vec_out = ((uintptr_t)dst % 16 == 0) && (ldd % 4 == 0);
+    a.vec_pw = pw ? (((uintptr_t)pw % 16 == 0) && (p->d.nx % 4 == 0)) : 0;
+    if (p->timing && p->ev_used + 2 > 2 * 1024) {
+        rc = flush_timing(p);
+        if (rc != ST_OK) return rc;
+    }
+    cudaError_t e = record(p, true);
+    if (e == cudaSuccess) e = tb2d_launch(c->shape, a, p->stream);
+    if (e == cudaSuccess) e = record(p, false);
+    return map_cuda(e);
+}
+
+int run_pass3(stencil_plan_s *p, const float *src, float *dst, const float *pw, const float *k,
+              int tsteps)
+{
+    PassCfg3D *c = nullptr;
+    int rc = prepare3(p, kernel_T_for(p, tsteps), &c);
+    if (rc != ST_OK) return rc;
+    Pass3D a;
+    a.in = src;
+    a.out = dst;
+    a.pw = pw;
+    a.nx = p->d.nx;
+    a.ny = p->d.ny;
+    a.nz = p->d.nz;
+    a.tsteps = tsteps;
+    a.ntx = c->ntx;
+    a.nty = c->nty;
+    a.total_cols = c->cols;
+    a.planes_per_cta = c->planes_per_cta;
+    a.ctas = c->ctas;
+    for (int i = 0; i < 9; i++) a.k[i] = i < ncoef(p->d) ? k[i] : 0.f;
+    a.vec = ((uintptr_t)src % 16 == 0) && ((uintptr_t)dst % 16 == 0) && (p->d.nx % 4 == 0);
+    if (p->timing && p->ev_used + 2 > 2 * 1024) {
+        rc = flush_timing(p);
+        if (rc != ST_OK) return rc;
+    }
+    cudaError_t e = record(p, true);
+    if (e == cudaSuccess) e = tb3d_launch(c->shape, a, p->stream);
+    if (e == cudaSuccess) e = record(p, false);
+    return map_cuda(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+int stencil_abi_version(void) { return ST_ABI_VERSION; }
+
+const char *stencil_strerror(int code)
+{
+    switch (code) {
+    case ST_OK: return "ok";
+    case ST_ERR_INVALID_ARG: return "invalid argument";
+    case ST_ERR_DIMS_MISMATCH: return "grid dimensions differ from the plan's";
+    case ST_ERR_UNSTABLE_COEFFS: return "coefficients violate the explicit stability bound";
+    case ST_ERR_CUDA: return "CUDA runtime error";
+    case ST_ERR_OOM: return "device memory allocation failed";
+    case ST_ERR_TIMEOUT: return "bounded device wait timed out";
+    case ST_ERR_UNSUPPORTED: return "unsupported parameter combination";
+    default: return "unknown status";
+    }
+}
+
+int stencil_plan_create(stencil_plan *out, const stencil_desc *desc)
+{
+    if (!out) return ST_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!desc) return ST_ERR_INVALID_ARG;
+    stencil_desc d = *desc;
+    if (d.kind != ST_DIFFUSION && d.kind != ST_THERMAL) return ST_ERR_INVALID_ARG;
+    if (d.ndim != 2 && d.ndim != 3) return ST_ERR_INVALID_ARG;
+    if (d.ndim == 2) d.nz = 1;
+    if (d.nx < 1 || d.ny < 1 || d.nz < 1) return ST_ERR_INVALID_ARG;
+    if (d.storage != ST_F32) return ST_ERR_UNSUPPORTED;
+    if (d.force_T < 0 || d.force_bx < 0 || d.force_by < 0 || d.force_vec < 0)
+        return ST_ERR_INVALID_ARG;
+
+    stencil_plan_s *p = new (std::nothrow) stencil_plan_s();
+    if (!p) return ST_ERR_OOM;
+    p->d = d;
+    p->stream = static_cast<cudaStream_t>(d.stream);
+    int rc = ST_OK;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return map_cuda(e);
+    }
+
+    if (d.ndim == 2) {
+        // tile: V cells per thread, W warps per block (bsize_x = 32 V W); defaults favour wide
+        // tiles (little halo overhead) unless the grid is too narrow to fill the device
+        p->V = d.force_vec ? d.force_vec : 4;
+        if (d.force_bx) {
+            if (d.force_bx % (32 * p->V)) rc = ST_ERR_UNSUPPORTED;
+            p->W = d.force_bx / (32 * p->V);
+        }
+        int want = d.force_T ? d.force_T : 12;
+        p->T = kernel_T_for(p, want);
+        if (!d.force_bx) {
+            // widest tile that still leaves every SM a few blocks' worth of tile columns;
+            // fall back to what is compiled for this (kind, exact, T, V)
+            const int pref[3] = {d.nx >= 2048 ? 4 : (d.nx >= 512 ? 2 : 1), 4, 1};
+            p->W = 0;
+            for (int w : pref)
+                if (!p->W && tb2d_available(Shape2D{d.kind, d.exact ? 1 : 0, p->T, p->V, w}))
+                    p->W = w;
+            if (!p->W) rc = ST_ERR_UNSUPPORTED;
+        }
+        if (d.force_T && p->T != d.force_T) rc = ST_ERR_UNSUPPORTED;
+        PassCfg2D *c = nullptr;
+        if (rc == ST_OK) rc = prepare2(p, p->T, &c);
+        if (rc == ST_OK) {
+            p->ld_scratch = ((long long)d.nx + 31) / 32 * 32;
+            p->scratch_bytes = (size_t)p->ld_scratch * d.ny * sizeof(float);
+        }
+    } else {
+        if (d.force_vec && d.force_vec != 2) rc = ST_ERR_UNSUPPORTED;
+        if (d.force_bx && d.force_bx != 64) rc = ST_ERR_UNSUPPORTED;
+        if (d.force_by && d.force_by != 64) rc = ST_ERR_UNSUPPORTED;
+        p->VY = 8;
+        p->NW = 8;
+        int want = d.force_T ? d.force_T : 4;
+        p->T = kernel_T_for(p, want);
+        if (d.force_T && p->T != d.force_T) rc = ST_ERR_UNSUPPORTED;
+        PassCfg3D *c = nullptr;
+        if (rc == ST_OK) rc = prepare3(p, p->T, &c);
+        p->scratch_bytes = (size_t)cells_of(d) * sizeof(float);
+    }
+    if (rc == ST_OK) {
+        e = cudaMalloc(&p->scratch, p->scratch_bytes);
+        if (e != cudaSuccess) rc = map_cuda(e);
+    }
+    if (rc != ST_OK) {
+        if (p->scratch) cudaFree(p->scratch);
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return ST_OK;
+}
+
+int stencil_run(stencil_plan p, const void *grid_in, void *grid_out, const void *power,
+                const float *coeffs, int nx, int ny, int nz, int steps)
+{
+    if (!p || !grid_in || !grid_out || !coeffs || steps < 0) return ST_ERR_INVALID_ARG;
+    const stencil_desc &d = p->d;
+    if (d.ndim == 2 && nz != 1) return ST_ERR_DIMS_MISMATCH;
+    if (nx != d.nx || ny != d.ny || nz != d.nz) return ST_ERR_DIMS_MISMATCH;
+    if ((d.kind == ST_THERMAL) != (power != nullptr)) return ST_ERR_INVALID_ARG;
+    const size_t bytes = (size_t)cells_of(d) * sizeof(float);
+    if (grid_in != grid_out && ranges_overlap(grid_in, grid_out, bytes)) return ST_ERR_INVALID_ARG;
+    if (power && ranges_overlap(power, grid_out, bytes)) return ST_ERR_INVALID_ARG;
+    if (d.strict && !stable(d, coeffs)) return ST_ERR_UNSTABLE_COEFFS;
+    if (p->sticky != ST_OK) return p->sticky;
+
+    const float *in = static_cast<const float *>(grid_in);
+    float *out = static_cast<float *>(grid_out);
+    const float *pw = static_cast<const float *>(power);
+    cudaError_t e;
+    if (steps == 0) {
+        if (in == out) return ST_OK;
+        e = cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, p->stream);
+        return map_cuda(e);
+    }
+    const int T = p->T;
+    const int passes = (steps + T - 1) / T;
+    const int last = steps - T * (passes - 1);
+    // buffer of pass i: the caller's output when (passes-1-i) is even, else the scratch grid;
+    // in place with an odd pass count, pass 0 cannot write the input it reads, so every pass
+    // shifts by one and a final copy brings the scratch result to the output.
+    const bool shift = (in == out) && (passes % 2 == 1);
+    const long long ldo = d.nx, ldsc = d.ndim == 2 ? p->ld_scratch : d.nx;
+    const float *src = in;
+    long long lds = d.nx;
+    for (int i = 0; i < passes; i++) {
+        const int ts = (i == passes - 1) ? last : T;
+        const bool to_out = shift ? ((passes - i) % 2 == 0) : ((passes - 1 - i) % 2 == 0);
+        float *dst = to_out ? out : p->scratch;
+        const long long ldd = to_out ? ldo : ldsc;
+        int rc = d.ndim == 2 ? run_pass2(p, src, lds, dst, ldd, pw, coeffs, ts)
+                             : run_pass3(p, src, dst, pw, coeffs, ts);
+        if (rc != ST_OK) {
+            p->sticky = rc;
+            return rc;
+        }
+        src = dst;
+        lds = ldd;
+    }
+    if (shift) {
+        if (d.ndim == 2)
+            e = cudaMemcpy2DAsync(out, (size_t)d.nx * sizeof(float), p->scratch,
+                                  (size_t)p->ld_scratch * sizeof(float), (size_t)d.nx * sizeof(float),
+                                  d.ny, cudaMemcpyDeviceToDevice, p->stream);
+        else
+            e = cudaMemcpyAsync(out, p->scratch, bytes, cudaMemcpyDeviceToDevice, p->stream);
+        if (e != cudaSuccess) return map_cuda(e);
+    }
+    return ST_OK;
+}
+
+int stencil_plan_sync(stencil_plan p)
+{
+    if (!p) return ST_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return map_cuda(e);
+    return p->sticky;
+}
+
+int stencil_plan_get_info(stencil_plan p, stencil_plan_info *info)
+{
+    if (!p || !info) return ST_ERR_INVALID_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->T = p->T;
+    info->sms = p->sms;
+    info->scratch_bytes = (long long)p->scratch_bytes;
+    info->exact = p->d.exact;
+    if (p->d.ndim == 2) {
+        PassCfg2D *c = nullptr;
+        int rc = prepare2(p, p->T, &c);
+        if (rc != ST_OK) return rc;
+        info->bx = 32 * p->V * p->W;
+        info->by = 0;
+        info->halo = (p->T + 3) / 4 * 4;
+        info->vec = p->V;
+        info->warps = p->W;
+        info->ctas = c->ctas;
+        info->kernel_id = 2;
+    } else {
+        PassCfg3D *c = nullptr;
+        int rc = prepare3(p, p->T, &c);
+        if (rc != ST_OK) return rc;
+        info->bx = 64;
+        info->by = p->VY * p->NW;
+        info->halo = p->T;
+        info->vec = 2;
+        info->warps = p->NW;
+        info->ctas = c->ctas;
+        info->kernel_id = 3;
+    }
+    return ST_OK;
+}
+
+int stencil_plan_set_timing(stencil_plan p, int enable)
+{
+    if (!p) return ST_ERR_INVALID_ARG;
+    p->timing = enable != 0;
+    return ST_OK;
+}
+
+int stencil_plan_kernel_time(stencil_plan p, double *ms, long long *launches, int reset)
+{
+    if (!p || !ms || !launches) return ST_ERR_INVALID_ARG;
+    int rc = flush_timing(p);
+    if (rc != ST_OK) return rc;
+    *ms = p->ms_acc;
+    *launches = p->launches;
+    if (reset) {
+        p->ms_acc = 0.0;
+        p->launches = 0;
+    }
+    return ST_OK;
+}
+
+int stencil_plan_destroy(stencil_plan p)
+{
+    if (!p) return ST_OK;
+    if (p->ev_used) cudaStreamSynchronize(p->stream);
+    for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+    if (p->scratch) cudaFree(p->scratch);
+    delete p;
+    return ST_OK;
+}
+
+}  // extern "C"

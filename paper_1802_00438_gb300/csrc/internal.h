@@ -1,0 +1,57 @@
+// Interface between the host runtime (api.cu) and the kernel translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace stn {
+
+// One pass of the 2D temporally-blocked sweep (tb2d.cu).
+struct Pass2D {
+    const float *in;
+    float *out;
+    const float *pw;       // power map (thermal) or nullptr
+    long long ld_in, ld_out, ld_pw;   // row pitches in floats
+    int nx, ny;
+    int tsteps;            // steps fused in this pass, 1..T
+    int ntx;               // tiles along x
+    long long total_rows;  // ntx * ny: the (tile column, row) pairs of the pass
+    long long rows_per_cta;
+    int ctas;
+    float k[5];
+    int vec_in, vec_out, vec_pw;   // 1: rows start on 16-byte boundaries
+};
+
+struct Shape2D { int kind, exact, T, V, W; };
+
+bool tb2d_available(const Shape2D &s);
+int tb2d_block_threads(const Shape2D &s);
+int tb2d_tile_width(const Shape2D &s);   // cells per tile incl. halos
+int tb2d_halo(const Shape2D &s);
+size_t tb2d_smem_bytes(const Shape2D &s);
+cudaError_t tb2d_prepare(const Shape2D &s, int *blocks_per_sm);   // smem opt-in + occupancy
+cudaError_t tb2d_launch(const Shape2D &s, const Pass2D &p, cudaStream_t st);
+
+// One pass of the 3D sweep (tb3d.cu).
+struct Pass3D {
+    const float *in;
+    float *out;
+    const float *pw;
+    int nx, ny, nz;
+    int tsteps;
+    int ntx, nty;          // tiles along x and y
+    long long total_cols;  // ntx * nty tile columns (each streamed along z)
+    long long planes_per_cta;
+    int ctas;
+    float k[9];
+    int vec;               // 1: rows start on 16-byte boundaries
+};
+
+struct Shape3D { int kind, exact, T, VY, NW; };   // tile 64 x (VY*NW) cells
+
+bool tb3d_available(const Shape3D &s);
+int tb3d_block_threads(const Shape3D &s);
+int tb3d_halo(const Shape3D &s);
+size_t tb3d_smem_bytes(const Shape3D &s);
+cudaError_t tb3d_prepare(const Shape3D &s, int *blocks_per_sm);
+cudaError_t tb3d_launch(const Shape3D &s, const Pass3D &p, cudaStream_t st);
+
+}  // namespace stn

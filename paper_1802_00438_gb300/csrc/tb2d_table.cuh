@@ -1,0 +1,22 @@
+// Registry of the compiled 2D kernel instances.
+#pragma once
+#include "tb2d_kernel.cuh"
+
+namespace stn {
+
+struct Tb2dEntry {
+    int kind, exact, T, V, W;
+    const void *fn;
+    size_t smem;
+};
+
+#define STN_TB2_ENTRY(K, E, T_, V_, W_)                                                      \
+    { K, E, T_, V_, W_, reinterpret_cast<const void *>(&k_tb2d<K, (E != 0), T_, V_, W_>),  \
+      TB2<K, (E != 0), T_, V_, W_>::SMEM }
+
+extern const Tb2dEntry tb2d_table_diff[];
+extern const int tb2d_table_diff_n;
+extern const Tb2dEntry tb2d_table_therm[];
+extern const int tb2d_table_therm_n;
+
+}  // namespace stn

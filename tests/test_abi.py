@@ -1,0 +1,70 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds and loads, exports every
+function include/stencil.h declares, and the Python binding names exactly those functions."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared(header):
+    src = open(os.path.join(ROOT, "include", header)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(stencil_\w+)\s*\(", src, re.M))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    import __graft_entry__
+    return __graft_entry__._engine_build_module().build()
+
+
+def test_header_functions_exported(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            names |= _declared(h)
+    assert "stencil_run" in names and "stencil_plan_create" in names
+    for n in sorted(names):
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+
+
+def test_binding_covers_header(lib_path):
+    import paper_1802_00438_gb300 as st
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            names |= _declared(h)
+    assert names == set(st.SIGNATURES), names ^ set(st.SIGNATURES)
+
+
+def test_host_only_calls(lib_path):
+    import paper_1802_00438_gb300 as st
+    assert st.lib.stencil_abi_version() == 1
+    assert st.strerror(0) == "ok"
+    assert "dimensions" in st.strerror(st.ST_ERR_DIMS_MISMATCH)
+    assert st.strerror(12345) == "unknown status"
+    # argument validation happens before any device work
+    assert st.lib.stencil_plan_create(None, None) == st.ST_ERR_INVALID_ARG
+    h = ctypes.c_void_p()
+    bad = st.stencil_desc(7, 2, 8, 8, 1, 0, 0, 0, 0, 0, 0, 0, None)
+    assert st.lib.stencil_plan_create(ctypes.byref(h), ctypes.byref(bad)) == st.ST_ERR_INVALID_ARG
+    bad = st.stencil_desc(0, 4, 8, 8, 1, 0, 0, 0, 0, 0, 0, 0, None)
+    assert st.lib.stencil_plan_create(ctypes.byref(h), ctypes.byref(bad)) == st.ST_ERR_INVALID_ARG
+    bad = st.stencil_desc(0, 2, 0, 8, 1, 0, 0, 0, 0, 0, 0, 0, None)
+    assert st.lib.stencil_plan_create(ctypes.byref(h), ctypes.byref(bad)) == st.ST_ERR_INVALID_ARG
+    assert st.lib.stencil_run(None, None, None, None, None, 1, 1, 1, 1) == st.ST_ERR_INVALID_ARG
+    assert st.lib.stencil_plan_destroy(None) == st.ST_OK
+
+
+def test_no_oracle_in_product():
+    """The engine package never imports, links or runs the oracle."""
+    pkg = os.path.join(ROOT, "paper_1802_00438_gb300")
+    for dp, _, fs in os.walk(pkg):
+        for f in fs:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dp, f)).read()
+                assert "oracle" not in txt.lower().replace("oracle's", ""), os.path.join(dp, f)

@@ -1,0 +1,212 @@
+"""GPU parity: the engine (through the C ABI) against the CPU oracle on the same seeded inputs.
+
+Bars (arXiv 1802.00438 fixes single precision, Sec. 5.1):
+  exact plans (Table 2 order, one rounding per operation)  -> bit-identical to the float32 oracle
+  contracted plans (fused multiply-adds)                    -> max relative error <= 1e-5
+with max relative error = max_i |g_i - o_i| / max(|o_i|, 1e-6 * max_j |o_j|).
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def eng():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1802_00438_gb300 as st
+    return st
+
+
+def max_rel(g, o):
+    g = np.asarray(g, np.float64)
+    o = np.asarray(o, np.float64)
+    floor = 1e-6 * max(np.max(np.abs(o)), 1e-300)
+    return float(np.max(np.abs(g - o) / np.maximum(np.abs(o), floor)))
+
+
+def gpu_run(st, w, steps, exact=False, T=0, bx=0, inplace=False):
+    import torch
+    u = torch.from_numpy(np.ascontiguousarray(w.u0)).cuda()
+    p = None if w.power is None else torch.from_numpy(np.ascontiguousarray(w.power)).cuda()
+    out = u if inplace else torch.full_like(u, float("nan"))
+    plan = st.Plan(w.kind, w.ndim, w.nx, w.ny, w.nz, exact=exact, force_T=T, force_bx=bx)
+    plan.run(u, out, w.coef, steps, power=p)
+    plan.sync()
+    info = plan.info()
+    plan.close()
+    return out.cpu().numpy(), info
+
+
+SIZES_2D = [(1, 1), (1, 7), (7, 1), (2, 2), (5, 3), (13, 11), (31, 17), (97, 61), (130, 67),
+            (257, 129), (509, 263), (1031, 45)]
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("T,bx", [(1, 128), (2, 128), (4, 512), (8, 128), (8, 512)])
+def test_exact_2d_bitwise(eng, orc, kind, T, bx):
+    for t, (nx, ny) in enumerate(SIZES_2D):
+        w = synth.make(kind, 2, nx, ny, seed=1000 + 37 * t + kind)
+        for steps in sorted({0, 1, max(T - 1, 1), T, T + 1, 2 * T + 3}):
+            g, _ = gpu_run(eng, w, steps, exact=True, T=T, bx=bx)
+            o = orc.run(kind, w.u0, w.coef, steps, w.power)
+            assert np.array_equal(g, o), (nx, ny, steps, max_rel(g, o))
+
+
+SIZES_3D = [(1, 1, 1), (2, 3, 4), (7, 5, 3), (33, 17, 9), (65, 66, 13), (130, 70, 20), (64, 64, 64)]
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("T", [1, 2, 4])
+def test_exact_3d_bitwise(eng, orc, kind, T):
+    for t, (nx, ny, nz) in enumerate(SIZES_3D):
+        w = synth.make(kind, 3, nx, ny, nz, seed=2000 + 31 * t + kind)
+        for steps in sorted({0, 1, T, T + 1, 2 * T + 1}):
+            g, _ = gpu_run(eng, w, steps, exact=True, T=T)
+            o = orc.run(kind, w.u0, w.coef, steps, w.power)
+            assert np.array_equal(g, o), (nx, ny, nz, steps, max_rel(g, o))
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("T,bx", [(1, 128), (4, 256), (8, 512), (12, 512), (12, 128), (8, 256)])
+def test_contracted_2d(eng, orc, kind, T, bx):
+    for t, (nx, ny) in enumerate(SIZES_2D[::2] + [(700, 300)]):
+        w = synth.make(kind, 2, nx, ny, seed=3000 + 41 * t + kind)
+        for steps in (1, T + 1, 3 * T + 2, 50):
+            g, _ = gpu_run(eng, w, steps, T=T, bx=bx)
+            o = orc.run(kind, w.u0, w.coef, steps, w.power)
+            assert max_rel(g, o) <= TOL, (nx, ny, steps, max_rel(g, o))
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("T", [1, 2, 3, 4])
+def test_contracted_3d(eng, orc, kind, T):
+    for t, (nx, ny, nz) in enumerate(SIZES_3D[2:]):
+        w = synth.make(kind, 3, nx, ny, nz, seed=4000 + 43 * t + kind)
+        for steps in (1, T + 2, 3 * T + 1):
+            g, _ = gpu_run(eng, w, steps, T=T)
+            o = orc.run(kind, w.u0, w.coef, steps, w.power)
+            assert max_rel(g, o) <= TOL, (nx, ny, nz, steps, max_rel(g, o))
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_in_place(eng, orc, ndim):
+    for kind in (0, 1):
+        if ndim == 2:
+            w = synth.make(kind, 2, 301, 77, seed=5000 + kind)
+            T = 4
+        else:
+            w = synth.make(kind, 3, 40, 30, 20, seed=5010 + kind)
+            T = 2
+        for steps in (1, T, T + 1, 3 * T, 3 * T + 1):   # odd and even pass counts
+            g, _ = gpu_run(eng, w, steps, exact=True, T=T, inplace=True)
+            o = orc.run(kind, w.u0, w.coef, steps, w.power)
+            assert np.array_equal(g, o), (kind, steps)
+
+
+def test_default_plans_configs_reduced(eng, orc):
+    """The default (autotuned) plans of each configuration on reduced grids, full step count."""
+    cases = [synth.c1_diffusion2d(),                                   # 1024^2, 100 steps
+             synth.c2_thermal2d(nx=1536, ny=1280, steps=1000),
+             synth.c3a_diffusion3d(n=96, steps=200),
+             synth.c3b_thermal3d(nx=96, ny=80, nz=48, steps=200)]
+    for w in cases:
+        g, info = gpu_run(eng, w, w.steps)
+        o = orc.run(w.kind, w.u0, w.coef, w.steps, w.power)
+        assert max_rel(g, o) <= TOL, (w.name, info, max_rel(g, o))
+
+
+def test_c1_exact_full(eng, orc):
+    w = synth.c1_diffusion2d()
+    g, _ = gpu_run(eng, w, w.steps, exact=True)
+    o = orc.run(w.kind, w.u0, w.coef, w.steps, w.power)
+    assert np.array_equal(g, o)
+
+
+def test_errors(eng):
+    import torch
+    st = eng
+    u = torch.zeros(16, 16, device="cuda")
+    plan = st.Plan(0, 2, 16, 16)
+    with pytest.raises(st.StencilError) as e:
+        st.stencil_run(plan.h, u, u, None, [0.2] * 5, 16, 15, 1, 1)
+    assert e.value.code == st.ST_ERR_DIMS_MISMATCH
+    with pytest.raises(st.StencilError) as e:
+        st.stencil_run(plan.h, u, u, u, [0.2] * 5, 16, 16, 1, 1)   # power on diffusion
+    assert e.value.code == st.ST_ERR_INVALID_ARG
+    with pytest.raises(st.StencilError) as e:
+        st.stencil_run(plan.h, u, u.view(-1)[1:].data_ptr(), None, [0.2] * 5, 16, 16, 1, 1)
+    assert e.value.code == st.ST_ERR_INVALID_ARG                  # partial overlap
+    with pytest.raises(st.StencilError) as e:
+        st.stencil_run(plan.h, u, u, None, [0.2] * 5, 16, 16, 1, -1)
+    assert e.value.code == st.ST_ERR_INVALID_ARG
+    strict = st.Plan(0, 2, 16, 16, strict=True)
+    with pytest.raises(st.StencilError) as e:
+        strict.run(u, u, [0.5, 0.5, 0.5, 0.1, 0.1], 1)
+    assert e.value.code == st.ST_ERR_UNSTABLE_COEFFS
+    strict.run(u, u, [0.2] * 5, 1)
+    strict.sync()
+    with pytest.raises(st.StencilError) as e:
+        st.Plan(0, 2, 16, 16, force_T=7)
+    assert e.value.code == st.ST_ERR_UNSUPPORTED
+
+
+# --- full sizes, in the launch configuration the benchmark times ---------------------------
+
+def _full(st, orc, w, steps):
+    g, info = gpu_run(st, w, steps)
+    o = orc.run(w.kind, w.u0, w.coef, steps, w.power)
+    return g, o, info
+
+
+@pytest.mark.slow
+def test_c2_full_size_elementwise(eng, orc):
+    """16384^2 thermal with the default plan: every cell after 2T+3 steps (multi-pass,
+    remainder pass, every tile and segment boundary)."""
+    w = synth.c2_thermal2d()
+    g0, info = gpu_run(eng, w, 0)
+    T = info["T"]
+    g, o, _ = _full(eng, orc, w, 2 * T + 3)
+    assert max_rel(g, o) <= TOL, max_rel(g, o)
+
+
+@pytest.mark.slow
+def test_c3_full_size_elementwise(eng, orc):
+    for w in (synth.c3a_diffusion3d(), synth.c3b_thermal3d()):
+        _, info = gpu_run(eng, w, 0)
+        T = info["T"]
+        g, o, _ = _full(eng, orc, w, 2 * T + 1)
+        assert max_rel(g, o) <= TOL, (w.name, max_rel(g, o))
+
+
+@pytest.mark.slow
+def test_c2_full_steps_closed_form(eng):
+    """16384^2, 1000 steps on a DCT-II eigenmode around the thermal steady state: the
+    deviation must decay by exactly lambda^1000 (a property that holds at any size)."""
+    import math
+    nx = ny = 16384
+    kdt, rx, ry, rz, amb, p0 = 0.75, 0.15, 0.125, 5e-4, 80.0, 0.125
+    tstar = amb + p0 / rz                     # 330 K
+    kx, ky = 3, 2
+    phx = np.cos(np.pi * kx * (np.arange(nx) + 0.5) / nx)
+    phy = np.cos(np.pi * ky * (np.arange(ny) + 0.5) / ny)
+    eps = 8.0
+    u0 = (tstar + eps * np.outer(phy, phx)).astype(np.float32)
+    w = synth.Workload("eig", 1, 2, nx, ny, 1, 1000, 0, u0,
+                       np.full((ny, nx), p0, np.float32),
+                       np.array([kdt, rx, ry, rz, amb], np.float32))
+    g, _ = gpu_run(eng, w, 1000)
+    lam = 1 - kdt * (2 * rx * (1 - math.cos(math.pi * kx / nx))
+                     + 2 * ry * (1 - math.cos(math.pi * ky / ny)) + rz)
+    rows = np.r_[0:4, 8000:8004, ny - 4:ny]
+    expect = tstar + eps * lam ** 1000 * np.outer(phy[rows], phx)
+    got = g[rows].astype(np.float64)
+    # float32 storage of ~330 K: ulp 3e-5; 1000 steps of rounding stay well under 2e-3 K
+    assert np.max(np.abs(got - expect)) < 2e-3
+    assert np.all(np.isfinite(g))
