@@ -194,6 +194,7 @@ def main():
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--T", type=int, default=0, help="force the fused step count")
     ap.add_argument("--bx", type=int, default=0, help="force the 2D tile width")
+    ap.add_argument("--vec", type=int, default=0, help="force cells per thread along x")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--nx", type=int, default=0, help="profiling: override the grid size")
@@ -229,7 +230,7 @@ def main():
     pw = None if w.power is None else torch.from_numpy(w.power).to(dev)
     out = torch.empty_like(u0)
     plan = st.Plan(w.kind, w.ndim, w.nx, w.ny, w.nz, force_T=args.T, force_bx=args.bx,
-                   stream=stream.cuda_stream)
+                   force_vec=args.vec, stream=stream.cuda_stream)
     info = plan.info()
     T = info["T"]
     passes = -(-w.steps // T)

@@ -64,10 +64,7 @@ struct stencil_plan_s {
 
 namespace {
 
-const int kT2[] = {1, 2, 4, 8, 12};
-const int kT2exact[] = {1, 2, 4, 8};
-const int kT3[] = {1, 2, 3, 4};
-const int kT3exact[] = {1, 2, 4};
+const int kTcand[] = {1, 2, 3, 4, 6, 8, 12, 16};
 
 int map_cuda(cudaError_t e)
 {
@@ -84,21 +81,22 @@ int ncoef(const stencil_desc &d)
     return d.kind == ST_DIFFUSION ? 7 : 9;
 }
 
-// smallest available kernel T >= want for the plan's family (or the largest available)
+bool available(const stencil_plan_s *p, int T)
+{
+    if (p->d.ndim == 2) return tb2d_available(Shape2D{p->d.kind, p->d.exact ? 1 : 0, T, p->V, p->W});
+    return tb3d_available(Shape3D{p->d.kind, p->d.exact ? 1 : 0, T, p->VY, p->NW});
+}
+
+// smallest compiled kernel T >= want for the plan's family (or the largest compiled one)
 int kernel_T_for(const stencil_plan_s *p, int want)
 {
-    const int *ts;
-    int n;
-    if (p->d.ndim == 2) {
-        ts = p->d.exact ? kT2exact : kT2;
-        n = p->d.exact ? 4 : 5;
-    } else {
-        ts = p->d.exact ? kT3exact : kT3;
-        n = p->d.exact ? 3 : 4;
+    int best = 0;
+    for (int t : kTcand) {
+        if (!available(p, t)) continue;
+        if (t >= want) return t;
+        best = t;
     }
-    for (int i = 0; i < n; i++)
-        if (ts[i] >= want) return ts[i];
-    return ts[n - 1];
+    return best;
 }
 
 int prepare2(stencil_plan_s *p, int Tk, PassCfg2D **out)
@@ -330,26 +328,20 @@ int stencil_plan_create(stencil_plan *out, const stencil_desc *desc)
     }
 
     if (d.ndim == 2) {
-        // tile: V cells per thread, W warps per block (bsize_x = 32 V W); defaults favour wide
-        // tiles (little halo overhead) unless the grid is too narrow to fill the device
-        p->V = d.force_vec ? d.force_vec : 4;
+        // Contracted plans run one-warp tiles of V = 8 cells per thread (bsize_x = 256) with
+        // partial-sum stages; exact plans run the rotating-window kernel, V = 4, with W warps
+        // per tile (bsize_x = 128 W).
+        p->V = d.force_vec ? d.force_vec : (d.exact ? 4 : 8);
         if (d.force_bx) {
             if (d.force_bx % (32 * p->V)) rc = ST_ERR_UNSUPPORTED;
             p->W = d.force_bx / (32 * p->V);
+        } else {
+            p->W = 1;
+            if (d.exact && d.nx >= 512) p->W = 4;
         }
-        int want = d.force_T ? d.force_T : 12;
+        const int want = d.force_T ? d.force_T : 8;
         p->T = kernel_T_for(p, want);
-        if (!d.force_bx) {
-            // widest tile that still leaves every SM a few blocks' worth of tile columns;
-            // fall back to what is compiled for this (kind, exact, T, V)
-            const int pref[3] = {d.nx >= 2048 ? 4 : (d.nx >= 512 ? 2 : 1), 4, 1};
-            p->W = 0;
-            for (int w : pref)
-                if (!p->W && tb2d_available(Shape2D{d.kind, d.exact ? 1 : 0, p->T, p->V, w}))
-                    p->W = w;
-            if (!p->W) rc = ST_ERR_UNSUPPORTED;
-        }
-        if (d.force_T && p->T != d.force_T) rc = ST_ERR_UNSUPPORTED;
+        if (p->T == 0 || (d.force_T && p->T != d.force_T)) rc = ST_ERR_UNSUPPORTED;
         PassCfg2D *c = nullptr;
         if (rc == ST_OK) rc = prepare2(p, p->T, &c);
         if (rc == ST_OK) {
@@ -362,9 +354,9 @@ int stencil_plan_create(stencil_plan *out, const stencil_desc *desc)
         if (d.force_by && d.force_by != 64) rc = ST_ERR_UNSUPPORTED;
         p->VY = 8;
         p->NW = 8;
-        int want = d.force_T ? d.force_T : 4;
+        const int want = d.force_T ? d.force_T : 4;
         p->T = kernel_T_for(p, want);
-        if (d.force_T && p->T != d.force_T) rc = ST_ERR_UNSUPPORTED;
+        if (p->T == 0 || (d.force_T && p->T != d.force_T)) rc = ST_ERR_UNSUPPORTED;
         PassCfg3D *c = nullptr;
         if (rc == ST_OK) rc = prepare3(p, p->T, &c);
         p->scratch_bytes = (size_t)cells_of(d) * sizeof(float);

@@ -11,7 +11,11 @@ enum { KDIFF = 0, KTHERM = 1 };
 // ---------------------------------------------------------------------------------------
 // Cell updates (arXiv 1802.00438, Table 2).  EXACT = true evaluates the printed expression
 // left to right with one rounding per operation (the __f*_rn intrinsics are never fused);
-// EXACT = false contracts the same expression into fused multiply-adds.
+// EXACT = false contracts the same expression into fused multiply-adds, ordered so that the
+// term of the neighbour the streaming kernels receive last (s in 2D, a in 3D: the row or
+// plane the previous stage has just produced) enters last.  Everything else of the update
+// is then ready before that neighbour arrives, and a fused stage adds only two dependent
+// operations to the chain between consecutive stages.
 // Neighbours: w = x-1, e = x+1, n = y-1, s = y+1, b = z-1, a = z+1.
 // ---------------------------------------------------------------------------------------
 
@@ -30,8 +34,8 @@ __device__ __forceinline__ float diff5(float c, float w, float e, float s, float
         float r = __fmul_rn(cc, c);
         r = __fmaf_rn(cw, w, r);
         r = __fmaf_rn(ce, e, r);
-        r = __fmaf_rn(cs, s, r);
-        return __fmaf_rn(cn, n, r);
+        r = __fmaf_rn(cn, n, r);
+        return __fmaf_rn(cs, s, r);
     }
 }
 
@@ -77,12 +81,14 @@ __device__ __forceinline__ float hot2(float c, float w, float e, float s, float 
         q = __fadd_rn(q, __fmul_rn(t3, rz));
         return __fadd_rn(c, __fmul_rn(sdc, q));
     } else {
-        float t1 = __fmaf_rn(-2.0f, c, __fadd_rn(n, s));
+        // (n + s - 2c) Ry split as (n - 2c) Ry + s Ry so that s enters last
         float t2 = __fmaf_rn(-2.0f, c, __fadd_rn(e, w));
         float t3 = __fsub_rn(amb, c);
-        float q = __fmaf_rn(t1, ry, p);
-        q = __fmaf_rn(t2, rx, q);
+        float n2 = __fmaf_rn(-2.0f, c, n);
+        float q = __fmaf_rn(t2, rx, p);
         q = __fmaf_rn(t3, rz, q);
+        q = __fmaf_rn(n2, ry, q);
+        q = __fmaf_rn(s, ry, q);
         return __fmaf_rn(sdc, q, c);
     }
 }
@@ -104,15 +110,14 @@ __device__ __forceinline__ float hot3(float c, float w, float e, float s, float 
         r = __fadd_rn(r, __fmul_rn(k[7], p));
         return __fadd_rn(r, ca_amb);
     } else {
-        float r = __fmul_rn(c, k[0]);
+        float r = __fmaf_rn(k[7], p, ca_amb);
+        r = __fmaf_rn(c, k[0], r);
         r = __fmaf_rn(n, k[4], r);
         r = __fmaf_rn(s, k[3], r);
         r = __fmaf_rn(e, k[2], r);
         r = __fmaf_rn(w, k[1], r);
-        r = __fmaf_rn(a, k[6], r);
         r = __fmaf_rn(b, k[5], r);
-        r = __fmaf_rn(k[7], p, r);
-        return __fadd_rn(r, ca_amb);
+        return __fmaf_rn(a, k[6], r);
     }
 }
 

@@ -20,14 +20,26 @@
 //            is copied when the window slides.
 //   x-neighbours of a thread's edge cells come from the adjacent lanes by shuffle; across
 //            warps, lane 0 / lane 31 of every warp publish their edge cell in shared memory
-//            and the neighbour warp reads it one row later (one barrier per row).
-//   Power rows (Hotspot) stay in a ring of T+PF+1 rows so every stage reads the power of the
-//            row it is computing.
+//            and the neighbour warp reads it one row later (one barrier per row).  Lanes with
+//            nothing to publish store to a spare slot, so the store is branch-free.
+//   Power rows (Hotspot) stay in a ring of >= T+PF+1 rows so every stage reads the power of
+//            the row it is computing.
+//   Three variants of the row body: PLAIN (interior warps), EDGE (a warp holding x = 0 or
+//            x = nx-1 clamps its neighbours) and SPECIAL (rows at the top or bottom of the grid,
+//            or a pass that forwards trailing stages); interior rows of interior warps carry
+//            no boundary test at all.
 #pragma once
 #include "common.cuh"
 #include "internal.h"
 
 namespace stn {
+
+constexpr int pow2_at_least(int v)
+{
+    int p = 1;
+    while (p < v) p *= 2;
+    return p;
+}
 
 template <int KIND, bool EXACT, int T, int V, int W>
 struct TB2 {
@@ -35,16 +47,19 @@ struct TB2 {
     static constexpr int BX = 32 * V * W;
     static constexpr int H = (T + 3) / 4 * 4;
     static constexpr int CX = BX - 2 * H;
-    static constexpr int PF = 3;                 // rows requested ahead of the consumer
-    static constexpr int NBF = PF + 3;           // field ring: rows r-1 .. r+1 plus PF ahead
-    static constexpr int NBP = (KIND == KTHERM) ? (T + PF + 1) : 0;
-    static constexpr int NS = T > 1 ? T - 1 : 1; // register-window stages (1..T-1)
-    static constexpr int NX = (W > 1 && T > 1) ? (T - 1) : 0;   // exchanged stage outputs
+    static constexpr int PF = 3;                              // rows requested ahead
+    static constexpr int NBF = pow2_at_least(PF + 3);         // field ring: r-1 .. r+1, PF ahead
+    static constexpr int NBP = (KIND == KTHERM) ? pow2_at_least(T + PF + 1) : 0;
+    static constexpr int NS = T > 1 ? T - 1 : 1;              // register-window stages 1..T-1
+    static constexpr int NX = (W > 1 && T > 1) ? (T - 1) : 0; // exchanged stage outputs
+    static constexpr int XB = (W + 3) * 2;                    // floats per (parity, stage) block
     static constexpr size_t SMEM =
-        sizeof(float) * ((size_t)(NBF + NBP) * BX + (size_t)2 * (NX > 0 ? NX : 1) * (W + 2) * 2);
+        sizeof(float) * ((size_t)(NBF + NBP) * BX + (size_t)2 * (NX > 0 ? NX : 1) * XB);
     static_assert(V % 4 == 0, "V must be a multiple of 4");
     static_assert(CX > 0, "tile narrower than its halos");
 };
+
+enum { MODE_PLAIN = 0, MODE_EDGE = 1, MODE_SPECIAL = 2 };
 
 struct Ctx2 {
     const float *__restrict__ in;
@@ -55,12 +70,14 @@ struct Ctx2 {
     int nx, ny, tsteps;
     int x0, xt;           // tile origin, my first cell
     int y_start, last_row, s0, s1;
-    int lcl, rcl;         // my cell index at x = 0 / x = nx-1, or -1
-    unsigned lmask, rmask;   // the same as bit masks (a per-cell index compare can be turned
-                             // into an indexed store, which would push the row to local memory)
+    unsigned lmask, rmask;   // bit j: my cell j is x = 0 / x = nx-1 (a mask rather than an
+                             // index: a per-cell index compare can be rewritten into an indexed
+                             // store, which would push the row to local memory)
     int st_lo, st_hi;     // my cells [st_lo, st_hi) are stored
+    bool st_full;         // all V cells stored with vector stores
     int xr_off, xw_off;   // exchange read / write offsets of this lane
     bool edge;            // this warp holds x = 0 or x = nx-1
+    bool is0, is31;       // lane 0 / lane 31
     int vec_in, vec_out, vec_pw;
     int tid, lane, wid;
     float k0, k1, k2, k3, k4;
@@ -74,6 +91,13 @@ __device__ __forceinline__ float upd2(const Ctx2 &c, float m, float w, float e, 
         return diff5<EXACT>(m, w, e, s, n, c.k0, c.k1, c.k2, c.k3, c.k4);
     else
         return hot2<EXACT>(m, w, e, s, n, p, c.k0, c.k1, c.k2, c.k3, c.k4);
+}
+
+template <int NT>
+__device__ __forceinline__ void tb2_sync()
+{
+    if (NT == 32) __syncwarp();
+    else __syncthreads();
 }
 
 // Issue the async copy of tile row y (field, and power for Hotspot) into ring slots.
@@ -124,7 +148,7 @@ __device__ __forceinline__ void ld_smem_row(const float *p, float (&v)[V])
 }
 
 // Neighbour values of my V cells of row `m`, given the cells just left and right of them.
-template <int V>
+template <int V, bool EDGE>
 __device__ __forceinline__ void neighbours(const Ctx2 &c, const float (&m)[V], float w_in,
                                            float e_in, float (&wv)[V], float (&ev)[V])
 {
@@ -134,7 +158,7 @@ __device__ __forceinline__ void neighbours(const Ctx2 &c, const float (&m)[V], f
     for (int j = 1; j < V; j++) wv[j] = m[j - 1];
 #pragma unroll
     for (int j = 0; j < V - 1; j++) ev[j] = m[j + 1];
-    if (c.edge) {   // warp-uniform: clamp x-1 at x = 0 and x+1 at x = nx-1 to the cell itself
+    if (EDGE) {   // clamp x-1 at x = 0 and x+1 at x = nx-1 to the cell itself
 #pragma unroll
         for (int j = 0; j < V; j++) {
             wv[j] = ((c.lmask >> j) & 1u) ? m[j] : wv[j];
@@ -147,45 +171,45 @@ template <int V>
 __device__ __forceinline__ void store_row(const Ctx2 &c, int r, const float (&v)[V])
 {
     float *dst = c.out + (long long)r * c.ld_out + c.xt;
+    if (c.st_full) {
 #pragma unroll
-    for (int q = 0; q < V / 4; q++) {
-        if (c.vec_out && 4 * q >= c.st_lo && 4 * q + 4 <= c.st_hi) {
+        for (int q = 0; q < V / 4; q++)
             *reinterpret_cast<float4 *>(dst + 4 * q) =
                 make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        } else {
+    } else {
 #pragma unroll
-            for (int j = 4 * q; j < 4 * q + 4; j++)
-                if (j >= c.st_lo && j < c.st_hi) dst[j] = v[j];
-        }
+        for (int j = 0; j < V; j++)
+            if (j >= c.st_lo && j < c.st_hi) dst[j] = v[j];
     }
 }
 
-template <int KIND, bool EXACT, int T, int V, int W, int P, bool SPECIAL>
+template <int KIND, bool EXACT, int T, int V, int W, int P, int MODE>
 __device__ __forceinline__ void tb2_stages(const Ctx2 &c,
                                            float (&B)[TB2<KIND, EXACT, T, V, W>::NS][3][V], int i,
                                            int R0, float (&out)[V]);
 
-// One row iteration in phase P (= i mod 3).  SPECIAL enables the boundary-row clamps and
-// the forwarding of stages beyond tsteps; ordinary rows skip those tests.
-template <int KIND, bool EXACT, int T, int V, int W, int P, bool SPECIAL>
+// One row iteration in phase P (= i mod 3) and boundary mode MODE.
+template <int KIND, bool EXACT, int T, int V, int W, int P, int MODE>
 __device__ __forceinline__ void tb2_iter(const Ctx2 &c, float (&B)[TB2<KIND, EXACT, T, V, W>::NS][3][V],
                                          int i)
 {
     using C = TB2<KIND, EXACT, T, V, W>;
+    constexpr bool SP = MODE == MODE_SPECIAL;
+    constexpr bool ED = MODE != MODE_PLAIN;
     const int R0 = c.y_start + i;   // row that arrived for this iteration
 
     // ---- stage 0: time 1 at row R0-1 from the time-0 rows in the ring -----------------------
     float out[V];
     {
-        const int R = R0 - 1;
-        int ru = R - 1, rd = R0;
-        if (SPECIAL) {
-            ru = max(ru, 0);
-            rd = min(rd, c.ny - 1);
+        int du = -2, dd = 0;   // rows R-1 and R+1 relative to R0
+        if (SP) {
+            const int R = R0 - 1;
+            du = max(R - 1, 0) - R0;
+            dd = min(R0, c.ny - 1) - R0;
         }
-        const float *fu = c.ringF + ((ru - c.y_start + 2 * C::NBF) % C::NBF) * C::BX;
-        const float *fm = c.ringF + ((R - c.y_start + 2 * C::NBF) % C::NBF) * C::BX;
-        const float *fd = c.ringF + ((rd - c.y_start + 2 * C::NBF) % C::NBF) * C::BX;
+        const float *fu = c.ringF + ((i + du) & (C::NBF - 1)) * C::BX;
+        const float *fm = c.ringF + ((i - 1) & (C::NBF - 1)) * C::BX;
+        const float *fd = c.ringF + ((i + dd) & (C::NBF - 1)) * C::BX;
         const int o = c.tid * V;
         float u[V], m[V], d[V], wv[V], ev[V];
         ld_smem_row<V>(fu + o, u);
@@ -193,12 +217,9 @@ __device__ __forceinline__ void tb2_iter(const Ctx2 &c, float (&B)[TB2<KIND, EXA
         ld_smem_row<V>(fd + o, d);
         const float w_in = fm[o > 0 ? o - 1 : 0];
         const float e_in = fm[o + V < C::BX ? o + V : C::BX - 1];
-        neighbours<V>(c, m, w_in, e_in, wv, ev);
+        neighbours<V, ED>(c, m, w_in, e_in, wv, ev);
         float pv[V];
-        if (KIND == KTHERM) {
-            const float *pr = c.ringP + ((R - c.y_start + 2 * C::NBP) % C::NBP) * C::BX;
-            ld_smem_row<V>(pr + o, pv);
-        }
+        if (KIND == KTHERM) ld_smem_row<V>(c.ringP + ((i - 1) & (C::NBP - 1)) * C::BX + o, pv);
 #pragma unroll
         for (int j = 0; j < V; j++)
             out[j] = upd2<KIND, EXACT>(c, m[j], wv[j], ev[j], d[j], u[j],
@@ -209,61 +230,63 @@ __device__ __forceinline__ void tb2_iter(const Ctx2 &c, float (&B)[TB2<KIND, EXA
         if (R >= c.s0 && R < c.s1) store_row<V>(c, R, out);
         return;
     } else {
-        tb2_stages<KIND, EXACT, T, V, W, P, SPECIAL>(c, B, i, R0, out);
+        tb2_stages<KIND, EXACT, T, V, W, P, MODE>(c, B, i, R0, out);
     }
 }
 
 // Stages 1 .. T-1 of one row iteration (T > 1).
-template <int KIND, bool EXACT, int T, int V, int W, int P, bool SPECIAL>
+template <int KIND, bool EXACT, int T, int V, int W, int P, int MODE>
 __device__ __forceinline__ void tb2_stages(const Ctx2 &c,
                                            float (&B)[TB2<KIND, EXACT, T, V, W>::NS][3][V], int i,
                                            int R0, float (&out)[V])
 {
     using C = TB2<KIND, EXACT, T, V, W>;
+    constexpr bool SP = MODE == MODE_SPECIAL;
+    constexpr bool ED = MODE != MODE_PLAIN;
     constexpr int PU = P, PM = (P + 1) % 3, PD = (P + 2) % 3;
+    // exchange blocks: this row's outputs go to parity i&1, the rows read now came from (i-1)&1
+    float *xw = c.xch + (i & 1) * (C::NX > 0 ? C::NX : 1) * C::XB + c.xw_off;
+    const float *xr = c.xch + ((i - 1) & 1) * (C::NX > 0 ? C::NX : 1) * C::XB + c.xr_off;
+    const float *pbase = c.ringP + c.tid * V;
+
     // hand stage 0's row to stage 1
 #pragma unroll
     for (int j = 0; j < V; j++) B[0][PD][j] = out[j];
-    if (C::NX > 0 && (c.lane == 0 || c.lane == 31))
-        c.xch[(((i & 1) * C::NX + 0) * (W + 2)) * 2 + c.xw_off] = c.lane == 0 ? out[0] : out[V - 1];
+    if (C::NX > 0) xw[0] = c.is0 ? out[0] : out[V - 1];
 
-    // ---- stages 1 .. T-1 -----------------------------------------------------------------
 #pragma unroll
     for (int s = 1; s < T; s++) {
         const int R = R0 - 1 - s;   // row this stage produces (time s+1)
         float(&Ws)[3][V] = B[s - 1];
-        if (SPECIAL && s >= c.tsteps) {
+        if (SP && s >= c.tsteps) {
             // beyond this pass's step count: forward the time-s row unchanged
 #pragma unroll
             for (int j = 0; j < V; j++) out[j] = Ws[PM][j];
         } else {
-            if (SPECIAL && R == c.ny - 1) {   // bottom edge: row ny is row ny-1
+            if (SP && R == c.ny - 1) {   // bottom edge: row ny is row ny-1
 #pragma unroll
                 for (int j = 0; j < V; j++) Ws[PD][j] = Ws[PM][j];
             }
             float w_in, e_in;
             {
-                float X = 0.f;
-                if (C::NX > 0)
-                    X = c.xch[((((i - 1) & 1) * C::NX + (s - 1)) * (W + 2)) * 2 + c.xr_off];
-                const float vw = (C::NX > 0 && c.lane == 31) ? X : Ws[PM][V - 1];
-                const float ve = (C::NX > 0 && c.lane == 0) ? X : Ws[PM][0];
+                float vw = Ws[PM][V - 1], ve = Ws[PM][0];
+                if (C::NX > 0) {
+                    const float X = xr[(s - 1) * C::XB];
+                    vw = c.is31 ? X : vw;
+                    ve = c.is0 ? X : ve;
+                }
                 w_in = __shfl_sync(0xffffffffu, vw, (c.lane + 31) & 31);
                 e_in = __shfl_sync(0xffffffffu, ve, (c.lane + 1) & 31);
             }
             float wv[V], ev[V];
-            neighbours<V>(c, Ws[PM], w_in, e_in, wv, ev);
+            neighbours<V, ED>(c, Ws[PM], w_in, e_in, wv, ev);
             float pv[V];
-            if (KIND == KTHERM) {
-                const float *pr =
-                    c.ringP + ((R - c.y_start + 2 * C::NBP) % C::NBP) * C::BX + c.tid * V;
-                ld_smem_row<V>(pr, pv);
-            }
+            if (KIND == KTHERM) ld_smem_row<V>(pbase + ((i - 1 - s) & (C::NBP - 1)) * C::BX, pv);
 #pragma unroll
             for (int j = 0; j < V; j++)
                 out[j] = upd2<KIND, EXACT>(c, Ws[PM][j], wv[j], ev[j], Ws[PD][j], Ws[PU][j],
                                            KIND == KTHERM ? pv[j] : 0.f);
-            if (SPECIAL && R == -1) {   // top edge: the next window's row -1 is row 0
+            if (SP && R == -1) {   // top edge: the next window's row -1 is row 0
 #pragma unroll
                 for (int j = 0; j < V; j++) Ws[PM][j] = Ws[PD][j];
             }
@@ -271,9 +294,7 @@ __device__ __forceinline__ void tb2_stages(const Ctx2 &c,
         if (s < T - 1) {
 #pragma unroll
             for (int j = 0; j < V; j++) B[s][PD][j] = out[j];
-            if (C::NX > 0 && (!SPECIAL || s + 1 < c.tsteps) && (c.lane == 0 || c.lane == 31))
-                c.xch[(((i & 1) * C::NX + s) * (W + 2)) * 2 + c.xw_off] =
-                    c.lane == 0 ? out[0] : out[V - 1];
+            if (C::NX > 0) xw[s * C::XB] = c.is0 ? out[0] : out[V - 1];
         } else {
             if (R >= c.s0 && R < c.s1) store_row<V>(c, R, out);
         }
@@ -304,10 +325,14 @@ __global__ void __launch_bounds__(32 * W) k_tb2d(const Pass2D p)
     c.tid = threadIdx.x;
     c.lane = threadIdx.x & 31;
     c.wid = threadIdx.x >> 5;
+    c.is0 = c.lane == 0;
+    c.is31 = c.lane == 31;
     c.k0 = p.k[0]; c.k1 = p.k[1]; c.k2 = p.k[2]; c.k3 = p.k[3]; c.k4 = p.k[4];
-    // lane 31 reads the left warp's right edge, lane 0 the right warp's left edge
-    c.xr_off = (c.lane == 31) ? (c.wid * 2 + 1) : ((c.wid + 2) * 2 + 0);
-    c.xw_off = (c.wid + 1) * 2 + (c.lane == 31 ? 1 : 0);
+    // exchange slots: 2*(w+1) = left edge of warp w, 2*(w+1)+1 = its right edge; slot 2*(W+2)
+    // is the spare one that lanes 1..30 write.  Lane 31 reads the left warp's right edge,
+    // lane 0 (and, harmlessly, every other lane) the right warp's left edge.
+    c.xr_off = c.is31 ? (c.wid * 2 + 1) : ((c.wid + 2) * 2 + 0);
+    c.xw_off = c.is0 ? (c.wid + 1) * 2 : (c.is31 ? (c.wid + 1) * 2 + 1 : (W + 2) * 2);
 
     float B[C::NS][3][V];
 #pragma unroll
@@ -331,15 +356,18 @@ __global__ void __launch_bounds__(32 * W) k_tb2d(const Pass2D p)
         c.xt = c.x0 + c.tid * V;
         c.y_start = max(0, s0 - c.tsteps);
         c.last_row = min(c.ny - 1, s1 - 1 + c.tsteps);
-        c.lcl = (c.xt <= 0 && 0 < c.xt + V) ? -c.xt : -1;
-        c.rcl = (c.xt <= c.nx - 1 && c.nx - 1 < c.xt + V) ? (c.nx - 1 - c.xt) : -1;
-        c.lmask = c.lcl >= 0 ? (1u << c.lcl) : 0u;
-        c.rmask = c.rcl >= 0 ? (1u << c.rcl) : 0u;
-        c.edge = __any_sync(0xffffffffu, c.lcl >= 0 || c.rcl >= 0);
+        {
+            const int lcl = (c.xt <= 0 && 0 < c.xt + V) ? -c.xt : -1;
+            const int rcl = (c.xt <= c.nx - 1 && c.nx - 1 < c.xt + V) ? (c.nx - 1 - c.xt) : -1;
+            c.lmask = lcl >= 0 ? (1u << lcl) : 0u;
+            c.rmask = rcl >= 0 ? (1u << rcl) : 0u;
+            c.edge = __any_sync(0xffffffffu, lcl >= 0 || rcl >= 0);
+        }
         {
             const int lo = max(c.x0 + C::H, 0), hi = min(c.x0 + C::H + C::CX, c.nx);
             c.st_lo = min(max(lo - c.xt, 0), V);
             c.st_hi = min(max(hi - c.xt, 0), V);
+            c.st_full = c.vec_out && c.st_lo == 0 && c.st_hi == V;
         }
         const int n_it = s1 + T - c.y_start;   // stage T-1 emits row s1-1 at i = n_it-1
         const int bot_i = c.ny - c.y_start;    // from here on a stage may sit on row ny-1
@@ -350,8 +378,8 @@ __global__ void __launch_bounds__(32 * W) k_tb2d(const Pass2D p)
         for (int j = 0; j < C::PF; j++) {
             const int y = c.y_start + j;
             if (y <= c.last_row)
-                tb2_load_row<KIND, C::BX, C::NT>(c, y, c.ringF + (j % C::NBF) * C::BX,
-                                                 c.ringP + (j % (C::NBP > 0 ? C::NBP : 1)) * C::BX);
+                tb2_load_row<KIND, C::BX, C::NT>(c, y, c.ringF + (j & (C::NBF - 1)) * C::BX,
+                                                 c.ringP + (j & (C::NBP > 0 ? C::NBP - 1 : 0)) * C::BX);
             cp_async_commit();
         }
 
@@ -359,17 +387,19 @@ __global__ void __launch_bounds__(32 * W) k_tb2d(const Pass2D p)
 #define STN_TB2_STEP(PH)                                                                       \
     if (i < n_it) {                                                                            \
         cp_async_wait<C::PF - 1>();                                                            \
-        __syncthreads();                                                                       \
+        tb2_sync<C::NT>();                                                                     \
         if (partial || (top && i <= T) || i >= bot_i)                                          \
-            tb2_iter<KIND, EXACT, T, V, W, PH, true>(c, B, i);                                 \
+            tb2_iter<KIND, EXACT, T, V, W, PH, MODE_SPECIAL>(c, B, i);                         \
+        else if (c.edge)                                                                       \
+            tb2_iter<KIND, EXACT, T, V, W, PH, MODE_EDGE>(c, B, i);                            \
         else                                                                                   \
-            tb2_iter<KIND, EXACT, T, V, W, PH, false>(c, B, i);                                \
+            tb2_iter<KIND, EXACT, T, V, W, PH, MODE_PLAIN>(c, B, i);                           \
         {                                                                                      \
             const int y = c.y_start + i + C::PF;                                               \
             if (y <= c.last_row)                                                               \
                 tb2_load_row<KIND, C::BX, C::NT>(                                              \
-                    c, y, c.ringF + ((i + C::PF) % C::NBF) * C::BX,                            \
-                    c.ringP + ((i + C::PF) % (C::NBP > 0 ? C::NBP : 1)) * C::BX);              \
+                    c, y, c.ringF + ((i + C::PF) & (C::NBF - 1)) * C::BX,                      \
+                    c.ringP + ((i + C::PF) & (C::NBP > 0 ? C::NBP - 1 : 0)) * C::BX);          \
             cp_async_commit();                                                                 \
         }                                                                                      \
         ++i;                                                                                   \
@@ -382,7 +412,7 @@ __global__ void __launch_bounds__(32 * W) k_tb2d(const Pass2D p)
         }
 #undef STN_TB2_STEP
         cp_async_wait<0>();
-        __syncthreads();
+        tb2_sync<C::NT>();
     }
 }
 

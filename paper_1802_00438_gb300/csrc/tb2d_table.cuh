@@ -1,6 +1,7 @@
 // Registry of the compiled 2D kernel instances.
 #pragma once
 #include "tb2d_kernel.cuh"
+#include "tb2f_kernel.cuh"
 
 namespace stn {
 
@@ -13,6 +14,10 @@ struct Tb2dEntry {
 #define STN_TB2_ENTRY(K, E, T_, V_, W_)                                                      \
     { K, E, T_, V_, W_, reinterpret_cast<const void *>(&k_tb2d<K, (E != 0), T_, V_, W_>),  \
       TB2<K, (E != 0), T_, V_, W_>::SMEM }
+
+// contracted path: one-warp blocks (W = 1), partial-sum stages
+#define STN_TB2F_ENTRY(K, T_, V_)                                                            \
+    { K, 0, T_, V_, 1, reinterpret_cast<const void *>(&k_tb2f<K, T_, V_>), TB2F<K, T_, V_>::SMEM }
 
 extern const Tb2dEntry tb2d_table_diff[];
 extern const int tb2d_table_diff_n;

@@ -1,20 +1,18 @@
 // Compiled instances of the 2D temporally-blocked sweep, Hotspot 2D.
-// Contracted (exact = 0): T in {1,2,4,8,12} with (V,W) in {(4,1),(4,2),(4,4)}, plus V = 8
-// (one warp per block) for T <= 8; larger T or V would not fit the register file.
-// Exact (Table 2 order, no fused multiply-add): T in {1,2,4,8} with (V,W) in {(4,1),(4,4)}.
+// Exact (Table 2 order, rotating register windows): T in {1,2,4,8}, V = 4, W in {1,4}.
+// Contracted (partial-sum stages, one warp per block): V = 8 for T in {1,2,4,6,8}, V = 4 for
+// T in {4,8,12}; larger T or V do not fit the register file.
 #include "tb2d_table.cuh"
 
 namespace stn {
 
-#define STN_FAST(T_) STN_TB2_ENTRY(1, 0, T_, 4, 1), STN_TB2_ENTRY(1, 0, T_, 4, 2), \
-                     STN_TB2_ENTRY(1, 0, T_, 4, 4)
-#define STN_FAST8(T_) STN_TB2_ENTRY(1, 0, T_, 8, 1)
 #define STN_EXACT(T_) STN_TB2_ENTRY(1, 1, T_, 4, 1), STN_TB2_ENTRY(1, 1, T_, 4, 4)
 
 const Tb2dEntry tb2d_table_therm[] = {
-    STN_FAST(1), STN_FAST(2), STN_FAST(4), STN_FAST(8), STN_FAST(12),
-    STN_FAST8(1), STN_FAST8(2), STN_FAST8(4), STN_FAST8(8),
     STN_EXACT(1), STN_EXACT(2), STN_EXACT(4), STN_EXACT(8),
+    STN_TB2F_ENTRY(1, 1, 8), STN_TB2F_ENTRY(1, 2, 8), STN_TB2F_ENTRY(1, 4, 8),
+    STN_TB2F_ENTRY(1, 8, 8), STN_TB2F_ENTRY(1, 6, 8),
+    STN_TB2F_ENTRY(1, 4, 4), STN_TB2F_ENTRY(1, 8, 4), STN_TB2F_ENTRY(1, 12, 4),
 };
 const int tb2d_table_therm_n = sizeof(tb2d_table_therm) / sizeof(tb2d_table_therm[0]);
 

@@ -1,0 +1,539 @@
+// 2D temporally-blocked Jacobi sweep, contracted arithmetic (fused multiply-adds): one pass
+// advances the grid by `tsteps` (<= T) steps.
+//
+// Same blocking as the exact kernel (tb2d_kernel.cuh; arXiv 1802.00438 Sec. 3.1-3.2, Eq. 2):
+// an overlapped x-tile streamed along y through a chain of T stages, stage s computing time
+// step s+1 one row behind stage s-1, halos computed redundantly, only the compute block stored,
+// trailing stages forwarding when the pass fuses fewer than T steps, clamped boundary
+// (Sec. 5.1) at every stage.
+//
+// What differs is how a stage holds its window.  When row y of time s reaches stage s it
+// completes row y-1 and starts rows y and y+1:
+//   out(y-1) = P + cs * d                      (the only operation on the stage-to-stage path)
+//   P'       = Q + cc * d + cw * d_w + ce * d_e  (row y, missing only its south term)
+//   Q'       = cn * d                           (row y+1's north term)
+// Hotspot 2D uses the same split of c + sdc*(p + (n+s-2c)*Ry + (e+w-2c)*Rx + (amb-c)*Rz):
+//   out(y-1) = P + (sdc*Ry) * d
+//   P'       = d + sdc * (Q + (d_e+d_w-2d)*Rx + (amb-d)*Rz - 2Ry*d)
+//   Q'       = Ry * d + p(y+1)
+// P' accumulates on top of Q and Q' is written where P was, so the two partial rows trade
+// places every row: the row loop is unrolled twice with the roles swapped and every update is
+// in place (no register copies).  Counted work per cell is unchanged (Table 2: 9 and 15 flops,
+// issued as 5 and 9 operations).
+//
+// GPU mapping: one warp per block; a tile is BX = 32*V cells wide incl. halos of
+// H = roundup(T, 4) cells per side; thread = V consecutive cells; x-neighbours of a thread's
+// edge cells by shuffle (the warp edge is the tile edge, inside the halo).  Field and power
+// rows arrive through shared-memory rings filled by cp.async PF rows ahead.  The power ring
+// keeps a mirrored copy of its first PW-1 slots, so the PW = max(T, 2) power rows an
+// iteration reads are
+// consecutive slots: one base address per row, constant offsets per stage.  Stage 0 needs no
+// partial rows: its three time-0 rows are all in the field ring, and it evaluates the update
+// from them directly.
+#pragma once
+#include "tb2d_kernel.cuh"
+
+namespace stn {
+
+template <int KIND, int T, int V>
+struct TB2F {
+    static constexpr int BX = 32 * V;
+    static constexpr int H = (T + 3) / 4 * 4;
+    static constexpr int CX = BX - 2 * H;
+    static constexpr int PF = 4;                                    // rows requested ahead
+    static constexpr int NBF = PF + 3;                              // field rows i-2 .. i+PF
+    static constexpr int PW = T > 1 ? T : 2;                        // power rows read per row:
+                                                                    // i-PW+1 .. i
+    static constexpr int NBP = (KIND == KTHERM) ? (PW + PF + 1) : 0; // power ring rows
+    static constexpr int NBPX = (KIND == KTHERM) ? (NBP + PW - 1) : 0;  // incl. mirror
+    static constexpr int NS = T > 1 ? T - 1 : 1;                    // partial-sum stages
+    static constexpr int ROWB = BX * 4;                             // bytes per ring row
+    static constexpr size_t SMEM = (size_t)(NBF + NBPX) * ROWB;
+    static_assert(V % 4 == 0, "V must be a multiple of 4");
+    static_assert(CX > 0, "tile narrower than its halos");
+};
+
+struct CoefF {
+    // diffusion: cc, cw, ce, cs, cn; Hotspot: sdc, Rx, Ry, Rz, amb, sdc*Ry, -2*Ry
+    float a0, a1, a2, a3, a4, a5, a6;
+};
+
+__device__ __forceinline__ float4 lds128(uint32_t a)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ float lds32(uint32_t a)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];\n" : "=f"(v) : "r"(a));
+    return v;
+}
+
+template <int V>
+__device__ __forceinline__ void lds_row(uint32_t a, float (&v)[V])
+{
+#pragma unroll
+    for (int q = 0; q < V / 4; q++) {
+        const float4 t = lds128(a + 16 * q);
+        v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+    }
+}
+
+__device__ __forceinline__ void cp16(uint32_t dst, const void *src, int nbytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(nbytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp4(uint32_t dst, const void *src, int nbytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(nbytes)
+                 : "memory");
+}
+
+struct CtxF {
+    const float *__restrict__ in;
+    float *__restrict__ out;
+    const float *__restrict__ pw;
+    long long ld_in, ld_out, ld_pw;
+    uint32_t sF, sP;       // shared byte addresses of the field and power rings
+    int nx, ny, tsteps;
+    int x0, xt;
+    int y_start, last_row, s0, s1;
+    unsigned lmask, rmask;
+    int st_lo, st_hi;
+    bool st_full, st_any, edge;
+    int vec_in, vec_out, vec_pw;
+    int lane;
+    uint32_t o4;           // my first cell's byte offset in a ring row
+    uint32_t ow4, oe4;     // byte offsets of the cells left and right of mine (clamped)
+};
+
+// Issue the async copies of tile row y into field slot fs and power slots ps (and ps2 >= 0:
+// the mirror slot).
+template <int KIND, int V>
+__device__ __forceinline__ void tbf_load(const CtxF &c, int y, int fs, int ps, int ps2)
+{
+    constexpr int BX = 32 * V, ROWB = BX * 4;
+    const float *srcF = c.in + (long long)y * c.ld_in;
+    const float *srcP = (KIND == KTHERM) ? c.pw + (long long)y * c.ld_pw : nullptr;
+#pragma unroll
+    for (int qq = 0; qq < V / 4; qq++) {
+        const int q = c.lane + qq * 32;
+        const int x = c.x0 + 4 * q;
+        const uint32_t off = 16u * q;
+        const int nb16 = (x >= 0 && x < c.nx) ? min(16, 4 * (c.nx - x)) : 0;
+        if (c.vec_in) {
+            cp16(c.sF + fs * ROWB + off, nb16 ? srcF + x : srcF, nb16);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int xx = x + j;
+                const int nb = (xx >= 0 && xx < c.nx) ? 4 : 0;
+                cp4(c.sF + fs * ROWB + off + 4 * j, nb ? srcF + xx : srcF, nb);
+            }
+        }
+        if (KIND == KTHERM) {
+            if (c.vec_pw) {
+                cp16(c.sP + ps * ROWB + off, nb16 ? srcP + x : srcP, nb16);
+                if (ps2 >= 0) cp16(c.sP + ps2 * ROWB + off, nb16 ? srcP + x : srcP, nb16);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const int xx = x + j;
+                    const int nb = (xx >= 0 && xx < c.nx) ? 4 : 0;
+                    cp4(c.sP + ps * ROWB + off + 4 * j, nb ? srcP + xx : srcP, nb);
+                    if (ps2 >= 0) cp4(c.sP + ps2 * ROWB + off + 4 * j, nb ? srcP + xx : srcP, nb);
+                }
+            }
+        }
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void tbf_store(const CtxF &c, int r, const float (&v)[V])
+{
+    float *dst = c.out + (long long)r * c.ld_out + c.xt;
+    if (c.st_full) {
+#pragma unroll
+        for (int q = 0; q < V / 4; q++)
+            *reinterpret_cast<float4 *>(dst + 4 * q) =
+                make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else if (c.st_any) {
+#pragma unroll
+        for (int j = 0; j < V; j++)
+            if (j >= c.st_lo && j < c.st_hi) dst[j] = v[j];
+    }
+}
+
+template <int V, bool EDGE>
+__device__ __forceinline__ void nbf(const CtxF &c, const float (&d)[V], float w_in, float e_in,
+                                    float (&dw)[V], float (&de)[V])
+{
+    dw[0] = w_in;
+    de[V - 1] = e_in;
+#pragma unroll
+    for (int j = 1; j < V; j++) dw[j] = d[j - 1];
+#pragma unroll
+    for (int j = 0; j < V - 1; j++) de[j] = d[j + 1];
+    if (EDGE) {
+#pragma unroll
+        for (int j = 0; j < V; j++) {
+            dw[j] = ((c.lmask >> j) & 1u) ? d[j] : dw[j];
+            de[j] = ((c.rmask >> j) & 1u) ? d[j] : de[j];
+        }
+    }
+}
+
+// Start row y+1: Xq = its north term (+ its power for Hotspot), written over the finished P.
+template <int KIND, int V>
+__device__ __forceinline__ void qf(const CoefF &k, const float (&d)[V], uint32_t p_next,
+                                   float (&Xq)[V])
+{
+    if (KIND == KDIFF) {
+#pragma unroll
+        for (int j = 0; j < V; j++) Xq[j] = __fmul_rn(k.a4, d[j]);
+    } else {
+        float p[V];
+        lds_row<V>(p_next, p);
+#pragma unroll
+        for (int j = 0; j < V; j++) Xq[j] = __fmaf_rn(k.a2, d[j], p[j]);
+    }
+}
+
+// One stage on the arrival of row y (values d, time s).  Xp holds P (row y-1, all but its
+// south term), Xq holds Q (row y's north term).  Emits out = row y-1 at time s+1, leaves
+// row y's P in Xq and row y+1's Q in Xp.
+template <int KIND, int V, int MODE>
+__device__ __forceinline__ void stf(const CtxF &c, const CoefF &k, int y, bool fwd, float (&Xp)[V],
+                                    float (&Xq)[V], const float (&d)[V], float w_in, float e_in,
+                                    uint32_t p_y, uint32_t p_next, float (&out)[V])
+{
+    constexpr bool SP = MODE == MODE_SPECIAL;
+    constexpr bool ED = MODE != MODE_PLAIN;
+    if (SP && fwd) {   // beyond this pass's step count: row y-1 of time s passes unchanged
+#pragma unroll
+        for (int j = 0; j < V; j++) {
+            out[j] = Xp[j];
+            Xq[j] = d[j];   // becomes "P" of the next row: forwarded one row later
+        }
+        return;
+    }
+    const float cs = (KIND == KDIFF) ? k.a3 : k.a5;
+#pragma unroll
+    for (int j = 0; j < V; j++) out[j] = __fmaf_rn(cs, d[j], Xp[j]);
+    if (SP && y == c.ny) {   // row ny-1 was completed on arrival (its south is itself)
+#pragma unroll
+        for (int j = 0; j < V; j++) out[j] = Xp[j];
+    }
+    if (SP && y == 0) qf<KIND, V>(k, d, p_y, Xq);   // top: the row above row 0 is row 0
+    float dw[V], de[V];
+    nbf<V, ED>(c, d, w_in, e_in, dw, de);
+    if (KIND == KDIFF) {
+#pragma unroll
+        for (int j = 0; j < V; j++) {
+            Xq[j] = __fmaf_rn(k.a0, d[j], Xq[j]);
+            Xq[j] = __fmaf_rn(k.a1, dw[j], Xq[j]);
+            Xq[j] = __fmaf_rn(k.a2, de[j], Xq[j]);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < V; j++) {
+            const float t2 = __fmaf_rn(-2.0f, d[j], __fadd_rn(de[j], dw[j]));
+            const float t3 = __fsub_rn(k.a4, d[j]);
+            Xq[j] = __fmaf_rn(t2, k.a1, Xq[j]);
+            Xq[j] = __fmaf_rn(t3, k.a3, Xq[j]);
+            Xq[j] = __fmaf_rn(k.a6, d[j], Xq[j]);
+            Xq[j] = __fmaf_rn(k.a0, Xq[j], d[j]);
+        }
+    }
+    qf<KIND, V>(k, d, p_next, Xp);
+    if (SP && y == c.ny - 1) {   // bottom: complete row ny-1 now with south = itself
+#pragma unroll
+        for (int j = 0; j < V; j++) Xq[j] = __fmaf_rn(cs, d[j], Xq[j]);
+    }
+}
+
+// Per-thread, per-segment state of the row loop.
+struct RowF {
+    const float *gF, *gP;   // field / power pointers at column x0 + 4*lane of the next row to load
+    float *gO;              // output pointer at my first cell of the next row to store
+    int colq[4];            // per 16-byte chunk: column offset to copy from (0 when off-grid)
+    int nbq[4];             // per chunk: bytes inside the grid (0..16)
+    int rf, rp;             // ring slots of field row i / of power row i
+    int i_store;            // first iteration that stores a row
+    int i_load_end;         // iterations i < i_load_end queue row i+PF
+};
+
+// One row iteration.  PH selects which of A/B holds P (PH = 0: A) for every stage.
+template <int KIND, int T, int V, int MODE, int PH>
+__device__ __forceinline__ void tbf_iter(const CtxF &c, const CoefF &k,
+                                         float (&A)[TB2F<KIND, T, V>::NS][V],
+                                         float (&B)[TB2F<KIND, T, V>::NS][V], int i,
+                                         uint32_t fu, uint32_t fm, uint32_t fd, uint32_t pbase,
+                                         float *gO, bool store)
+{
+    using C = TB2F<KIND, T, V>;
+    constexpr bool ED = MODE != MODE_PLAIN;
+    const int R0 = c.y_start + i;
+    float d[V], out[V];
+    // stage 0: row R0-1 at time 1 straight from the time-0 rows R0-2, R0-1, R0 in the ring
+    // (fu, fm, fd are those rows, already clamped to the grid for the boundary rows)
+    {
+        float u[V], m[V], dd[V], w[V], e[V];
+        lds_row<V>(fu + c.o4, u);
+        lds_row<V>(fm + c.o4, m);
+        lds_row<V>(fd + c.o4, dd);
+        nbf<V, ED>(c, m, lds32(fm + c.ow4), lds32(fm + c.oe4), w, e);
+        if (KIND == KDIFF) {
+#pragma unroll
+            for (int j = 0; j < V; j++)
+                out[j] = diff5<false>(m[j], w[j], e[j], dd[j], u[j], k.a0, k.a1, k.a2, k.a3, k.a4);
+        } else {
+            float pv[V];
+            lds_row<V>(pbase - C::ROWB + c.o4, pv);   // power of row R0-1
+#pragma unroll
+            for (int j = 0; j < V; j++)
+                out[j] = hot2<false>(m[j], w[j], e[j], dd[j], u[j], pv[j], k.a0, k.a1, k.a2, k.a3,
+                                     k.a4);
+        }
+    }
+    // stages 1 .. T-1: stage s receives row R0-s of time s; pbase is the slot of power row
+    // R0 (ring-relative i), row i-t sits t slots below it
+#pragma unroll
+    for (int s = 1; s < T; s++) {
+#pragma unroll
+        for (int j = 0; j < V; j++) d[j] = out[j];
+        const float w_in = __shfl_sync(0xffffffffu, d[V - 1], (c.lane + 31) & 31);
+        const float e_in = __shfl_sync(0xffffffffu, d[0], (c.lane + 1) & 31);
+        stf<KIND, V, MODE>(c, k, R0 - s, s >= c.tsteps, PH == 0 ? A[s - 1] : B[s - 1],
+                           PH == 0 ? B[s - 1] : A[s - 1], d, w_in, e_in,
+                           pbase - s * C::ROWB + c.o4, pbase - (s - 1) * C::ROWB + c.o4, out);
+    }
+    if (store) {
+        if (c.st_full) {
+#pragma unroll
+            for (int q = 0; q < V / 4; q++)
+                *reinterpret_cast<float4 *>(gO + 4 * q) =
+                    make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
+        } else if (c.st_any) {
+#pragma unroll
+            for (int j = 0; j < V; j++)
+                if (j >= c.st_lo && j < c.st_hi) gO[j] = out[j];
+        }
+    }
+}
+
+// Queue tile row (row pointers in r) into field slot lf and power slot lp (plus its mirror).
+template <int KIND, int T, int V>
+__device__ __forceinline__ void tbf_queue(const CtxF &c, const RowF &r, int lf, int lp)
+{
+    using C = TB2F<KIND, T, V>;
+    const uint32_t df = c.sF + lf * C::ROWB + 16u * c.lane;
+    const uint32_t dp = c.sP + lp * C::ROWB + 16u * c.lane;
+    if (c.vec_in && (KIND == KDIFF || c.vec_pw)) {
+#pragma unroll
+        for (int q = 0; q < V / 4; q++) {
+            cp16(df + 512u * q, r.gF + r.colq[q], r.nbq[q]);
+            if (KIND == KTHERM) {
+                cp16(dp + 512u * q, r.gP + r.colq[q], r.nbq[q]);
+                if (lp < C::PW - 1) cp16(dp + C::NBP * C::ROWB + 512u * q, r.gP + r.colq[q], r.nbq[q]);
+            }
+        }
+    } else {   // rows not 16-byte aligned: element-wise copies
+#pragma unroll
+        for (int q = 0; q < V / 4; q++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int nb = (4 * j < r.nbq[q]) ? 4 : 0;
+                const int col = nb ? r.colq[q] + j : 0;
+                cp4(df + 512u * q + 4 * j, r.gF + col, nb);
+                if (KIND == KTHERM) {
+                    cp4(dp + 512u * q + 4 * j, r.gP + col, nb);
+                    if (lp < C::PW - 1) cp4(dp + C::NBP * C::ROWB + 512u * q + 4 * j, r.gP + col, nb);
+                }
+            }
+    }
+}
+
+// One row: wait for row i, run the stages, queue row i+PF, advance pointers and rings.
+template <int KIND, int T, int V, int MODE, int PH>
+__device__ __forceinline__ void tbf_step(const CtxF &c, const CoefF &k,
+                                         float (&A)[TB2F<KIND, T, V>::NS][V],
+                                         float (&B)[TB2F<KIND, T, V>::NS][V], int i, RowF &r)
+{
+    using C = TB2F<KIND, T, V>;
+    cp_async_wait<C::PF - 1>();   // row i has landed
+    __syncwarp();
+    // field ring slots of rows i-2, i-1, i (rows above or below the grid clamp to its edge)
+    int su = r.rf - 2, sm = r.rf - 1, sd = r.rf;
+    su += (su < 0) ? C::NBF : 0;
+    sm += (sm < 0) ? C::NBF : 0;
+    if (MODE == MODE_SPECIAL) {
+        const int R = c.y_start + i - 1;    // stage 0's row
+        if (R == 0) su = sm;                // row -1 is row 0
+        if (R == c.ny - 1) sd = sm;         // row ny is row ny-1
+    }
+    const uint32_t pbase = c.sP + ((KIND == KTHERM && r.rp < C::PW - 1) ? C::NBP + r.rp : r.rp) * C::ROWB;
+    const bool store = i >= r.i_store;
+    tbf_iter<KIND, T, V, MODE, PH>(c, k, A, B, i, c.sF + su * C::ROWB, c.sF + sm * C::ROWB,
+                                   c.sF + sd * C::ROWB, pbase, r.gO, store);
+    if (store) r.gO += c.ld_out;
+    __syncwarp();
+    int lf = r.rf + C::PF;
+    lf -= (lf >= C::NBF) ? C::NBF : 0;
+    int lp = 0;
+    if (KIND == KTHERM) {
+        lp = r.rp + C::PF;
+        lp -= (lp >= C::NBP) ? C::NBP : 0;
+    }
+    if (i < r.i_load_end) {
+        tbf_queue<KIND, T, V>(c, r, lf, lp);
+        r.gF += c.ld_in;
+        if (KIND == KTHERM) r.gP += c.ld_pw;
+    }
+    cp_async_commit();
+    r.rf = (r.rf + 1 == C::NBF) ? 0 : r.rf + 1;
+    if (KIND == KTHERM) r.rp = (r.rp + 1 == C::NBP) ? 0 : r.rp + 1;
+}
+
+template <int KIND, int T, int V, int MODE>
+__device__ __forceinline__ void tbf_step_rt(const CtxF &c, const CoefF &k,
+                                            float (&A)[TB2F<KIND, T, V>::NS][V],
+                                            float (&B)[TB2F<KIND, T, V>::NS][V], int i, RowF &r)
+{
+    if (i & 1) tbf_step<KIND, T, V, MODE, 1>(c, k, A, B, i, r);
+    else tbf_step<KIND, T, V, MODE, 0>(c, k, A, B, i, r);
+}
+
+template <int KIND, int T, int V>
+__global__ void __launch_bounds__(32) k_tb2f(const Pass2D p)
+{
+    using C = TB2F<KIND, T, V>;
+    extern __shared__ __align__(16) float smem[];
+    CtxF c;
+    c.in = p.in;
+    c.out = p.out;
+    c.pw = p.pw;
+    c.ld_in = p.ld_in;
+    c.ld_out = p.ld_out;
+    c.ld_pw = p.ld_pw;
+    c.sF = smem_u32(smem);
+    c.sP = c.sF + C::NBF * C::ROWB;
+    c.nx = p.nx;
+    c.ny = p.ny;
+    c.tsteps = p.tsteps;
+    c.vec_in = p.vec_in;
+    c.vec_out = p.vec_out;
+    c.vec_pw = p.vec_pw;
+    c.lane = threadIdx.x;
+    c.o4 = 4u * V * c.lane;
+    c.ow4 = c.lane > 0 ? c.o4 - 4 : 0;
+    c.oe4 = c.lane < 31 ? c.o4 + 4 * V : c.o4 + 4 * V - 4;
+    CoefF k;
+    k.a0 = p.k[0]; k.a1 = p.k[1]; k.a2 = p.k[2]; k.a3 = p.k[3]; k.a4 = p.k[4];
+    k.a5 = __fmul_rn(p.k[0], p.k[2]);   // Hotspot: sdc * Ry
+    k.a6 = -2.0f * p.k[2];              // Hotspot: -2 Ry (exact)
+
+    float A[C::NS][V], B[C::NS][V];
+#pragma unroll
+    for (int s = 0; s < C::NS; s++)
+#pragma unroll
+        for (int j = 0; j < V; j++) A[s][j] = B[s][j] = 0.f;
+
+    long long f = (long long)blockIdx.x * p.rows_per_cta;
+    const long long fend = min(f + p.rows_per_cta, p.total_rows);
+    while (f < fend) {
+        const int tx = (int)(f / p.ny);
+        const int s0 = (int)(f - (long long)tx * p.ny);
+        const int s1 = (int)min((long long)p.ny, (long long)s0 + (fend - f));
+        f += s1 - s0;
+
+        c.s0 = s0;
+        c.s1 = s1;
+        c.x0 = tx * C::CX - C::H;
+        c.xt = c.x0 + c.lane * V;
+        c.y_start = max(0, s0 - c.tsteps);
+        c.last_row = min(c.ny - 1, s1 - 1 + c.tsteps);
+        {
+            const int lcl = (c.xt <= 0 && 0 < c.xt + V) ? -c.xt : -1;
+            const int rcl = (c.xt <= c.nx - 1 && c.nx - 1 < c.xt + V) ? (c.nx - 1 - c.xt) : -1;
+            c.lmask = lcl >= 0 ? (1u << lcl) : 0u;
+            c.rmask = rcl >= 0 ? (1u << rcl) : 0u;
+            c.edge = __any_sync(0xffffffffu, lcl >= 0 || rcl >= 0);
+        }
+        {
+            const int lo = max(c.x0 + C::H, 0), hi = min(c.x0 + C::H + C::CX, c.nx);
+            c.st_lo = min(max(lo - c.xt, 0), V);
+            c.st_hi = min(max(hi - c.xt, 0), V);
+            c.st_full = c.vec_out && c.st_lo == 0 && c.st_hi == V;
+            c.st_any = c.st_hi > c.st_lo;
+        }
+        RowF r;
+#pragma unroll
+        for (int q = 0; q < V / 4; q++) {
+            const int x = c.x0 + 4 * (c.lane + 32 * q);   // chunk q of my lane
+            r.nbq[q] = (x >= 0 && x < c.nx) ? min(16, 4 * (c.nx - x)) : 0;
+            r.colq[q] = r.nbq[q] ? x : 0;
+        }
+        r.gF = c.in + (long long)c.y_start * c.ld_in;
+        r.gP = (KIND == KTHERM) ? c.pw + (long long)c.y_start * c.ld_pw : nullptr;
+        r.rf = 0;
+        r.rp = 0;
+        const int n_it = s1 + T - c.y_start;           // the last stage emits row s1-1 last
+        r.i_store = s0 - c.y_start + T;                 // it emits row s0 at this iteration
+        r.gO = c.out + (long long)s0 * c.ld_out + c.xt;
+        r.i_load_end = c.last_row - c.y_start - C::PF + 1;
+
+        // queue the first PF rows
+#pragma unroll 1
+        for (int j = 0; j < C::PF; j++) {
+            if (c.y_start + j <= c.last_row) {
+                tbf_queue<KIND, T, V>(c, r, j, (KIND == KTHERM) ? j : 0);
+                r.gF += c.ld_in;
+                if (KIND == KTHERM) r.gP += c.ld_pw;
+            }
+            cp_async_commit();
+        }
+
+        // rows that need boundary handling: the grid's top rows (for every stage), its bottom
+        // rows, and every row of a pass that forwards trailing stages
+        const bool partial = (c.tsteps < T);
+        const int i_a = partial ? n_it : ((c.y_start == 0) ? min(T + 1, n_it) : 0);
+        // (a stage meets row 0 at i <= T when the segment starts at the top, and rows ny-1 / ny
+        // from i = ny - y_start on; the bounds below keep one row of margin)
+        const int i_b = partial ? n_it : max(i_a, min(n_it, c.ny - 1 - c.y_start));
+        int i = 0;
+#pragma unroll 1
+        for (; i < i_a; i++) tbf_step_rt<KIND, T, V, MODE_SPECIAL>(c, k, A, B, i, r);
+        if (i < i_b && (i & 1)) {
+            if (c.edge) tbf_step<KIND, T, V, MODE_EDGE, 1>(c, k, A, B, i, r);
+            else tbf_step<KIND, T, V, MODE_PLAIN, 1>(c, k, A, B, i, r);
+            i++;
+        }
+        if (c.edge) {
+#pragma unroll 1
+            for (; i + 1 < i_b; i += 2) {
+                tbf_step<KIND, T, V, MODE_EDGE, 0>(c, k, A, B, i, r);
+                tbf_step<KIND, T, V, MODE_EDGE, 1>(c, k, A, B, i + 1, r);
+            }
+        } else {
+#pragma unroll 1
+            for (; i + 1 < i_b; i += 2) {
+                tbf_step<KIND, T, V, MODE_PLAIN, 0>(c, k, A, B, i, r);
+                tbf_step<KIND, T, V, MODE_PLAIN, 1>(c, k, A, B, i + 1, r);
+            }
+        }
+#pragma unroll 1
+        for (; i < n_it; i++) tbf_step_rt<KIND, T, V, MODE_SPECIAL>(c, k, A, B, i, r);
+        cp_async_wait<0>();
+        __syncwarp();
+    }
+}
+
+}  // namespace stn
