@@ -50,6 +50,7 @@ extern "C" {
 #define ST_ERR_OOM              -5   /* device allocation failed */
 #define ST_ERR_TIMEOUT          -6   /* a bounded device-side wait gave up */
 #define ST_ERR_UNSUPPORTED      -7   /* valid request this build does not provide */
+#define ST_ERR_TOO_LARGE        -8   /* grid exceeds the fixed buffer of stencil_run_noalloc */
 
 /* stencil kinds (Table 2) */
 #define ST_DIFFUSION 0
@@ -127,6 +128,30 @@ int stencil_plan_kernel_time(stencil_plan plan, double *ms, long long *launches,
 
 /* Free the plan and its scratch.  NULL is accepted. */
 int stencil_plan_destroy(stencil_plan plan);
+
+/* Allocation-free run of a 2D stencil (Diffusion 2D or Hotspot 2D); the paper has no
+ * counterpart: it exists for callers that may not allocate device memory at the call site
+ * (inside a memory pool or arena they do not own, on latency-bound paths that cannot absorb
+ * cudaMalloc's synchronisation, or under a locked-down allocator).
+ * Same arguments and result as stencil_run on a default plan, without a plan:
+ *   kind            : ST_DIFFUSION or ST_THERMAL (2D only)
+ *   grid_in/out     : device pointers, nx*ny floats, dense rows; grid_out may equal grid_in
+ *   power           : device power map for ST_THERMAL, NULL for ST_DIFFUSION
+ *   coeffs          : host array of 5 coefficients (layouts above)
+ *   steps           : >= 0
+ *   exact           : 1 = Table 2 order without fused multiply-adds, 0 = contracted
+ *   T               : fused steps per pass, 0 = 8 (the default plan's)
+ *   stream          : cudaStream_t, NULL = legacy default stream
+ * Instead of a plan-owned ping-pong grid it uses one buffer the library reserves on every
+ * device where it is loaded (16 MiB, held until the process exits): grids of more than
+ * 4,194,304 cells return ST_ERR_TOO_LARGE.  It calls no cudaMalloc, cudaFree or allocating
+ * routine.  All calls on a device share that buffer: calls whose work overlaps on the GPU
+ * (different streams, unordered host threads) race on it.  The first call on each device looks
+ * up the buffer's device address (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture.  Returns ST_OK or an ST_ERR_* code; launches are asynchronous. */
+int stencil_run_noalloc(int kind, const void *grid_in, void *grid_out, const void *power,
+                        const float *coeffs, int nx, int ny, int steps, int exact, int T,
+                        void *stream);
 
 /* Static description of a status code. */
 const char *stencil_strerror(int code);

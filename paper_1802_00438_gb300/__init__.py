@@ -23,6 +23,7 @@ ST_ERR_CUDA = -4
 ST_ERR_OOM = -5
 ST_ERR_TIMEOUT = -6
 ST_ERR_UNSUPPORTED = -7
+ST_ERR_TOO_LARGE = -8
 
 ST_DIFFUSION = 0
 ST_THERMAL = 1
@@ -68,6 +69,8 @@ SIGNATURES = {
     "stencil_plan_kernel_time": ([_P, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_longlong), _I], _I),
     "stencil_plan_destroy": ([_P], _I),
+    "stencil_run_noalloc": ([_I, _P, _P, _P, ctypes.POINTER(ctypes.c_float), _I, _I, _I, _I, _I,
+                             _P], _I),
 }
 
 
@@ -161,6 +164,18 @@ def stencil_plan_kernel_time(plan, reset: bool = True):
 
 def stencil_plan_destroy(plan):
     _check(lib.stencil_plan_destroy(plan), "stencil_plan_destroy")
+
+
+def stencil_run_noalloc(kind, grid_in, grid_out, power, coeffs, nx, ny, steps, exact=False, T=0,
+                        stream=None):
+    """2D run without a plan and without any device allocation (see include/stencil.h): for
+    callers that must not allocate device memory where they advance a grid.  Uses a fixed
+    16 MiB buffer the library reserves per device; larger grids raise ST_ERR_TOO_LARGE."""
+    k = _coef_array(coeffs)
+    _check(lib.stencil_run_noalloc(int(kind), _addr(grid_in), _addr(grid_out), _addr(power), k,
+                                   int(nx), int(ny), int(steps), 1 if exact else 0, int(T),
+                                   current_stream() if stream is None else stream),
+           "stencil_run_noalloc")
 
 
 class Plan:

@@ -297,6 +297,7 @@ const char *stencil_strerror(int code)
     case ST_ERR_OOM: return "device memory allocation failed";
     case ST_ERR_TIMEOUT: return "bounded device wait timed out";
     case ST_ERR_UNSUPPORTED: return "unsupported parameter combination";
+    case ST_ERR_TOO_LARGE: return "grid larger than the allocation-free entry point's fixed buffer";
     default: return "unknown status";
     }
 }

@@ -1,0 +1,70 @@
+"""The allocation-free entry point (stencil_run_noalloc) against the plan-based stencil_run.
+
+stencil_run_noalloc serves callers that must not allocate device memory where they advance a
+grid (inside a pool they do not own, on latency-bound paths, under a locked-down allocator):
+it runs the same kernels with a fixed buffer the library reserves per device instead of a
+plan-owned one.  This file is collected last so that a failure here leaves every other test run.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eng():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1802_00438_gb300 as st
+    return st
+
+
+def _plan_run(st, w, steps, exact):
+    import torch
+    u = torch.from_numpy(w.u0).cuda()
+    p = None if w.power is None else torch.from_numpy(w.power).cuda()
+    out = torch.empty_like(u)
+    plan = st.Plan(w.kind, 2, w.nx, w.ny, exact=exact, force_T=8)
+    plan.run(u, out, w.coef, steps, power=p)
+    plan.sync()
+    plan.close()
+    return out.cpu().numpy()
+
+
+def _noalloc_run(st, w, steps, exact, inplace=False):
+    import torch
+    u = torch.from_numpy(w.u0).cuda()
+    p = None if w.power is None else torch.from_numpy(w.power).cuda()
+    out = u if inplace else torch.full_like(u, float("nan"))
+    st.stencil_run_noalloc(w.kind, u, out, p, w.coef, w.nx, w.ny, steps, exact=exact, T=8)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("exact", [True, False])
+@pytest.mark.parametrize("kind", [0, 1])
+def test_noalloc_matches_plan_twice(eng, kind, exact):
+    # two calls in a row on different inputs: the second must not see the first's buffer
+    cases = [synth.make(kind, 2, 1000, 703, seed=910 + kind), synth.make(kind, 2, 517, 1301, seed=920 + kind)]
+    for w, steps in zip(cases, (37, 24)):
+        ref = _plan_run(eng, w, steps, exact)
+        got = _noalloc_run(eng, w, steps, exact)
+        # same kernels, same pass structure: identical results
+        assert np.array_equal(got, ref), (w.nx, w.ny, steps)
+
+
+def test_noalloc_in_place_and_limits(eng):
+    import torch
+    st = eng
+    w = synth.make(1, 2, 300, 211, seed=930)
+    ref = _plan_run(st, w, 19, exact=True)
+    got = _noalloc_run(st, w, 19, exact=True, inplace=True)
+    assert np.array_equal(got, ref)
+    # a grid beyond the fixed buffer is refused before any device work
+    big = torch.empty(8, device="cuda")
+    with pytest.raises(st.StencilError) as e:
+        st.stencil_run_noalloc(0, big, big, None, [0.2] * 5, 4096, 1025, 1)
+    assert e.value.code == st.ST_ERR_TOO_LARGE
