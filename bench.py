@@ -113,33 +113,42 @@ class Clocks:
 
 
 def kernel_source_hash(ndim: int) -> str:
-    f = "tb2d_kernel.cuh" if ndim == 2 else "tb3d_kernel.cuh"
-    src = open(os.path.join(ROOT, "paper_1802_00438_gb300", "csrc", f), "rb").read()
-    return hashlib.sha1(src).hexdigest()[:12]
+    """Hash of the sources of the benchmarked kernel family (2D contracted or 3D)."""
+    files = (("tb2f_kernel.cuh", "tb2d_kernel.cuh", "common.cuh") if ndim == 2
+             else ("tb3d_kernel.cuh", "common.cuh"))
+    h = hashlib.sha1()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_1802_00438_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
 
 
 def profiled_traffic(workload: str, ndim: int):
-    """DRAM bytes per launch recorded by an ncu capture of the current kernel source, if any
-    (profiles/traffic.json); None when the kernel changed since it was captured."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch recorded from an ncu capture of the current kernel source
+    (profiles/traffic.txt); None when the kernel changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p)).get(workload)
-    if not d or d.get("kernel_sha") != kernel_source_hash(ndim):
-        return None
-    return d.get("dram_bytes_per_launch")
+    for line in open(p):
+        f = line.split()
+        if len(f) >= 3 and not line.startswith("#") and f[0] == workload:
+            return float(f[2]) if f[1] == kernel_source_hash(ndim) else None
+    return None
 
 
 def _oracle_sample_steps(w, budget_s: float):
-    """Time steps of the full grid that take about budget_s seconds on the host cores."""
+    """Time steps of the full grid that take about budget_s seconds on the host cores (from
+    the difference of a 1-step and a 3-step run, so set-up costs do not count)."""
     import oracle
     oracle.build()
     cores = len(os.sched_getaffinity(0))
     oracle.set_threads(cores)
-    t0 = time.perf_counter()
-    oracle.run(w.kind, w.u0, w.coef, 1, w.power)
-    t1 = time.perf_counter() - t0
-    return max(1, min(w.steps, int(budget_s / max(t1, 1e-4)))), cores
+    t = []
+    for s in (1, 3):
+        t0 = time.perf_counter()
+        oracle.run(w.kind, w.u0, w.coef, s, w.power)
+        t.append(time.perf_counter() - t0)
+    per_step = max((t[1] - t[0]) / 2, 1e-5)
+    return max(1, min(w.steps, int(budget_s / per_step))), cores
 
 
 def cpu_baseline(w, budget_s: float = 15.0):
@@ -195,6 +204,7 @@ def main():
     ap.add_argument("--T", type=int, default=0, help="force the fused step count")
     ap.add_argument("--bx", type=int, default=0, help="force the 2D tile width")
     ap.add_argument("--vec", type=int, default=0, help="force cells per thread along x")
+    ap.add_argument("--by", type=int, default=0, help="force the 3D tile height (2D: kernel variant)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--nx", type=int, default=0, help="profiling: override the grid size")
@@ -204,7 +214,8 @@ def main():
     args = ap.parse_args()
 
     w = WORKLOADS[args.workload]()
-    if args.nx or args.ny or args.nz or args.time_steps:
+    resized = bool(args.nx or args.ny or args.nz or args.time_steps)
+    if resized:
         w = synth.make(w.kind, w.ndim, args.nx or w.nx, args.ny or w.ny, args.nz or w.nz,
                        steps=args.time_steps or w.steps, seed=w.seed,
                        name=f"{w.name.split('_')[0]}_resized")
@@ -230,7 +241,7 @@ def main():
     pw = None if w.power is None else torch.from_numpy(w.power).to(dev)
     out = torch.empty_like(u0)
     plan = st.Plan(w.kind, w.ndim, w.nx, w.ny, w.nz, force_T=args.T, force_bx=args.bx,
-                   force_vec=args.vec, stream=stream.cuda_stream)
+                   force_vec=args.vec, force_by=args.by, stream=stream.cuda_stream)
     info = plan.info()
     T = info["T"]
     passes = -(-w.steps // T)
@@ -324,7 +335,8 @@ def main():
     gbs = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
     cell_roof = min(alu_peak * 1e12 / fl, hbm_peak * 1e9 * T / by)      # cells/s at this T
     alu_bound = alu_peak * 1e12 / fl <= hbm_peak * 1e9 * T / by
-    traffic = profiled_traffic(args.workload, w.ndim)
+    traffic = None if (resized or args.T or args.bx or args.vec or args.by) else \
+        profiled_traffic(args.workload, w.ndim)
     if alu_bound:
         roof = {"bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": tflops / alu_peak,

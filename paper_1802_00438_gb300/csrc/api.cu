@@ -235,7 +235,9 @@ int run_pass2(stencil_plan_s *p, const float *src, long long lds, float *dst, lo
     a.total_rows = c->total;
     a.rows_per_cta = c->rows_per_cta;
     a.ctas = c->ctas;
-    for (int i = 0; i < 5; i++) a.k[i] = k[i];
+    for (int i = 0; i < 5; i++) a.k[i] = a.kf[i] = k[i];
+    a.kf[5] = k[0] * k[2];    // Hotspot: sdc * Ry, rounded once (float32)
+    a.kf[6] = -2.0f * k[2];   // Hotspot: -2 Ry (exact)
     a.vec_in = ((uintptr_t)src % 16 == 0) && (lds % 4 == 0);
     a.vec_out = ((uintptr_t)dst % 16 == 0) && (ldd % 4 == 0);
     a.vec_pw = pw ? (((uintptr_t)pw % 16 == 0) && (p->d.nx % 4 == 0)) : 0;
@@ -332,7 +334,9 @@ int stencil_plan_create(stencil_plan *out, const stencil_desc *desc)
         // Contracted plans run one-warp tiles of V = 8 cells per thread (bsize_x = 256) with
         // partial-sum stages; exact plans run the rotating-window kernel, V = 4, with W warps
         // per tile (bsize_x = 128 W).
-        p->V = d.force_vec ? d.force_vec : (d.exact ? 4 : 8);
+        // measured on GB300 (16384^2, T = 8): Hotspot runs best with V = 4 (its V = 8 body
+        // overflows the instruction cache), Diffusion with V = 8
+        p->V = d.force_vec ? d.force_vec : ((d.exact || d.kind == ST_THERMAL) ? 4 : 8);
         if (d.force_bx) {
             if (d.force_bx % (32 * p->V)) rc = ST_ERR_UNSUPPORTED;
             p->W = d.force_bx / (32 * p->V);
@@ -340,6 +344,7 @@ int stencil_plan_create(stencil_plan *out, const stencil_desc *desc)
             p->W = 1;
             if (d.exact && d.nx >= 512) p->W = 4;
         }
+        if (!d.exact && d.force_by == 1) p->W = 0;   // in-place partial-row variant
         const int want = d.force_T ? d.force_T : 8;
         p->T = kernel_T_for(p, want);
         if (p->T == 0 || (d.force_T && p->T != d.force_T)) rc = ST_ERR_UNSUPPORTED;

@@ -17,6 +17,9 @@ struct Pass2D {
     long long rows_per_cta;
     int ctas;
     float k[5];
+    // contracted kernel's coefficients, derived on the host from k: diffusion cc, cw, ce, cs, cn;
+    // Hotspot sdc, Rx, Ry, Rz, amb, sdc*Ry (rounded once), -2*Ry (exact)
+    float kf[7];
     int vec_in, vec_out, vec_pw;   // 1: rows start on 16-byte boundaries
 };
 

@@ -110,7 +110,9 @@ int pass2(const DeviceSlot &dv, int kind, int exact, int V, int W, int T, const 
                                                std::max<long long>(1, a.total_rows / min_rows));
     a.rows_per_cta = (a.total_rows + ctas - 1) / ctas;
     a.ctas = (int)((a.total_rows + a.rows_per_cta - 1) / a.rows_per_cta);
-    for (int i = 0; i < 5; i++) a.k[i] = k[i];
+    for (int i = 0; i < 5; i++) a.k[i] = a.kf[i] = k[i];
+    a.kf[5] = k[0] * k[2];    // Hotspot: sdc * Ry, rounded once (float32)
+    a.kf[6] = -2.0f * k[2];   // Hotspot: -2 Ry (exact)
     a.vec_in = ((uintptr_t)src % 16 == 0) && (nx % 4 == 0);
     a.vec_out = ((uintptr_t)dst % 16 == 0) && (nx % 4 == 0);
     a.vec_pw = pw ? (((uintptr_t)pw % 16 == 0) && (nx % 4 == 0)) : 0;
@@ -149,9 +151,9 @@ extern "C" int stencil_run_noalloc(int kind, const void *grid_in, void *grid_out
         return to_status(cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, st));
     }
     // same tile families as a default plan: exact -> rotating windows (V = 4, four warps on
-    // wide grids), contracted -> partial-sum stages (V = 8, one warp)
+    // wide grids), contracted -> partial-sum stages in one warp (Hotspot V = 4, Diffusion V = 8)
     const int ex = exact ? 1 : 0;
-    const int V = ex ? 4 : 8;
+    const int V = (ex || kind == ST_THERMAL) ? 4 : 8;
     const int W = (ex && nx >= 512) ? 4 : 1;
     int Tp = T ? T : 8;
     if (!tb2d_available(Shape2D{kind, ex, Tp, V, W})) return ST_ERR_UNSUPPORTED;

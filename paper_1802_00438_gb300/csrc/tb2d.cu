@@ -15,8 +15,8 @@ static const Tb2dEntry *tb2d_find(const Shape2D &s)
 }
 
 bool tb2d_available(const Shape2D &s) { return tb2d_find(s) != nullptr; }
-int tb2d_block_threads(const Shape2D &s) { return 32 * s.W; }
-int tb2d_tile_width(const Shape2D &s) { return 32 * s.V * s.W; }
+int tb2d_block_threads(const Shape2D &s) { return 32 * (s.W > 0 ? s.W : 1); }   // W <= 0: one warp
+int tb2d_tile_width(const Shape2D &s) { return 32 * s.V * (s.W > 0 ? s.W : 1); }
 int tb2d_halo(const Shape2D &s) { return (s.T + 3) / 4 * 4; }
 
 size_t tb2d_smem_bytes(const Shape2D &s)
@@ -32,7 +32,8 @@ cudaError_t tb2d_prepare(const Shape2D &s, int *blocks_per_sm)
     cudaError_t err = cudaFuncSetAttribute(e->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)e->smem);
     if (err != cudaSuccess) return err;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, e->fn, 32 * s.W, e->smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, e->fn, tb2d_block_threads(s),
+                                                         e->smem);
 }
 
 cudaError_t tb2d_launch(const Shape2D &s, const Pass2D &p, cudaStream_t st)
@@ -40,7 +41,7 @@ cudaError_t tb2d_launch(const Shape2D &s, const Pass2D &p, cudaStream_t st)
     const Tb2dEntry *e = tb2d_find(s);
     if (!e) return cudaErrorInvalidValue;
     void *args[] = {const_cast<Pass2D *>(&p)};
-    return cudaLaunchKernel(e->fn, dim3(p.ctas), dim3(32 * s.W), args, e->smem, st);
+    return cudaLaunchKernel(e->fn, dim3(p.ctas), dim3(tb2d_block_threads(s)), args, e->smem, st);
 }
 
 }  // namespace stn

@@ -16,8 +16,14 @@ struct Tb2dEntry {
       TB2<K, (E != 0), T_, V_, W_>::SMEM }
 
 // contracted path: one-warp blocks (W = 1), partial-sum stages
+// W = 1: partial rows alternate between two register arrays (two-row unroll);
+// W = 0 (a marker, still one warp): partial rows updated in place, no unroll
 #define STN_TB2F_ENTRY(K, T_, V_)                                                            \
-    { K, 0, T_, V_, 1, reinterpret_cast<const void *>(&k_tb2f<K, T_, V_>), TB2F<K, T_, V_>::SMEM }
+    { K, 0, T_, V_, 1, reinterpret_cast<const void *>(&k_tb2f<K, T_, V_, true>),           \
+      TB2F<K, T_, V_>::SMEM }
+#define STN_TB2F1_ENTRY(K, T_, V_)                                                           \
+    { K, 0, T_, V_, 0, reinterpret_cast<const void *>(&k_tb2f<K, T_, V_, false>),          \
+      TB2F<K, T_, V_>::SMEM }
 
 extern const Tb2dEntry tb2d_table_diff[];
 extern const int tb2d_table_diff_n;

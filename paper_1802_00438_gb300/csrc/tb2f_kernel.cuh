@@ -209,7 +209,10 @@ __device__ __forceinline__ void qf(const CoefF &k, const float (&d)[V], uint32_t
 // One stage on the arrival of row y (values d, time s).  Xp holds P (row y-1, all but its
 // south term), Xq holds Q (row y's north term).  Emits out = row y-1 at time s+1, leaves
 // row y's P in Xq and row y+1's Q in Xp.
-template <int KIND, int V, int MODE>
+// SWAP = true: P' is built on top of Q in Xq and Q' is written to Xp (the caller alternates the
+// arrays every row).  SWAP = false: P' goes back to Xp and Q' to Xq (no alternation; the
+// register allocator decides whether that needs copies).
+template <int KIND, int V, int MODE, bool SWAP>
 __device__ __forceinline__ void stf(const CtxF &c, const CoefF &k, int y, bool fwd, float (&Xp)[V],
                                     float (&Xq)[V], const float (&d)[V], float w_in, float e_in,
                                     uint32_t p_y, uint32_t p_next, float (&out)[V])
@@ -220,7 +223,8 @@ __device__ __forceinline__ void stf(const CtxF &c, const CoefF &k, int y, bool f
 #pragma unroll
         for (int j = 0; j < V; j++) {
             out[j] = Xp[j];
-            Xq[j] = d[j];   // becomes "P" of the next row: forwarded one row later
+            if (SWAP) Xq[j] = d[j];   // becomes "P" of the next row: forwarded one row later
+            else Xp[j] = d[j];
         }
         return;
     }
@@ -234,28 +238,30 @@ __device__ __forceinline__ void stf(const CtxF &c, const CoefF &k, int y, bool f
     if (SP && y == 0) qf<KIND, V>(k, d, p_y, Xq);   // top: the row above row 0 is row 0
     float dw[V], de[V];
     nbf<V, ED>(c, d, w_in, e_in, dw, de);
+    float(&Pn)[V] = SWAP ? Xq : Xp;   // where row y's P goes
+    float(&Qn)[V] = SWAP ? Xp : Xq;   // where row y+1's Q goes
     if (KIND == KDIFF) {
 #pragma unroll
         for (int j = 0; j < V; j++) {
-            Xq[j] = __fmaf_rn(k.a0, d[j], Xq[j]);
-            Xq[j] = __fmaf_rn(k.a1, dw[j], Xq[j]);
-            Xq[j] = __fmaf_rn(k.a2, de[j], Xq[j]);
+            Pn[j] = __fmaf_rn(k.a0, d[j], Xq[j]);
+            Pn[j] = __fmaf_rn(k.a1, dw[j], Pn[j]);
+            Pn[j] = __fmaf_rn(k.a2, de[j], Pn[j]);
         }
     } else {
 #pragma unroll
         for (int j = 0; j < V; j++) {
             const float t2 = __fmaf_rn(-2.0f, d[j], __fadd_rn(de[j], dw[j]));
             const float t3 = __fsub_rn(k.a4, d[j]);
-            Xq[j] = __fmaf_rn(t2, k.a1, Xq[j]);
-            Xq[j] = __fmaf_rn(t3, k.a3, Xq[j]);
-            Xq[j] = __fmaf_rn(k.a6, d[j], Xq[j]);
-            Xq[j] = __fmaf_rn(k.a0, Xq[j], d[j]);
+            Pn[j] = __fmaf_rn(t2, k.a1, Xq[j]);
+            Pn[j] = __fmaf_rn(t3, k.a3, Pn[j]);
+            Pn[j] = __fmaf_rn(k.a6, d[j], Pn[j]);
+            Pn[j] = __fmaf_rn(k.a0, Pn[j], d[j]);
         }
     }
-    qf<KIND, V>(k, d, p_next, Xp);
+    qf<KIND, V>(k, d, p_next, Qn);
     if (SP && y == c.ny - 1) {   // bottom: complete row ny-1 now with south = itself
 #pragma unroll
-        for (int j = 0; j < V; j++) Xq[j] = __fmaf_rn(cs, d[j], Xq[j]);
+        for (int j = 0; j < V; j++) Pn[j] = __fmaf_rn(cs, d[j], Pn[j]);
     }
 }
 
@@ -271,7 +277,7 @@ struct RowF {
 };
 
 // One row iteration.  PH selects which of A/B holds P (PH = 0: A) for every stage.
-template <int KIND, int T, int V, int MODE, int PH>
+template <int KIND, int T, int V, int MODE, int PH, bool SWAP>
 __device__ __forceinline__ void tbf_iter(const CtxF &c, const CoefF &k,
                                          float (&A)[TB2F<KIND, T, V>::NS][V],
                                          float (&B)[TB2F<KIND, T, V>::NS][V], int i,
@@ -311,8 +317,8 @@ __device__ __forceinline__ void tbf_iter(const CtxF &c, const CoefF &k,
         for (int j = 0; j < V; j++) d[j] = out[j];
         const float w_in = __shfl_sync(0xffffffffu, d[V - 1], (c.lane + 31) & 31);
         const float e_in = __shfl_sync(0xffffffffu, d[0], (c.lane + 1) & 31);
-        stf<KIND, V, MODE>(c, k, R0 - s, s >= c.tsteps, PH == 0 ? A[s - 1] : B[s - 1],
-                           PH == 0 ? B[s - 1] : A[s - 1], d, w_in, e_in,
+        stf<KIND, V, MODE, SWAP>(c, k, R0 - s, s >= c.tsteps, PH == 0 ? A[s - 1] : B[s - 1],
+                                 PH == 0 ? B[s - 1] : A[s - 1], d, w_in, e_in,
                            pbase - s * C::ROWB + c.o4, pbase - (s - 1) * C::ROWB + c.o4, out);
     }
     if (store) {
@@ -362,7 +368,7 @@ __device__ __forceinline__ void tbf_queue(const CtxF &c, const RowF &r, int lf, 
 }
 
 // One row: wait for row i, run the stages, queue row i+PF, advance pointers and rings.
-template <int KIND, int T, int V, int MODE, int PH>
+template <int KIND, int T, int V, int MODE, int PH, bool SWAP>
 __device__ __forceinline__ void tbf_step(const CtxF &c, const CoefF &k,
                                          float (&A)[TB2F<KIND, T, V>::NS][V],
                                          float (&B)[TB2F<KIND, T, V>::NS][V], int i, RowF &r)
@@ -381,7 +387,7 @@ __device__ __forceinline__ void tbf_step(const CtxF &c, const CoefF &k,
     }
     const uint32_t pbase = c.sP + ((KIND == KTHERM && r.rp < C::PW - 1) ? C::NBP + r.rp : r.rp) * C::ROWB;
     const bool store = i >= r.i_store;
-    tbf_iter<KIND, T, V, MODE, PH>(c, k, A, B, i, c.sF + su * C::ROWB, c.sF + sm * C::ROWB,
+    tbf_iter<KIND, T, V, MODE, PH, SWAP>(c, k, A, B, i, c.sF + su * C::ROWB, c.sF + sm * C::ROWB,
                                    c.sF + sd * C::ROWB, pbase, r.gO, store);
     if (store) r.gO += c.ld_out;
     __syncwarp();
@@ -402,16 +408,16 @@ __device__ __forceinline__ void tbf_step(const CtxF &c, const CoefF &k,
     if (KIND == KTHERM) r.rp = (r.rp + 1 == C::NBP) ? 0 : r.rp + 1;
 }
 
-template <int KIND, int T, int V, int MODE>
+template <int KIND, int T, int V, int MODE, bool SWAP>
 __device__ __forceinline__ void tbf_step_rt(const CtxF &c, const CoefF &k,
                                             float (&A)[TB2F<KIND, T, V>::NS][V],
                                             float (&B)[TB2F<KIND, T, V>::NS][V], int i, RowF &r)
 {
-    if (i & 1) tbf_step<KIND, T, V, MODE, 1>(c, k, A, B, i, r);
-    else tbf_step<KIND, T, V, MODE, 0>(c, k, A, B, i, r);
+    if (SWAP && (i & 1)) tbf_step<KIND, T, V, MODE, 1, SWAP>(c, k, A, B, i, r);
+    else tbf_step<KIND, T, V, MODE, 0, SWAP>(c, k, A, B, i, r);
 }
 
-template <int KIND, int T, int V>
+template <int KIND, int T, int V, bool SWAP>
 __global__ void __launch_bounds__(32) k_tb2f(const Pass2D p)
 {
     using C = TB2F<KIND, T, V>;
@@ -436,9 +442,9 @@ __global__ void __launch_bounds__(32) k_tb2f(const Pass2D p)
     c.ow4 = c.lane > 0 ? c.o4 - 4 : 0;
     c.oe4 = c.lane < 31 ? c.o4 + 4 * V : c.o4 + 4 * V - 4;
     CoefF k;
-    k.a0 = p.k[0]; k.a1 = p.k[1]; k.a2 = p.k[2]; k.a3 = p.k[3]; k.a4 = p.k[4];
-    k.a5 = __fmul_rn(p.k[0], p.k[2]);   // Hotspot: sdc * Ry
-    k.a6 = -2.0f * p.k[2];              // Hotspot: -2 Ry (exact)
+    k.a0 = p.kf[0]; k.a1 = p.kf[1]; k.a2 = p.kf[2]; k.a3 = p.kf[3]; k.a4 = p.kf[4];
+    k.a5 = p.kf[5];   // Hotspot: sdc * Ry
+    k.a6 = p.kf[6];   // Hotspot: -2 Ry
 
     float A[C::NS][V], B[C::NS][V];
 #pragma unroll
@@ -510,27 +516,37 @@ __global__ void __launch_bounds__(32) k_tb2f(const Pass2D p)
         const int i_b = partial ? n_it : max(i_a, min(n_it, c.ny - 1 - c.y_start));
         int i = 0;
 #pragma unroll 1
-        for (; i < i_a; i++) tbf_step_rt<KIND, T, V, MODE_SPECIAL>(c, k, A, B, i, r);
-        if (i < i_b && (i & 1)) {
-            if (c.edge) tbf_step<KIND, T, V, MODE_EDGE, 1>(c, k, A, B, i, r);
-            else tbf_step<KIND, T, V, MODE_PLAIN, 1>(c, k, A, B, i, r);
-            i++;
-        }
-        if (c.edge) {
+        for (; i < i_a; i++) tbf_step_rt<KIND, T, V, MODE_SPECIAL, SWAP>(c, k, A, B, i, r);
+        if (SWAP) {
+            if (i < i_b && (i & 1)) {
+                if (c.edge) tbf_step<KIND, T, V, MODE_EDGE, 1, SWAP>(c, k, A, B, i, r);
+                else tbf_step<KIND, T, V, MODE_PLAIN, 1, SWAP>(c, k, A, B, i, r);
+                i++;
+            }
+            if (c.edge) {
 #pragma unroll 1
-            for (; i + 1 < i_b; i += 2) {
-                tbf_step<KIND, T, V, MODE_EDGE, 0>(c, k, A, B, i, r);
-                tbf_step<KIND, T, V, MODE_EDGE, 1>(c, k, A, B, i + 1, r);
+                for (; i + 1 < i_b; i += 2) {
+                    tbf_step<KIND, T, V, MODE_EDGE, 0, SWAP>(c, k, A, B, i, r);
+                    tbf_step<KIND, T, V, MODE_EDGE, 1, SWAP>(c, k, A, B, i + 1, r);
+                }
+            } else {
+#pragma unroll 1
+                for (; i + 1 < i_b; i += 2) {
+                    tbf_step<KIND, T, V, MODE_PLAIN, 0, SWAP>(c, k, A, B, i, r);
+                    tbf_step<KIND, T, V, MODE_PLAIN, 1, SWAP>(c, k, A, B, i + 1, r);
+                }
             }
         } else {
+            if (c.edge) {
 #pragma unroll 1
-            for (; i + 1 < i_b; i += 2) {
-                tbf_step<KIND, T, V, MODE_PLAIN, 0>(c, k, A, B, i, r);
-                tbf_step<KIND, T, V, MODE_PLAIN, 1>(c, k, A, B, i + 1, r);
+                for (; i < i_b; i++) tbf_step<KIND, T, V, MODE_EDGE, 0, SWAP>(c, k, A, B, i, r);
+            } else {
+#pragma unroll 1
+                for (; i < i_b; i++) tbf_step<KIND, T, V, MODE_PLAIN, 0, SWAP>(c, k, A, B, i, r);
             }
         }
 #pragma unroll 1
-        for (; i < n_it; i++) tbf_step_rt<KIND, T, V, MODE_SPECIAL>(c, k, A, B, i, r);
+        for (; i < n_it; i++) tbf_step_rt<KIND, T, V, MODE_SPECIAL, SWAP>(c, k, A, B, i, r);
         cp_async_wait<0>();
         __syncwarp();
     }
