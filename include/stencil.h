@@ -129,6 +129,69 @@ int stencil_plan_kernel_time(stencil_plan plan, double *ms, long long *launches,
 /* Free the plan and its scratch.  NULL is accepted. */
 int stencil_plan_destroy(stencil_plan plan);
 
+/* ---- performance models (host only, no device work) ------------------------------------ */
+
+/* Inputs of the paper's FPGA performance model (Sec. 4, Table 1 parameters). */
+typedef struct {
+    int ndim;                      /* 2 or 3 */
+    long long dim_x, dim_y, dim_z; /* input size per dimension (dim_z ignored for 2D) */
+    int bsize_x, bsize_y;          /* spatial block size (bsize_y: 3D only) */
+    int rad, par_vec, par_time;    /* stencil radius, vector width, parallel time steps */
+    int size_cell;                 /* bytes per cell */
+    int num_read, num_write;       /* external memory accesses per cell update */
+    long long iter;                /* iterations */
+    double fmax_hz;                /* kernel operating frequency */
+    double th_max_gbs;             /* maximum memory throughput, GB/s (10^9 B/s) */
+} stencil_fpga_model_in;
+
+typedef struct {
+    double th_mem_gbs;             /* Eq. 3 */
+    long long csize_x, csize_y;    /* Eq. 4 (csize_y: 3D) */
+    long long bnum_x, bnum_y;      /* Eq. 5 */
+    double t_cell;                 /* Eq. 6 */
+    double t_read, t_write;        /* Eq. 7 and the write count (input size x num_write) */
+    double run_time_s;             /* Eq. 8 */
+    double throughput_gbs;         /* Eq. 9 */
+} stencil_fpga_model_out;
+
+/* The paper's performance model, Eqs. 3-9 (Sec. 4).  For 3D, where the paper gives Eq. 7 for
+ * 2D only, the out-of-bound traversal is subtracted along x and along y.  Returns ST_OK or
+ * ST_ERR_INVALID_ARG (missing pointer, non-positive sizes, a block no wider than its halos). */
+int stencil_model_fpga(const stencil_fpga_model_in *in, stencil_fpga_model_out *out);
+
+/* Inputs of the GPU restatement of the model (one fused pass = one launch). */
+typedef struct {
+    int ndim;                      /* 2 or 3 */
+    long long nx, ny, nz;          /* grid */
+    int steps;                     /* time steps of the run */
+    int T;                         /* fused steps per pass (par_time) */
+    int bx, by;                    /* tile incl. halos (by: 3D) */
+    int halo_x, halo_y;            /* halo per side */
+    int sms;                       /* streaming multiprocessors */
+    double sm_hz;                  /* SM clock */
+    double hbm_gbs;                /* device memory bandwidth, GB/s */
+    double bytes_per_cell;         /* algorithmic bytes per cell per pass (8 or 12 for float32) */
+    double ops_per_cell;           /* issued thread instructions per computed cell update */
+    double issue_eff, hbm_eff;     /* calibration factors (fraction of peak reached) */
+    double stream_overhead;        /* extra computed rows/planes of the streamed axis, fraction */
+    double launch_s;               /* fixed cost per pass */
+} stencil_gpu_model_in;
+
+typedef struct {
+    double passes;                 /* ceil(steps / T) */
+    double bytes_per_pass;         /* algorithmic HBM bytes */
+    double cells_computed_per_pass;/* halos included, times T */
+    double t_hbm_s, t_alu_s;       /* HBM time and issue time of one pass */
+    double t_pass_s;               /* max of the two, plus the launch cost */
+    double run_time_s;             /* passes x t_pass_s */
+    double gcells;                 /* nx*ny*nz*steps / run_time, in 10^9 cell updates/s */
+} stencil_gpu_model_out;
+
+/* GPU restatement of Eqs. 3-9: per pass, time = max(algorithmic bytes / (HBM bandwidth x
+ * hbm_eff), computed cells x ops_per_cell / (SMs x 128 lanes x clock x issue_eff)) + launch
+ * cost; run time over ceil(steps/T) passes (Eq. 8).  Returns ST_OK or ST_ERR_INVALID_ARG. */
+int stencil_model_gpu(const stencil_gpu_model_in *in, stencil_gpu_model_out *out);
+
 /* Allocation-free run of a 2D stencil (Diffusion 2D or Hotspot 2D); the paper has no
  * counterpart: it exists for callers that may not allocate device memory at the call site
  * (inside a memory pool or arena they do not own, on latency-bound paths that cannot absorb

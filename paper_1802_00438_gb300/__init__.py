@@ -55,6 +55,47 @@ class stencil_plan_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class stencil_fpga_model_in(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("dim_x", ctypes.c_longlong), ("dim_y", ctypes.c_longlong),
+                ("dim_z", ctypes.c_longlong), ("bsize_x", ctypes.c_int), ("bsize_y", ctypes.c_int),
+                ("rad", ctypes.c_int), ("par_vec", ctypes.c_int), ("par_time", ctypes.c_int),
+                ("size_cell", ctypes.c_int), ("num_read", ctypes.c_int), ("num_write", ctypes.c_int),
+                ("iter", ctypes.c_longlong), ("fmax_hz", ctypes.c_double),
+                ("th_max_gbs", ctypes.c_double)]
+
+
+class stencil_fpga_model_out(ctypes.Structure):
+    _fields_ = [("th_mem_gbs", ctypes.c_double), ("csize_x", ctypes.c_longlong),
+                ("csize_y", ctypes.c_longlong), ("bnum_x", ctypes.c_longlong),
+                ("bnum_y", ctypes.c_longlong), ("t_cell", ctypes.c_double),
+                ("t_read", ctypes.c_double), ("t_write", ctypes.c_double),
+                ("run_time_s", ctypes.c_double), ("throughput_gbs", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class stencil_gpu_model_in(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_longlong), ("ny", ctypes.c_longlong),
+                ("nz", ctypes.c_longlong), ("steps", ctypes.c_int), ("T", ctypes.c_int),
+                ("bx", ctypes.c_int), ("by", ctypes.c_int), ("halo_x", ctypes.c_int),
+                ("halo_y", ctypes.c_int), ("sms", ctypes.c_int), ("sm_hz", ctypes.c_double),
+                ("hbm_gbs", ctypes.c_double), ("bytes_per_cell", ctypes.c_double),
+                ("ops_per_cell", ctypes.c_double), ("issue_eff", ctypes.c_double),
+                ("hbm_eff", ctypes.c_double), ("stream_overhead", ctypes.c_double),
+                ("launch_s", ctypes.c_double)]
+
+
+class stencil_gpu_model_out(ctypes.Structure):
+    _fields_ = [("passes", ctypes.c_double), ("bytes_per_pass", ctypes.c_double),
+                ("cells_computed_per_pass", ctypes.c_double), ("t_hbm_s", ctypes.c_double),
+                ("t_alu_s", ctypes.c_double), ("t_pass_s", ctypes.c_double),
+                ("run_time_s", ctypes.c_double), ("gcells", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 # C ABI symbols, with their argument types
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -69,6 +110,10 @@ SIGNATURES = {
     "stencil_plan_kernel_time": ([_P, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_longlong), _I], _I),
     "stencil_plan_destroy": ([_P], _I),
+    "stencil_model_fpga": ([ctypes.POINTER(stencil_fpga_model_in),
+                            ctypes.POINTER(stencil_fpga_model_out)], _I),
+    "stencil_model_gpu": ([ctypes.POINTER(stencil_gpu_model_in),
+                           ctypes.POINTER(stencil_gpu_model_out)], _I),
     "stencil_run_noalloc": ([_I, _P, _P, _P, ctypes.POINTER(ctypes.c_float), _I, _I, _I, _I, _I,
                              _P], _I),
 }
@@ -164,6 +209,23 @@ def stencil_plan_kernel_time(plan, reset: bool = True):
 
 def stencil_plan_destroy(plan):
     _check(lib.stencil_plan_destroy(plan), "stencil_plan_destroy")
+
+
+def stencil_model_fpga(**kw) -> dict:
+    """The paper's performance model (Eqs. 3-9); keyword arguments are the fields of
+    stencil_fpga_model_in."""
+    m = stencil_fpga_model_in(**kw)
+    r = stencil_fpga_model_out()
+    _check(lib.stencil_model_fpga(ctypes.byref(m), ctypes.byref(r)), "stencil_model_fpga")
+    return r.as_dict()
+
+
+def stencil_model_gpu(**kw) -> dict:
+    """GPU restatement of the model; keyword arguments are the fields of stencil_gpu_model_in."""
+    m = stencil_gpu_model_in(**kw)
+    r = stencil_gpu_model_out()
+    _check(lib.stencil_model_gpu(ctypes.byref(m), ctypes.byref(r)), "stencil_model_gpu")
+    return r.as_dict()
 
 
 def stencil_run_noalloc(kind, grid_in, grid_out, power, coeffs, nx, ny, steps, exact=False, T=0,

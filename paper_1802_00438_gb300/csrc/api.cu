@@ -87,6 +87,49 @@ bool available(const stencil_plan_s *p, int T)
     return tb3d_available(Shape3D{p->d.kind, p->d.exact ? 1 : 0, T, p->VY, p->NW});
 }
 
+// ---- parameter choice seeded by the GPU restatement of the paper's model (Eqs. 3-9) -------
+//
+// Calibration (GB300 ncu counts of the contracted 2D kernels): each stage issues its Table 2
+// operations (5 Diffusion, 9 Hotspot per cell) plus ~4 per thread (2 shuffles, power loads,
+// addressing), each row ~100 more per thread (waits, copies, ring and pointer updates); issue
+// efficiency grows with resident warps (0.69 at 8, 0.77 at 12 per SM); a hot loop beyond ~12 KB
+// of code loses issue rate in proportion (instruction-cache misses); these kernels reach ~62 %
+// of the measured copy bandwidth when they are memory-bound.  With these factors the model
+// ranks the compiled variants as measured on 16384^2 grids at T in {4, 6, 8, 12}.
+struct Cand2D { int T, V, W; };
+
+double model_gcells_2d(const stencil_desc &d, int sms, const Cand2D &k, int bps, int steps)
+{
+    const bool swap = k.W == 1;
+    const double fp = d.kind == ST_DIFFUSION ? 5.0 : 9.0;
+    const double ops = fp + 4.0 / k.V + 100.0 / (k.T * k.V);
+    const double code_kb = (swap ? 2.0 : 1.0) * k.T * (k.V * fp + 6.0) * 16.0 / 1024.0;
+    const int warps = std::min(bps, 16);
+    double eff = std::min(0.85, 0.45 + 0.027 * warps);
+    if (code_kb > 12.0) eff *= 12.0 / code_kb;
+    stencil_gpu_model_in m = {};
+    m.ndim = 2;
+    m.nx = d.nx;
+    m.ny = d.ny;
+    m.nz = 1;
+    m.steps = steps > 0 ? steps : 1000;
+    m.T = k.T;
+    m.bx = 32 * k.V;
+    m.halo_x = (k.T + 3) / 4 * 4;
+    m.sms = sms;
+    m.sm_hz = 2.07e9;
+    m.hbm_gbs = 6800.0;
+    m.bytes_per_cell = d.kind == ST_DIFFUSION ? 8.0 : 12.0;
+    m.ops_per_cell = ops;
+    m.issue_eff = eff;
+    m.hbm_eff = 0.62;
+    m.stream_overhead = 0.05;
+    m.launch_s = 4e-6;
+    stencil_gpu_model_out r;
+    if (stencil_model_gpu(&m, &r) != ST_OK) return 0.0;
+    return r.gcells;
+}
+
 // smallest compiled kernel T >= want for the plan's family (or the largest compiled one)
 int kernel_T_for(const stencil_plan_s *p, int want)
 {
@@ -345,8 +388,43 @@ int stencil_plan_create(stencil_plan *out, const stencil_desc *desc)
             if (d.exact && d.nx >= 512) p->W = 4;
         }
         if (!d.exact && d.force_by == 1) p->W = 0;   // in-place partial-row variant
+        if (!d.exact && !d.force_T && !d.force_vec && !d.force_bx && !d.force_by) {
+            // contracted, nothing forced: the compiled (T, V, variant) the model rates best
+            const Cand2D cands[] = {{4, 4, 1}, {8, 4, 1}, {12, 4, 1}, {4, 8, 1}, {6, 8, 1},
+                                    {8, 8, 1}, {8, 8, 0}, {12, 4, 0}};
+            double best = -1.0;
+            for (const Cand2D &k : cands) {
+                const Shape2D sh{d.kind, 0, k.T, k.V, k.W};
+                if (!tb2d_available(sh)) continue;
+                int bps = 0;
+                if (tb2d_prepare(sh, &bps) != cudaSuccess || bps < 1) continue;
+                const double g = model_gcells_2d(d, p->sms, k, bps, 1000);
+                if (g > best) {
+                    best = g;
+                    p->V = k.V;
+                    p->W = k.W;
+                }
+            }
+            (void)cudaGetLastError();
+        }
         const int want = d.force_T ? d.force_T : 8;
         p->T = kernel_T_for(p, want);
+        if (!d.exact && !d.force_T && !d.force_vec && !d.force_bx && !d.force_by) {
+            // and the T the model rates best within that family
+            double best = -1.0;
+            for (int t : kTcand) {
+                const Shape2D sh{d.kind, 0, t, p->V, p->W};
+                if (!tb2d_available(sh)) continue;
+                int bps = 0;
+                if (tb2d_prepare(sh, &bps) != cudaSuccess || bps < 1) continue;
+                const double g = model_gcells_2d(d, p->sms, Cand2D{t, p->V, p->W}, bps, 1000);
+                if (g > best) {
+                    best = g;
+                    p->T = t;
+                }
+            }
+            (void)cudaGetLastError();
+        }
         if (p->T == 0 || (d.force_T && p->T != d.force_T)) rc = ST_ERR_UNSUPPORTED;
         PassCfg2D *c = nullptr;
         if (rc == ST_OK) rc = prepare2(p, p->T, &c);
