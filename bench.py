@@ -165,6 +165,29 @@ def cpu_baseline(w, budget_s: float = 15.0):
                       f"time steps ({t:.1f} s; float32 oracle, OpenMP over rows)"}
 
 
+def lowp_errors(w, st, stream, side=2048):
+    """Relative L2 / L-inf error after the full step count, float32 / bf16 / fp16 storage, vs
+    the float64 oracle, on a side x side grid of the same workload (seeded like it)."""
+    import torch
+    import oracle
+    ws = synth.make(w.kind, 2, min(side, w.nx), min(side, w.ny), steps=w.steps, seed=w.seed)
+    ref = oracle.run(ws.kind, ws.u0, ws.coef, ws.steps, ws.power, dtype=np.float64)
+    u = torch.from_numpy(ws.u0).cuda()
+    p = None if ws.power is None else torch.from_numpy(ws.power).cuda()
+    res = {"grid": f"{ws.nx}x{ws.ny}", "time_steps": ws.steps}
+    for name, stor in (("f32", st.ST_F32), ("bf16", st.ST_BF16), ("fp16", st.ST_F16)):
+        o = torch.empty_like(u)
+        pl = st.Plan(ws.kind, 2, ws.nx, ws.ny, storage=stor, stream=stream.cuda_stream)
+        pl.run(u, o, ws.coef, ws.steps, power=p)
+        pl.sync()
+        pl.close()
+        g = o.cpu().numpy().astype(np.float64)
+        d = g - ref
+        res[name] = {"rel_l2": float(np.linalg.norm(d) / np.linalg.norm(ref)),
+                     "rel_linf": float(np.abs(d).max() / np.abs(ref).max())}
+    return res
+
+
 def run_reference(args, w):
     """Reference arm: the CPU oracle, each benchmark step a bounded sample of the workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -205,8 +228,10 @@ def main():
     ap.add_argument("--bx", type=int, default=0, help="force the 2D tile width")
     ap.add_argument("--vec", type=int, default=0, help="force cells per thread along x")
     ap.add_argument("--by", type=int, default=0, help="force the 3D tile height (2D: kernel variant)")
+    ap.add_argument("--storage", type=int, default=0, help="grid storage: 0 float32, 1 bf16, 2 fp16")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    ap.add_argument("--no-lowp", action="store_true", help="skip the bf16/fp16 storage runs")
     ap.add_argument("--nx", type=int, default=0, help="profiling: override the grid size")
     ap.add_argument("--ny", type=int, default=0)
     ap.add_argument("--nz", type=int, default=0)
@@ -241,7 +266,8 @@ def main():
     pw = None if w.power is None else torch.from_numpy(w.power).to(dev)
     out = torch.empty_like(u0)
     plan = st.Plan(w.kind, w.ndim, w.nx, w.ny, w.nz, force_T=args.T, force_bx=args.bx,
-                   force_vec=args.vec, force_by=args.by, stream=stream.cuda_stream)
+                   force_vec=args.vec, force_by=args.by, storage=args.storage,
+                   stream=stream.cuda_stream)
     info = plan.info()
     T = info["T"]
     passes = -(-w.steps // T)
@@ -352,6 +378,31 @@ def main():
     roof["kernel_ms_per_launch"] = avg_launch_ms
 
     clocks = clk.summary()
+
+    # ---- 16-bit storage: speed on the same workload, error vs the float64 oracle ------------
+    lowp = None
+    if w.ndim == 2 and not resized and not args.no_lowp and not args.storage:
+        lowp = {}
+        for name, stor in (("bf16", st.ST_BF16), ("fp16", st.ST_F16)):
+            qplan = st.Plan(w.kind, 2, w.nx, w.ny, storage=stor, stream=stream.cuda_stream)
+            for _ in range(2):
+                qplan.run(u0, out, w.coef, w.steps, power=pw)
+            torch.cuda.synchronize()
+            q0 = torch.cuda.Event(enable_timing=True)
+            q1 = torch.cuda.Event(enable_timing=True)
+            q0.record(stream)
+            for _ in range(args.steps):
+                qplan.run(u0, out, w.coef, w.steps, power=pw)
+            q1.record(stream)
+            torch.cuda.synchronize()
+            qms = q0.elapsed_time(q1)
+            qv = world * cells_step * args.steps / (qms * 1e-3) / 1e9
+            lowp[name] = {"value": qv, "unit": "GCell/s", "speedup_vs_f32": qv / value,
+                          "T": qplan.info()["T"]}
+            qplan.close()
+        if not args.no_cpu and world == 1:
+            lowp["error_vs_f64_oracle"] = lowp_errors(w, st, stream)
+
     if dist:
         dist.barrier()
     if rank == 0:
@@ -367,7 +418,7 @@ def main():
                            "passes_per_step": passes,
                            "l2": "inputs larger than L2 (%.0f MiB per grid)" % (w.u0.nbytes / 2**20),
                            "parallelism": f"replicas{world}" if world > 1 else "single"},
-                "roofline": roof, "e2e": e2e,
+                "roofline": roof, "e2e": e2e, "lowp": lowp,
                 "gpu_launches": launches, "clocks": clocks}
         if not args.no_cpu and world == 1:
             line["cpu_baseline"] = cpu_baseline(w)

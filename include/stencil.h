@@ -35,6 +35,8 @@
 #ifndef GB300_STENCIL_H
 #define GB300_STENCIL_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -60,6 +62,7 @@ extern "C" {
 #define ST_F32  0
 #define ST_BF16 1
 #define ST_F16  2
+#define ST_F64  3   /* verification reductions only */
 
 typedef struct stencil_plan_s *stencil_plan;
 
@@ -128,6 +131,60 @@ int stencil_plan_kernel_time(stencil_plan plan, double *ms, long long *launches,
 
 /* Free the plan and its scratch.  NULL is accepted. */
 int stencil_plan_destroy(stencil_plan plan);
+
+/* ---- many grids in one graph launch ----------------------------------------------------- */
+
+typedef struct stencil_batch_s *stencil_batch;
+
+/* One 2D grid of a batch (contracted arithmetic). */
+typedef struct {
+    int kind;              /* ST_DIFFUSION or ST_THERMAL */
+    int nx, ny;            /* >= 1 */
+    int steps;             /* >= 0 */
+    const void *grid_in;   /* device, nx*ny floats */
+    void *grid_out;        /* device, nx*ny floats; may equal grid_in, no other overlap */
+    const void *power;     /* device power map (ST_THERMAL) or NULL */
+    float coeffs[5];       /* Table 2 coefficients (layouts above) */
+} stencil_batch_grid;
+
+/* Prepare `count` grids for repeated batched runs: each grid gets (T, cells per thread) from
+ * the GPU restatement of the paper's model (Eqs. 3-9) and its own ping-pong scratch (Sec. 2.1);
+ * grids that share a kernel form a group, and pass p of a group is one launch over a work
+ * queue spanning all its grids that still have a pass p (Eq. 8: ceil(steps/T) passes per grid,
+ * the last fusing the remainder, Sec. 3.2).  All launches are captured into one CUDA graph on
+ * `stream` (NULL: an owned stream that synchronises with the legacy default stream).  Buffers
+ * and coefficients are fixed at creation.  Errors: ST_ERR_INVALID_ARG, ST_ERR_UNSUPPORTED,
+ * ST_ERR_OOM, ST_ERR_CUDA. */
+int stencil_batch_create(stencil_batch *out, const stencil_batch_grid *grids, int count,
+                         void *stream);
+
+/* Replay the batch's graph (asynchronous): every grid advances by its step count into its
+ * grid_out. */
+int stencil_batch_run(stencil_batch b);
+
+/* Grid g's chosen fused steps T, cells per thread and pass count. */
+int stencil_batch_get_grid(stencil_batch b, int g, int *T, int *vec, int *passes);
+
+/* Kernel launches in the batch's graph (or ST_ERR_INVALID_ARG). */
+int stencil_batch_launch_count(stencil_batch b);
+
+/* Wait for the batch's stream, free its graph and scratch.  NULL is accepted. */
+int stencil_batch_destroy(stencil_batch b);
+
+/* ---- float64 verification reductions ----------------------------------------------------- */
+
+/* Bytes of device workspace stencil_reduce needs (caller-allocated, 8-byte aligned). */
+size_t stencil_reduce_workspace_bytes(void);
+
+/* Float64 statistics of a grid a (and of b and a - b when b is not NULL), for verification:
+ * global sum / energy (sum of squares) to check conservation, and the L2 / L-infinity norms of
+ * a difference against a reference.  Writes 8 doubles to the DEVICE pointer out, in order:
+ *   sum(a), sum(a^2), max|a|, sum(b), sum(b^2), max|b|, sum((a-b)^2), max|a-b|
+ * (entries 3..7 are 0 when b is NULL).  a_type / b_type: ST_F32 or ST_F64; n: elements (>= 1);
+ * workspace: stencil_reduce_workspace_bytes() of device memory.  Deterministic: the summation
+ * order depends on n only.  Asynchronous on `stream`.  Errors: ST_ERR_INVALID_ARG, ST_ERR_CUDA. */
+int stencil_reduce(const void *a, int a_type, const void *b, int b_type, long long n,
+                   double *out, void *workspace, void *stream);
 
 /* ---- performance models (host only, no device work) ------------------------------------ */
 

@@ -27,7 +27,7 @@ ST_ERR_TOO_LARGE = -8
 
 ST_DIFFUSION = 0
 ST_THERMAL = 1
-ST_F32, ST_BF16, ST_F16 = 0, 1, 2
+ST_F32, ST_BF16, ST_F16, ST_F64 = 0, 1, 2, 3
 
 
 class StencilError(RuntimeError):
@@ -96,6 +96,13 @@ class stencil_gpu_model_out(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class stencil_batch_grid(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("steps", ctypes.c_int), ("grid_in", ctypes.c_void_p),
+                ("grid_out", ctypes.c_void_p), ("power", ctypes.c_void_p),
+                ("coeffs", ctypes.c_float * 5)]
+
+
 # C ABI symbols, with their argument types
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -110,6 +117,13 @@ SIGNATURES = {
     "stencil_plan_kernel_time": ([_P, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_longlong), _I], _I),
     "stencil_plan_destroy": ([_P], _I),
+    "stencil_batch_create": ([ctypes.POINTER(_P), ctypes.POINTER(stencil_batch_grid), _I, _P], _I),
+    "stencil_batch_run": ([_P], _I),
+    "stencil_batch_get_grid": ([_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "stencil_batch_launch_count": ([_P], _I),
+    "stencil_batch_destroy": ([_P], _I),
+    "stencil_reduce_workspace_bytes": ([], ctypes.c_size_t),
+    "stencil_reduce": ([_P, _I, _P, _I, ctypes.c_longlong, _P, _P, _P], _I),
     "stencil_model_fpga": ([ctypes.POINTER(stencil_fpga_model_in),
                             ctypes.POINTER(stencil_fpga_model_out)], _I),
     "stencil_model_gpu": ([ctypes.POINTER(stencil_gpu_model_in),
@@ -211,6 +225,36 @@ def stencil_plan_destroy(plan):
     _check(lib.stencil_plan_destroy(plan), "stencil_plan_destroy")
 
 
+REDUCE_FIELDS = ("sum_a", "sumsq_a", "maxabs_a", "sum_b", "sumsq_b", "maxabs_b", "sumsq_diff",
+                 "maxabs_diff")
+
+
+def stencil_reduce(a, b=None, stream=None) -> dict:
+    """Float64 statistics of grid a (float32 or float64 CUDA tensor) and, with b, of b and a-b
+    (see include/stencil.h).  Synchronises the stream to return host values."""
+    import torch
+
+    def typed(t):
+        if t.dtype == torch.float32:
+            return ST_F32
+        if t.dtype == torch.float64:
+            return ST_F64
+        raise ValueError("float32 or float64 tensors only")
+
+    if not (a.is_cuda and a.is_contiguous()) or (b is not None and not (b.is_cuda and b.is_contiguous())):
+        raise ValueError("contiguous CUDA tensors only")
+    if b is not None and b.numel() != a.numel():
+        raise ValueError("a and b differ in size")
+    ws = torch.empty(lib.stencil_reduce_workspace_bytes() // 8, dtype=torch.float64, device=a.device)
+    out = torch.zeros(8, dtype=torch.float64, device=a.device)
+    st = current_stream() if stream is None else stream
+    _check(lib.stencil_reduce(a.data_ptr(), typed(a), None if b is None else b.data_ptr(),
+                              typed(b) if b is not None else 0, a.numel(), out.data_ptr(),
+                              ws.data_ptr(), st), "stencil_reduce")
+    vals = out.cpu().tolist()
+    return dict(zip(REDUCE_FIELDS, vals))
+
+
 def stencil_model_fpga(**kw) -> dict:
     """The paper's performance model (Eqs. 3-9); keyword arguments are the fields of
     stencil_fpga_model_in."""
@@ -238,6 +282,51 @@ def stencil_run_noalloc(kind, grid_in, grid_out, power, coeffs, nx, ny, steps, e
                                    int(nx), int(ny), int(steps), 1 if exact else 0, int(T),
                                    current_stream() if stream is None else stream),
            "stencil_run_noalloc")
+
+
+class Batch:
+    """Owning wrapper of stencil_batch: grids is a list of dicts with keys kind, nx, ny, steps,
+    grid_in, grid_out, power (CUDA tensors or None) and coeffs."""
+
+    def __init__(self, grids, stream=None):
+        arr = (stencil_batch_grid * len(grids))()
+        for i, g in enumerate(grids):
+            arr[i].kind = g["kind"]
+            arr[i].nx = g["nx"]
+            arr[i].ny = g["ny"]
+            arr[i].steps = g["steps"]
+            arr[i].grid_in = _addr(g["grid_in"])
+            arr[i].grid_out = _addr(g["grid_out"])
+            arr[i].power = _addr(g.get("power"))
+            for j, c in enumerate(list(g["coeffs"])[:5]):
+                arr[i].coeffs[j] = float(c)
+        self.keep = grids
+        self.h = ctypes.c_void_p()
+        _check(lib.stencil_batch_create(ctypes.byref(self.h), arr, len(grids), stream),
+               "stencil_batch_create")
+
+    def run(self):
+        _check(lib.stencil_batch_run(self.h), "stencil_batch_run")
+
+    def grid_info(self, g):
+        t, v, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib.stencil_batch_get_grid(self.h, g, ctypes.byref(t), ctypes.byref(v), ctypes.byref(p)),
+               "stencil_batch_get_grid")
+        return {"T": t.value, "vec": v.value, "passes": p.value}
+
+    def launches(self):
+        return int(lib.stencil_batch_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _check(lib.stencil_batch_destroy(self.h), "stencil_batch_destroy")
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:

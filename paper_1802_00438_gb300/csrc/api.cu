@@ -60,6 +60,14 @@ struct stencil_plan_s {
     double ms_acc = 0.0;
     long long launches = 0;
     int sticky = ST_OK;
+    // 16-bit storage (2D contracted plans): ping-pong grids and block codes, coded power map
+    int stor = 0;
+    long long ld_q = 0;
+    int cx = 0, ntx = 0;
+    void *q[2] = {nullptr, nullptr};
+    float2 *qm[2] = {nullptr, nullptr};
+    void *qp = nullptr;
+    float2 *qpm = nullptr;
 };
 
 namespace {
@@ -83,7 +91,8 @@ int ncoef(const stencil_desc &d)
 
 bool available(const stencil_plan_s *p, int T)
 {
-    if (p->d.ndim == 2) return tb2d_available(Shape2D{p->d.kind, p->d.exact ? 1 : 0, T, p->V, p->W});
+    if (p->d.ndim == 2)
+        return tb2d_available(Shape2D{p->d.kind, p->d.exact ? 1 : 0, T, p->V, p->W, p->stor});
     return tb3d_available(Shape3D{p->d.kind, p->d.exact ? 1 : 0, T, p->VY, p->NW});
 }
 
@@ -130,6 +139,24 @@ double model_gcells_2d(const stencil_desc &d, int sms, const Cand2D &k, int bps,
     return r.gcells;
 }
 
+}  // namespace
+
+namespace stn {
+// the batch's per-grid choice uses the same calibrated model
+double batch_model_gcells(int kind, int nx, int ny, int steps, int sms, int T, int V, int bps)
+{
+    stencil_desc d = {};
+    d.kind = kind;
+    d.ndim = 2;
+    d.nx = nx;
+    d.ny = ny;
+    d.nz = 1;
+    return model_gcells_2d(d, sms, Cand2D{T, V, 1}, bps, steps);
+}
+}  // namespace stn
+
+namespace {
+
 // smallest compiled kernel T >= want for the plan's family (or the largest compiled one)
 int kernel_T_for(const stencil_plan_s *p, int want)
 {
@@ -147,7 +174,7 @@ int prepare2(stencil_plan_s *p, int Tk, PassCfg2D **out)
     if ((int)p->cfg2.size() <= Tk) p->cfg2.resize(Tk + 1);
     PassCfg2D &c = p->cfg2[Tk];
     if (!c.ready) {
-        c.shape = Shape2D{p->d.kind, p->d.exact ? 1 : 0, Tk, p->V, p->W};
+        c.shape = Shape2D{p->d.kind, p->d.exact ? 1 : 0, Tk, p->V, p->W, p->stor};
         if (!tb2d_available(c.shape)) return ST_ERR_UNSUPPORTED;
         int bps = 0;
         cudaError_t e = tb2d_prepare(c.shape, &bps);
@@ -294,6 +321,39 @@ int run_pass2(stencil_plan_s *p, const float *src, long long lds, float *dst, lo
     return map_cuda(e);
 }
 
+// one pass of a 16-bit plan: coded grid q[src] -> q[dst], always the plan's T kernel (the
+// trailing stages forward when tsteps < T), so the block codes keep the plan's tiling
+int run_pass2q(stencil_plan_s *p, int src, int dst, const float *k, int tsteps)
+{
+    PassCfg2D *c = nullptr;
+    int rc = prepare2(p, p->T, &c);
+    if (rc != ST_OK) return rc;
+    Pass2D a = {};
+    a.nx = p->d.nx;
+    a.ny = p->d.ny;
+    a.tsteps = tsteps;
+    a.ntx = c->ntx;
+    a.total_rows = c->total;
+    a.rows_per_cta = c->rows_per_cta;
+    a.ctas = c->ctas;
+    for (int i = 0; i < 5; i++) a.k[i] = a.kf[i] = k[i];
+    a.kf[5] = k[0] * k[2];
+    a.kf[6] = -2.0f * k[2];
+    a.vec_in = a.vec_out = a.vec_pw = 1;
+    a.stor = p->stor;
+    a.qin = p->q[src];
+    a.qout = p->q[dst];
+    a.min_ = p->qm[src];
+    a.mout = p->qm[dst];
+    a.qpw = p->qp;
+    a.mpw = p->qpm;
+    a.ld_q = p->ld_q;
+    cudaError_t e = record(p, true);
+    if (e == cudaSuccess) e = tb2d_launch(c->shape, a, p->stream);
+    if (e == cudaSuccess) e = record(p, false);
+    return map_cuda(e);
+}
+
 int run_pass3(stencil_plan_s *p, const float *src, float *dst, const float *pw, const float *k,
               int tsteps)
 {
@@ -347,6 +407,8 @@ const char *stencil_strerror(int code)
     }
 }
 
+int stencil_plan_destroy(stencil_plan p);
+
 int stencil_plan_create(stencil_plan *out, const stencil_desc *desc)
 {
     if (!out) return ST_ERR_INVALID_ARG;
@@ -357,7 +419,10 @@ int stencil_plan_create(stencil_plan *out, const stencil_desc *desc)
     if (d.ndim != 2 && d.ndim != 3) return ST_ERR_INVALID_ARG;
     if (d.ndim == 2) d.nz = 1;
     if (d.nx < 1 || d.ny < 1 || d.nz < 1) return ST_ERR_INVALID_ARG;
-    if (d.storage != ST_F32) return ST_ERR_UNSUPPORTED;
+    if (d.storage != ST_F32 && d.storage != ST_BF16 && d.storage != ST_F16)
+        return ST_ERR_INVALID_ARG;
+    // 16-bit storage: 2D contracted plans only
+    if (d.storage != ST_F32 && (d.ndim != 2 || d.exact)) return ST_ERR_UNSUPPORTED;
     if (d.force_T < 0 || d.force_bx < 0 || d.force_by < 0 || d.force_vec < 0)
         return ST_ERR_INVALID_ARG;
 
@@ -373,6 +438,7 @@ int stencil_plan_create(stencil_plan *out, const stencil_desc *desc)
         return map_cuda(e);
     }
 
+    p->stor = d.storage == ST_BF16 ? 1 : (d.storage == ST_F16 ? 2 : 0);
     if (d.ndim == 2) {
         // Contracted plans run one-warp tiles of V = 8 cells per thread (bsize_x = 256) with
         // partial-sum stages; exact plans run the rotating-window kernel, V = 4, with W warps
@@ -388,7 +454,7 @@ int stencil_plan_create(stencil_plan *out, const stencil_desc *desc)
             if (d.exact && d.nx >= 512) p->W = 4;
         }
         if (!d.exact && d.force_by == 1) p->W = 0;   // in-place partial-row variant
-        if (!d.exact && !d.force_T && !d.force_vec && !d.force_bx && !d.force_by) {
+        if (!d.exact && !p->stor && !d.force_T && !d.force_vec && !d.force_bx && !d.force_by) {
             // contracted, nothing forced: the compiled (T, V, variant) the model rates best
             const Cand2D cands[] = {{4, 4, 1}, {8, 4, 1}, {12, 4, 1}, {4, 8, 1}, {6, 8, 1},
                                     {8, 8, 1}, {8, 8, 0}, {12, 4, 0}};
@@ -409,7 +475,7 @@ int stencil_plan_create(stencil_plan *out, const stencil_desc *desc)
         }
         const int want = d.force_T ? d.force_T : 8;
         p->T = kernel_T_for(p, want);
-        if (!d.exact && !d.force_T && !d.force_vec && !d.force_bx && !d.force_by) {
+        if (!d.exact && !p->stor && !d.force_T && !d.force_vec && !d.force_bx && !d.force_by) {
             // and the T the model rates best within that family
             double best = -1.0;
             for (int t : kTcand) {
@@ -428,7 +494,24 @@ int stencil_plan_create(stencil_plan *out, const stencil_desc *desc)
         if (p->T == 0 || (d.force_T && p->T != d.force_T)) rc = ST_ERR_UNSUPPORTED;
         PassCfg2D *c = nullptr;
         if (rc == ST_OK) rc = prepare2(p, p->T, &c);
-        if (rc == ST_OK) {
+        if (rc == ST_OK && p->stor) {
+            // coded grids: rows padded to 8 cells (16 bytes), codes per (row, tile column)
+            p->cx = 32 * p->V - 2 * ((p->T + 3) / 4 * 4);
+            p->ntx = (d.nx + p->cx - 1) / p->cx;
+            p->ld_q = ((long long)d.nx + 7) / 8 * 8;
+            const size_t qb = (size_t)p->ld_q * d.ny * 2, mb = (size_t)p->ntx * d.ny * sizeof(float2);
+            for (int b = 0; b < 2 && rc == ST_OK; b++) {
+                e = cudaMalloc(&p->q[b], qb);
+                if (e == cudaSuccess) e = cudaMalloc(&p->qm[b], mb);
+                if (e != cudaSuccess) rc = map_cuda(e);
+            }
+            if (rc == ST_OK && d.kind == ST_THERMAL) {
+                e = cudaMalloc(&p->qp, qb);
+                if (e == cudaSuccess) e = cudaMalloc(&p->qpm, mb);
+                if (e != cudaSuccess) rc = map_cuda(e);
+            }
+            p->scratch_bytes = 0;   // no float32 scratch: the coded grids take its place
+        } else if (rc == ST_OK) {
             p->ld_scratch = ((long long)d.nx + 31) / 32 * 32;
             p->scratch_bytes = (size_t)p->ld_scratch * d.ny * sizeof(float);
         }
@@ -445,13 +528,12 @@ int stencil_plan_create(stencil_plan *out, const stencil_desc *desc)
         if (rc == ST_OK) rc = prepare3(p, p->T, &c);
         p->scratch_bytes = (size_t)cells_of(d) * sizeof(float);
     }
-    if (rc == ST_OK) {
+    if (rc == ST_OK && p->scratch_bytes) {
         e = cudaMalloc(&p->scratch, p->scratch_bytes);
         if (e != cudaSuccess) rc = map_cuda(e);
     }
     if (rc != ST_OK) {
-        if (p->scratch) cudaFree(p->scratch);
-        delete p;
+        stencil_plan_destroy(p);
         return rc;
     }
     *out = p;
@@ -484,6 +566,26 @@ int stencil_run(stencil_plan p, const void *grid_in, void *grid_out, const void 
     const int T = p->T;
     const int passes = (steps + T - 1) / T;
     const int last = steps - T * (passes - 1);
+    if (p->stor) {
+        // 16-bit storage: code the field (and the power map), run every pass on the coded
+        // grids, decode into the output
+        e = lp_encode(p->stor, in, d.nx, p->q[0], p->ld_q, p->qm[0], d.nx, d.ny, p->cx, p->stream);
+        if (e == cudaSuccess && pw)
+            e = lp_encode(p->stor, pw, d.nx, p->qp, p->ld_q, p->qpm, d.nx, d.ny, p->cx, p->stream);
+        if (e != cudaSuccess) return map_cuda(e);
+        int cur = 0;
+        for (int i = 0; i < passes; i++) {
+            const int rc = run_pass2q(p, cur, 1 - cur, coeffs, (i == passes - 1) ? last : T);
+            if (rc != ST_OK) {
+                p->sticky = rc;
+                return rc;
+            }
+            cur = 1 - cur;
+        }
+        e = lp_decode(p->stor, p->q[cur], p->ld_q, p->qm[cur], out, d.nx, d.nx, d.ny, p->cx,
+                      p->stream);
+        return map_cuda(e);
+    }
     // buffer of pass i: the caller's output when (passes-1-i) is even, else the scratch grid;
     // in place with an odd pass count, pass 0 cannot write the input it reads, so every pass
     // shifts by one and a final copy brings the scratch result to the output.
@@ -586,6 +688,12 @@ int stencil_plan_destroy(stencil_plan p)
     if (p->ev_used) cudaStreamSynchronize(p->stream);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
     if (p->scratch) cudaFree(p->scratch);
+    for (int b = 0; b < 2; b++) {
+        if (p->q[b]) cudaFree(p->q[b]);
+        if (p->qm[b]) cudaFree(p->qm[b]);
+    }
+    if (p->qp) cudaFree(p->qp);
+    if (p->qpm) cudaFree(p->qpm);
     delete p;
     return ST_OK;
 }

@@ -21,9 +21,41 @@ struct Pass2D {
     // Hotspot sdc, Rx, Ry, Rz, amb, sdc*Ry (rounded once), -2*Ry (exact)
     float kf[7];
     int vec_in, vec_out, vec_pw;   // 1: rows start on 16-byte boundaries
+    // 16-bit storage (contracted kernel, stor != 0): raw grids, block codes per (row, tile)
+    int stor;                      // 0 float32, 1 bf16, 2 fp16
+    const void *qin;
+    void *qout;
+    const void *qpw;
+    const float2 *min_;
+    float2 *mout;
+    const float2 *mpw;
+    long long ld_q;                // row pitch of the 16-bit grids, cells (multiple of 8)
 };
 
-struct Shape2D { int kind, exact, T, V, W; };
+struct Shape2D { int kind, exact, T, V, W; int stor = 0; };
+
+// One pass over many 2D grids (contracted kernels): grids[g] describes grid g's pass (its
+// tile columns ntx, sizes, buffers, coefficients, tsteps); prefix[g] = sum of ntx*ny of the
+// grids before g (prefix[ngrids] = total_units).  Device pointers.
+struct BatchPass2D {
+    const Pass2D *grids;
+    const long long *prefix;
+    int ngrids;
+    long long total_units;
+    long long units_per_cta;
+    int ctas;
+};
+
+bool tb2d_batch_available(const Shape2D &s);
+cudaError_t tb2d_batch_prepare(const Shape2D &s, int *blocks_per_sm);
+cudaError_t tb2d_batch_launch(const Shape2D &s, const BatchPass2D &bp, cudaStream_t st);
+
+// Block codec of the 16-bit storage: one (offset, scale) per (row, tile column) of the tiling
+// with compute width cx; x = offset + scale * q, q in [-1, 1].
+cudaError_t lp_encode(int stor, const float *src, long long ld_src, void *dst, long long ld_q,
+                      float2 *meta, int nx, int ny, int cx, cudaStream_t st);
+cudaError_t lp_decode(int stor, const void *src, long long ld_q, const float2 *meta, float *dst,
+                      long long ld_dst, int nx, int ny, int cx, cudaStream_t st);
 
 bool tb2d_available(const Shape2D &s);
 int tb2d_block_threads(const Shape2D &s);

@@ -10,7 +10,9 @@ static const Tb2dEntry *tb2d_find(const Shape2D &s)
     if (s.kind < 0 || s.kind > 1) return nullptr;
     const Tb2dEntry *t = tabs[s.kind];
     for (int i = 0; i < ns[s.kind]; i++)
-        if (t[i].exact == s.exact && t[i].T == s.T && t[i].V == s.V && t[i].W == s.W) return &t[i];
+        if (t[i].exact == s.exact && t[i].T == s.T && t[i].V == s.V && t[i].W == s.W &&
+            t[i].stor == s.stor)
+            return &t[i];
     return nullptr;
 }
 

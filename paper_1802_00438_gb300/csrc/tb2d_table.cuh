@@ -9,21 +9,26 @@ struct Tb2dEntry {
     int kind, exact, T, V, W;
     const void *fn;
     size_t smem;
+    int stor;   // 0 float32 grids; 1 bf16, 2 fp16 block-coded grids
 };
 
 #define STN_TB2_ENTRY(K, E, T_, V_, W_)                                                      \
     { K, E, T_, V_, W_, reinterpret_cast<const void *>(&k_tb2d<K, (E != 0), T_, V_, W_>),  \
-      TB2<K, (E != 0), T_, V_, W_>::SMEM }
+      TB2<K, (E != 0), T_, V_, W_>::SMEM, 0 }
 
 // contracted path: one-warp blocks (W = 1), partial-sum stages
 // W = 1: partial rows alternate between two register arrays (two-row unroll);
 // W = 0 (a marker, still one warp): partial rows updated in place, no unroll
 #define STN_TB2F_ENTRY(K, T_, V_)                                                            \
-    { K, 0, T_, V_, 1, reinterpret_cast<const void *>(&k_tb2f<K, T_, V_, true>),           \
-      TB2F<K, T_, V_>::SMEM }
+    { K, 0, T_, V_, 1, reinterpret_cast<const void *>(&k_tb2f<K, T_, V_, true, 0>),        \
+      TB2F<K, T_, V_>::SMEM, 0 }
 #define STN_TB2F1_ENTRY(K, T_, V_)                                                           \
-    { K, 0, T_, V_, 0, reinterpret_cast<const void *>(&k_tb2f<K, T_, V_, false>),          \
-      TB2F<K, T_, V_>::SMEM }
+    { K, 0, T_, V_, 0, reinterpret_cast<const void *>(&k_tb2f<K, T_, V_, false, 0>),       \
+      TB2F<K, T_, V_>::SMEM, 0 }
+// 16-bit block-coded storage (S = 1 bf16, 2 fp16), two-row unroll
+#define STN_TB2FQ_ENTRY(K, T_, V_, S)                                                        \
+    { K, 0, T_, V_, 1, reinterpret_cast<const void *>(&k_tb2f<K, T_, V_, true, S>),        \
+      TB2F<K, T_, V_, S>::SMEM, S }
 
 extern const Tb2dEntry tb2d_table_diff[];
 extern const int tb2d_table_diff_n;

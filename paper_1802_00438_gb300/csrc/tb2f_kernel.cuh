@@ -31,11 +31,16 @@
 // partial rows: its three time-0 rows are all in the field ring, and it evaluates the update
 // from them directly.
 #pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "tb2d_kernel.cuh"
 
 namespace stn {
 
-template <int KIND, int T, int V>
+enum { STOR_F32 = 0, STOR_BF16 = 1, STOR_F16 = 2 };
+
+template <int KIND, int T, int V, int STOR = STOR_F32>
 struct TB2F {
     static constexpr int BX = 32 * V;
     static constexpr int H = (T + 3) / 4 * 4;
@@ -48,7 +53,12 @@ struct TB2F {
     static constexpr int NBPX = (KIND == KTHERM) ? (NBP + PW - 1) : 0;  // incl. mirror
     static constexpr int NS = T > 1 ? T - 1 : 1;                    // partial-sum stages
     static constexpr int ROWB = BX * 4;                             // bytes per ring row
-    static constexpr size_t SMEM = (size_t)(NBF + NBPX) * ROWB;
+    // 16-bit storage: rows arrive raw (32-byte header of block codes + 2 bytes per cell) in a
+    // staging ring of PF+1 rows per input and are decoded into the float rings once
+    static constexpr int NBR = (STOR != STOR_F32) ? PF + 1 : 0;
+    static constexpr int RAWB = 32 + 2 * BX;
+    static constexpr size_t SMEM = (size_t)(NBF + NBPX) * ROWB +
+                                   (size_t)NBR * RAWB * (KIND == KTHERM ? 2 : 1);
     static_assert(V % 4 == 0, "V must be a multiple of 4");
     static_assert(CX > 0, "tile narrower than its halos");
 };
@@ -96,6 +106,56 @@ __device__ __forceinline__ void cp4(uint32_t dst, const void *src, int nbytes)
                  : "memory");
 }
 
+__device__ __forceinline__ void cp8(uint32_t dst, const void *src, int nbytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src), "r"(nbytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint2 lds64u(uint32_t a)
+{
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];\n" : "=r"(v.x), "=r"(v.y) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ void sts128(uint32_t a, float x, float y, float z, float w)
+{
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(a), "f"(x), "f"(y), "f"(z),
+                 "f"(w)
+                 : "memory");
+}
+
+// 16-bit codes: bf16 / fp16 bit patterns of q in [-1, 1]
+template <int STOR>
+__device__ __forceinline__ float q2f(unsigned q)
+{
+    if (STOR == STOR_BF16) return __uint_as_float(q << 16);
+    return __half2float(__ushort_as_half((unsigned short)q));
+}
+
+template <int STOR>
+__device__ __forceinline__ unsigned f2q(float x)
+{
+    if (STOR == STOR_BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    return __half_as_ushort(__float2half_rn(x));
+}
+
+// warp-wide float min / max in one instruction (sm_100 family)
+__device__ __forceinline__ float warp_min(float v)
+{
+    float r;
+    asm volatile("redux.sync.min.f32 %0, %1, 0xffffffff;\n" : "=f"(r) : "f"(v));
+    return r;
+}
+
+__device__ __forceinline__ float warp_max(float v)
+{
+    float r;
+    asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;\n" : "=f"(r) : "f"(v));
+    return r;
+}
+
 struct CtxF {
     const float *__restrict__ in;
     float *__restrict__ out;
@@ -112,64 +172,16 @@ struct CtxF {
     int lane;
     uint32_t o4;           // my first cell's byte offset in a ring row
     uint32_t ow4, oe4;     // byte offsets of the cells left and right of mine (clamped)
+    // 16-bit storage
+    uint32_t sRF, sRP;     // staging rings (raw field / raw power rows)
+    const uint16_t *qin, *qpw;
+    uint16_t *qout;
+    const float2 *min_, *mpw;   // block codes (offset, scale) per (row, tile column)
+    float2 *mout;
+    long long ld_q;        // row pitch of 16-bit grids (cells)
+    int ntx, tx;           // tile columns; my tile column
+    int msel;              // which of the three blocks of a loaded row my cells belong to
 };
-
-// Issue the async copies of tile row y into field slot fs and power slots ps (and ps2 >= 0:
-// the mirror slot).
-template <int KIND, int V>
-__device__ __forceinline__ void tbf_load(const CtxF &c, int y, int fs, int ps, int ps2)
-{
-    constexpr int BX = 32 * V, ROWB = BX * 4;
-    const float *srcF = c.in + (long long)y * c.ld_in;
-    const float *srcP = (KIND == KTHERM) ? c.pw + (long long)y * c.ld_pw : nullptr;
-#pragma unroll
-    for (int qq = 0; qq < V / 4; qq++) {
-        const int q = c.lane + qq * 32;
-        const int x = c.x0 + 4 * q;
-        const uint32_t off = 16u * q;
-        const int nb16 = (x >= 0 && x < c.nx) ? min(16, 4 * (c.nx - x)) : 0;
-        if (c.vec_in) {
-            cp16(c.sF + fs * ROWB + off, nb16 ? srcF + x : srcF, nb16);
-        } else {
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const int xx = x + j;
-                const int nb = (xx >= 0 && xx < c.nx) ? 4 : 0;
-                cp4(c.sF + fs * ROWB + off + 4 * j, nb ? srcF + xx : srcF, nb);
-            }
-        }
-        if (KIND == KTHERM) {
-            if (c.vec_pw) {
-                cp16(c.sP + ps * ROWB + off, nb16 ? srcP + x : srcP, nb16);
-                if (ps2 >= 0) cp16(c.sP + ps2 * ROWB + off, nb16 ? srcP + x : srcP, nb16);
-            } else {
-#pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const int xx = x + j;
-                    const int nb = (xx >= 0 && xx < c.nx) ? 4 : 0;
-                    cp4(c.sP + ps * ROWB + off + 4 * j, nb ? srcP + xx : srcP, nb);
-                    if (ps2 >= 0) cp4(c.sP + ps2 * ROWB + off + 4 * j, nb ? srcP + xx : srcP, nb);
-                }
-            }
-        }
-    }
-}
-
-template <int V>
-__device__ __forceinline__ void tbf_store(const CtxF &c, int r, const float (&v)[V])
-{
-    float *dst = c.out + (long long)r * c.ld_out + c.xt;
-    if (c.st_full) {
-#pragma unroll
-        for (int q = 0; q < V / 4; q++)
-            *reinterpret_cast<float4 *>(dst + 4 * q) =
-                make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-    } else if (c.st_any) {
-#pragma unroll
-        for (int j = 0; j < V; j++)
-            if (j >= c.st_lo && j < c.st_hi) dst[j] = v[j];
-    }
-}
 
 template <int V, bool EDGE>
 __device__ __forceinline__ void nbf(const CtxF &c, const float (&d)[V], float w_in, float e_in,
@@ -274,17 +286,25 @@ struct RowF {
     int rf, rp;             // ring slots of field row i / of power row i
     int i_store;            // first iteration that stores a row
     int i_load_end;         // iterations i < i_load_end queue row i+PF
+    // 16-bit storage
+    const uint16_t *qF, *qP;     // raw rows of the next row to load (at column x0)
+    const float2 *mF, *mP;       // block-code rows of the next row to load
+    uint16_t *qO;                // raw output at my first cell of the next row to store
+    float2 *mO;                  // block-code row of the next row to store
+    int rr;                      // staging slot of row i
+    int nbr;                     // my raw bytes inside the grid (0 .. 2V), colr: my column
+    int colr;
 };
 
 // One row iteration.  PH selects which of A/B holds P (PH = 0: A) for every stage.
-template <int KIND, int T, int V, int MODE, int PH, bool SWAP>
+template <int KIND, int T, int V, int MODE, int PH, bool SWAP, int STOR>
 __device__ __forceinline__ void tbf_iter(const CtxF &c, const CoefF &k,
                                          float (&A)[TB2F<KIND, T, V>::NS][V],
                                          float (&B)[TB2F<KIND, T, V>::NS][V], int i,
                                          uint32_t fu, uint32_t fm, uint32_t fd, uint32_t pbase,
-                                         float *gO, bool store)
+                                         float *gO, const RowF &r, bool store)
 {
-    using C = TB2F<KIND, T, V>;
+    using C = TB2F<KIND, T, V, STOR>;
     constexpr bool ED = MODE != MODE_PLAIN;
     const int R0 = c.y_start + i;
     float d[V], out[V];
@@ -322,24 +342,96 @@ __device__ __forceinline__ void tbf_iter(const CtxF &c, const CoefF &k,
                            pbase - s * C::ROWB + c.o4, pbase - (s - 1) * C::ROWB + c.o4, out);
     }
     if (store) {
-        if (c.st_full) {
+        if (STOR == STOR_F32) {
+            if (c.st_full) {
 #pragma unroll
-            for (int q = 0; q < V / 4; q++)
-                *reinterpret_cast<float4 *>(gO + 4 * q) =
-                    make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
-        } else if (c.st_any) {
+                for (int q = 0; q < V / 4; q++)
+                    *reinterpret_cast<float4 *>(gO + 4 * q) =
+                        make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
+            } else if (c.st_any) {
+#pragma unroll
+                for (int j = 0; j < V; j++)
+                    if (j >= c.st_lo && j < c.st_hi) gO[j] = out[j];
+            }
+        } else {
+            // encode the row segment of this tile: offset = mid-range, scale = half-range of the
+            // stored cells, q = (x - offset) / scale in [-1, 1] rounded to the 16-bit format
+            float lo = __int_as_float(0x7f800000), hi = -lo;
 #pragma unroll
             for (int j = 0; j < V; j++)
-                if (j >= c.st_lo && j < c.st_hi) gO[j] = out[j];
+                if (j >= c.st_lo && j < c.st_hi) {
+                    lo = fminf(lo, out[j]);
+                    hi = fmaxf(hi, out[j]);
+                }
+            lo = warp_min(lo);
+            hi = warp_max(hi);
+            const float mid = 0.5f * (lo + hi);
+            float sc = 0.5f * (hi - lo);
+            sc = (sc > 0.f) ? sc : 1.f;
+            const float inv = __frcp_rn(sc);
+            // |x - mid| * inv <= 1 + 3 * 2^-24 for the block's own cells, which rounds to 1 in
+            // either 16-bit format: no clamp needed
+            unsigned q[V];
+#pragma unroll
+            for (int j = 0; j < V; j++) q[j] = f2q<STOR>((out[j] - mid) * inv);
+            if (c.st_full) {
+#pragma unroll
+                for (int t = 0; t < V / 4; t++)
+                    *reinterpret_cast<uint2 *>(r.qO + 4 * t) =
+                        make_uint2(q[4 * t] | (q[4 * t + 1] << 16), q[4 * t + 2] | (q[4 * t + 3] << 16));
+            } else if (c.st_any) {
+#pragma unroll
+                for (int j = 0; j < V; j++)
+                    if (j >= c.st_lo && j < c.st_hi) r.qO[j] = (uint16_t)q[j];
+            }
+            if (c.lane == 0) r.mO[c.tx] = make_float2(mid, sc);
         }
     }
 }
 
-// Queue tile row (row pointers in r) into field slot lf and power slot lp (plus its mirror).
-template <int KIND, int T, int V>
-__device__ __forceinline__ void tbf_queue(const CtxF &c, const RowF &r, int lf, int lp)
+// Decode my V cells of a staged raw row (header: codes of the blocks tx-1, tx, tx+1) into a
+// float ring row (and into its mirror when mirror != 0).
+template <int V, int STOR>
+__device__ __forceinline__ void tbf_decode(const CtxF &c, uint32_t raw, uint32_t dst, uint32_t mirror)
 {
-    using C = TB2F<KIND, T, V>;
+    const uint2 cw = lds64u(raw + 8u * c.msel);
+    const float mid = __uint_as_float(cw.x), sc = __uint_as_float(cw.y);
+#pragma unroll
+    for (int t = 0; t < V / 4; t++) {
+        const uint2 w = lds64u(raw + 32u + 2u * V * c.lane + 8u * t);
+        const float x0 = __fmaf_rn(sc, q2f<STOR>(w.x & 0xffffu), mid);
+        const float x1 = __fmaf_rn(sc, q2f<STOR>(w.x >> 16), mid);
+        const float x2 = __fmaf_rn(sc, q2f<STOR>(w.y & 0xffffu), mid);
+        const float x3 = __fmaf_rn(sc, q2f<STOR>(w.y >> 16), mid);
+        sts128(dst + c.o4 + 16u * t, x0, x1, x2, x3);
+        if (mirror) sts128(mirror + c.o4 + 16u * t, x0, x1, x2, x3);
+    }
+}
+
+// Queue tile row (row pointers in r) into field slot lf and power slot lp (plus its mirror);
+// with 16-bit storage, into staging slot lr instead.
+template <int KIND, int T, int V, int STOR>
+__device__ __forceinline__ void tbf_queue(const CtxF &c, const RowF &r, int lf, int lp, int lr)
+{
+    using C = TB2F<KIND, T, V, STOR>;
+    if (STOR != STOR_F32) {
+#pragma unroll
+        for (int in = 0; in < (KIND == KTHERM ? 2 : 1); in++) {
+            const uint32_t dr = (in == 0 ? c.sRF : c.sRP) + lr * C::RAWB;
+            const uint16_t *src = in == 0 ? r.qF : r.qP;
+            const float2 *m = in == 0 ? r.mF : r.mP;
+#pragma unroll
+            for (int t = 0; t < V / 4; t++) {
+                const int nb = max(0, min(8, r.nbr - 8 * t));
+                cp8(dr + 32u + 2u * V * c.lane + 8u * t, nb ? src + r.colr + 4 * t : src, nb);
+            }
+            if (c.lane < 6) {
+                const int b = min(max(c.tx - 1 + (c.lane >> 1), 0), c.ntx - 1);
+                cp4(dr + 4u * c.lane, reinterpret_cast<const float *>(m + b) + (c.lane & 1), 4);
+            }
+        }
+        return;
+    }
     const uint32_t df = c.sF + lf * C::ROWB + 16u * c.lane;
     const uint32_t dp = c.sP + lp * C::ROWB + 16u * c.lane;
     if (c.vec_in && (KIND == KDIFF || c.vec_pw)) {
@@ -368,14 +460,21 @@ __device__ __forceinline__ void tbf_queue(const CtxF &c, const RowF &r, int lf, 
 }
 
 // One row: wait for row i, run the stages, queue row i+PF, advance pointers and rings.
-template <int KIND, int T, int V, int MODE, int PH, bool SWAP>
+template <int KIND, int T, int V, int MODE, int PH, bool SWAP, int STOR>
 __device__ __forceinline__ void tbf_step(const CtxF &c, const CoefF &k,
                                          float (&A)[TB2F<KIND, T, V>::NS][V],
                                          float (&B)[TB2F<KIND, T, V>::NS][V], int i, RowF &r)
 {
-    using C = TB2F<KIND, T, V>;
+    using C = TB2F<KIND, T, V, STOR>;
     cp_async_wait<C::PF - 1>();   // row i has landed
     __syncwarp();
+    if (STOR != STOR_F32) {       // decode row i into the float rings
+        tbf_decode<V, STOR>(c, c.sRF + r.rr * C::RAWB, c.sF + r.rf * C::ROWB, 0u);
+        if (KIND == KTHERM)
+            tbf_decode<V, STOR>(c, c.sRP + r.rr * C::RAWB, c.sP + r.rp * C::ROWB,
+                                r.rp < C::PW - 1 ? c.sP + (C::NBP + r.rp) * C::ROWB : 0u);
+        __syncwarp();
+    }
     // field ring slots of rows i-2, i-1, i (rows above or below the grid clamp to its edge)
     int su = r.rf - 2, sm = r.rf - 1, sd = r.rf;
     su += (su < 0) ? C::NBF : 0;
@@ -387,9 +486,16 @@ __device__ __forceinline__ void tbf_step(const CtxF &c, const CoefF &k,
     }
     const uint32_t pbase = c.sP + ((KIND == KTHERM && r.rp < C::PW - 1) ? C::NBP + r.rp : r.rp) * C::ROWB;
     const bool store = i >= r.i_store;
-    tbf_iter<KIND, T, V, MODE, PH, SWAP>(c, k, A, B, i, c.sF + su * C::ROWB, c.sF + sm * C::ROWB,
-                                   c.sF + sd * C::ROWB, pbase, r.gO, store);
-    if (store) r.gO += c.ld_out;
+    tbf_iter<KIND, T, V, MODE, PH, SWAP, STOR>(c, k, A, B, i, c.sF + su * C::ROWB,
+                                               c.sF + sm * C::ROWB, c.sF + sd * C::ROWB, pbase,
+                                               r.gO, r, store);
+    if (store) {
+        if (STOR == STOR_F32) r.gO += c.ld_out;
+        else {
+            r.qO += c.ld_q;
+            r.mO += c.ntx;
+        }
+    }
     __syncwarp();
     int lf = r.rf + C::PF;
     lf -= (lf >= C::NBF) ? C::NBF : 0;
@@ -398,30 +504,48 @@ __device__ __forceinline__ void tbf_step(const CtxF &c, const CoefF &k,
         lp = r.rp + C::PF;
         lp -= (lp >= C::NBP) ? C::NBP : 0;
     }
+    int lr = 0;
+    if (STOR != STOR_F32) {
+        lr = r.rr + C::PF;
+        lr -= (lr >= C::NBR) ? C::NBR : 0;
+    }
     if (i < r.i_load_end) {
-        tbf_queue<KIND, T, V>(c, r, lf, lp);
-        r.gF += c.ld_in;
-        if (KIND == KTHERM) r.gP += c.ld_pw;
+        tbf_queue<KIND, T, V, STOR>(c, r, lf, lp, lr);
+        if (STOR == STOR_F32) {
+            r.gF += c.ld_in;
+            if (KIND == KTHERM) r.gP += c.ld_pw;
+        } else {
+            r.qF += c.ld_q;
+            r.mF += c.ntx;
+            if (KIND == KTHERM) {
+                r.qP += c.ld_q;
+                r.mP += c.ntx;
+            }
+        }
     }
     cp_async_commit();
     r.rf = (r.rf + 1 == C::NBF) ? 0 : r.rf + 1;
     if (KIND == KTHERM) r.rp = (r.rp + 1 == C::NBP) ? 0 : r.rp + 1;
+    if (STOR != STOR_F32) r.rr = (r.rr + 1 == C::NBR) ? 0 : r.rr + 1;
 }
 
-template <int KIND, int T, int V, int MODE, bool SWAP>
+template <int KIND, int T, int V, int MODE, bool SWAP, int STOR>
 __device__ __forceinline__ void tbf_step_rt(const CtxF &c, const CoefF &k,
                                             float (&A)[TB2F<KIND, T, V>::NS][V],
                                             float (&B)[TB2F<KIND, T, V>::NS][V], int i, RowF &r)
 {
-    if (SWAP && (i & 1)) tbf_step<KIND, T, V, MODE, 1, SWAP>(c, k, A, B, i, r);
-    else tbf_step<KIND, T, V, MODE, 0, SWAP>(c, k, A, B, i, r);
+    if (SWAP && (i & 1)) tbf_step<KIND, T, V, MODE, 1, SWAP, STOR>(c, k, A, B, i, r);
+    else tbf_step<KIND, T, V, MODE, 0, SWAP, STOR>(c, k, A, B, i, r);
 }
 
-template <int KIND, int T, int V, bool SWAP>
-__global__ void __launch_bounds__(32) k_tb2f(const Pass2D p)
+// Work units [f, fend) of one grid's pass: unit f = (tile column f / ny, row f % ny); a block
+// walks them as segments of consecutive rows of one tile column.
+template <int KIND, int T, int V, bool SWAP, int STOR>
+__device__ __forceinline__ void tbf_range(const Pass2D &p, long long f, const long long fend,
+                                          float (&A)[TB2F<KIND, T, V>::NS][V],
+                                          float (&B)[TB2F<KIND, T, V>::NS][V], float *smem)
 {
-    using C = TB2F<KIND, T, V>;
-    extern __shared__ __align__(16) float smem[];
+    using C = TB2F<KIND, T, V, STOR>;
     CtxF c;
     c.in = p.in;
     c.out = p.out;
@@ -431,6 +555,16 @@ __global__ void __launch_bounds__(32) k_tb2f(const Pass2D p)
     c.ld_pw = p.ld_pw;
     c.sF = smem_u32(smem);
     c.sP = c.sF + C::NBF * C::ROWB;
+    c.sRF = c.sP + C::NBPX * C::ROWB;
+    c.sRP = c.sRF + C::NBR * C::RAWB;
+    c.qin = static_cast<const uint16_t *>(p.qin);
+    c.qpw = static_cast<const uint16_t *>(p.qpw);
+    c.qout = static_cast<uint16_t *>(p.qout);
+    c.min_ = p.min_;
+    c.mpw = p.mpw;
+    c.mout = p.mout;
+    c.ld_q = p.ld_q;
+    c.ntx = p.ntx;
     c.nx = p.nx;
     c.ny = p.ny;
     c.tsteps = p.tsteps;
@@ -446,14 +580,6 @@ __global__ void __launch_bounds__(32) k_tb2f(const Pass2D p)
     k.a5 = p.kf[5];   // Hotspot: sdc * Ry
     k.a6 = p.kf[6];   // Hotspot: -2 Ry
 
-    float A[C::NS][V], B[C::NS][V];
-#pragma unroll
-    for (int s = 0; s < C::NS; s++)
-#pragma unroll
-        for (int j = 0; j < V; j++) A[s][j] = B[s][j] = 0.f;
-
-    long long f = (long long)blockIdx.x * p.rows_per_cta;
-    const long long fend = min(f + p.rows_per_cta, p.total_rows);
     while (f < fend) {
         const int tx = (int)(f / p.ny);
         const int s0 = (int)(f - (long long)tx * p.ny);
@@ -487,6 +613,19 @@ __global__ void __launch_bounds__(32) k_tb2f(const Pass2D p)
             r.nbq[q] = (x >= 0 && x < c.nx) ? min(16, 4 * (c.nx - x)) : 0;
             r.colq[q] = r.nbq[q] ? x : 0;
         }
+        c.tx = tx;
+        c.msel = (c.xt < tx * C::CX) ? 0 : ((c.xt >= (tx + 1) * C::CX) ? 2 : 1);
+        if (STOR != STOR_F32) {
+            r.qF = c.qin + (long long)c.y_start * c.ld_q;
+            r.mF = c.min_ + (long long)c.y_start * c.ntx;
+            r.qP = (KIND == KTHERM) ? c.qpw + (long long)c.y_start * c.ld_q : nullptr;
+            r.mP = (KIND == KTHERM) ? c.mpw + (long long)c.y_start * c.ntx : nullptr;
+            r.qO = c.qout + (long long)s0 * c.ld_q + c.xt;
+            r.mO = c.mout + (long long)s0 * c.ntx;
+            r.rr = 0;
+            r.colr = (c.xt >= 0 && c.xt < c.nx) ? c.xt : 0;
+            r.nbr = (c.xt >= 0 && c.xt < c.nx) ? 2 * min(V, c.nx - c.xt) : 0;
+        }
         r.gF = c.in + (long long)c.y_start * c.ld_in;
         r.gP = (KIND == KTHERM) ? c.pw + (long long)c.y_start * c.ld_pw : nullptr;
         r.rf = 0;
@@ -500,9 +639,18 @@ __global__ void __launch_bounds__(32) k_tb2f(const Pass2D p)
 #pragma unroll 1
         for (int j = 0; j < C::PF; j++) {
             if (c.y_start + j <= c.last_row) {
-                tbf_queue<KIND, T, V>(c, r, j, (KIND == KTHERM) ? j : 0);
-                r.gF += c.ld_in;
-                if (KIND == KTHERM) r.gP += c.ld_pw;
+                tbf_queue<KIND, T, V, STOR>(c, r, j, (KIND == KTHERM) ? j : 0, j);
+                if (STOR == STOR_F32) {
+                    r.gF += c.ld_in;
+                    if (KIND == KTHERM) r.gP += c.ld_pw;
+                } else {
+                    r.qF += c.ld_q;
+                    r.mF += c.ntx;
+                    if (KIND == KTHERM) {
+                        r.qP += c.ld_q;
+                        r.mP += c.ntx;
+                    }
+                }
             }
             cp_async_commit();
         }
@@ -516,39 +664,81 @@ __global__ void __launch_bounds__(32) k_tb2f(const Pass2D p)
         const int i_b = partial ? n_it : max(i_a, min(n_it, c.ny - 1 - c.y_start));
         int i = 0;
 #pragma unroll 1
-        for (; i < i_a; i++) tbf_step_rt<KIND, T, V, MODE_SPECIAL, SWAP>(c, k, A, B, i, r);
+        for (; i < i_a; i++) tbf_step_rt<KIND, T, V, MODE_SPECIAL, SWAP, STOR>(c, k, A, B, i, r);
         if (SWAP) {
             if (i < i_b && (i & 1)) {
-                if (c.edge) tbf_step<KIND, T, V, MODE_EDGE, 1, SWAP>(c, k, A, B, i, r);
-                else tbf_step<KIND, T, V, MODE_PLAIN, 1, SWAP>(c, k, A, B, i, r);
+                if (c.edge) tbf_step<KIND, T, V, MODE_EDGE, 1, SWAP, STOR>(c, k, A, B, i, r);
+                else tbf_step<KIND, T, V, MODE_PLAIN, 1, SWAP, STOR>(c, k, A, B, i, r);
                 i++;
             }
             if (c.edge) {
 #pragma unroll 1
                 for (; i + 1 < i_b; i += 2) {
-                    tbf_step<KIND, T, V, MODE_EDGE, 0, SWAP>(c, k, A, B, i, r);
-                    tbf_step<KIND, T, V, MODE_EDGE, 1, SWAP>(c, k, A, B, i + 1, r);
+                    tbf_step<KIND, T, V, MODE_EDGE, 0, SWAP, STOR>(c, k, A, B, i, r);
+                    tbf_step<KIND, T, V, MODE_EDGE, 1, SWAP, STOR>(c, k, A, B, i + 1, r);
                 }
             } else {
 #pragma unroll 1
                 for (; i + 1 < i_b; i += 2) {
-                    tbf_step<KIND, T, V, MODE_PLAIN, 0, SWAP>(c, k, A, B, i, r);
-                    tbf_step<KIND, T, V, MODE_PLAIN, 1, SWAP>(c, k, A, B, i + 1, r);
+                    tbf_step<KIND, T, V, MODE_PLAIN, 0, SWAP, STOR>(c, k, A, B, i, r);
+                    tbf_step<KIND, T, V, MODE_PLAIN, 1, SWAP, STOR>(c, k, A, B, i + 1, r);
                 }
             }
         } else {
             if (c.edge) {
 #pragma unroll 1
-                for (; i < i_b; i++) tbf_step<KIND, T, V, MODE_EDGE, 0, SWAP>(c, k, A, B, i, r);
+                for (; i < i_b; i++) tbf_step<KIND, T, V, MODE_EDGE, 0, SWAP, STOR>(c, k, A, B, i, r);
             } else {
 #pragma unroll 1
-                for (; i < i_b; i++) tbf_step<KIND, T, V, MODE_PLAIN, 0, SWAP>(c, k, A, B, i, r);
+                for (; i < i_b; i++) tbf_step<KIND, T, V, MODE_PLAIN, 0, SWAP, STOR>(c, k, A, B, i, r);
             }
         }
 #pragma unroll 1
-        for (; i < n_it; i++) tbf_step_rt<KIND, T, V, MODE_SPECIAL, SWAP>(c, k, A, B, i, r);
+        for (; i < n_it; i++) tbf_step_rt<KIND, T, V, MODE_SPECIAL, SWAP, STOR>(c, k, A, B, i, r);
         cp_async_wait<0>();
         __syncwarp();
+    }
+}
+
+
+template <int KIND, int T, int V, bool SWAP, int STOR>
+__global__ void __launch_bounds__(32) k_tb2f(const Pass2D p)
+{
+    using C = TB2F<KIND, T, V, STOR>;
+    extern __shared__ __align__(16) float smem[];
+    float A[C::NS][V], B[C::NS][V];
+#pragma unroll
+    for (int s = 0; s < C::NS; s++)
+#pragma unroll
+        for (int j = 0; j < V; j++) A[s][j] = B[s][j] = 0.f;
+    const long long f = (long long)blockIdx.x * p.rows_per_cta;
+    tbf_range<KIND, T, V, SWAP, STOR>(p, f, min(f + p.rows_per_cta, p.total_rows), A, B, smem);
+}
+
+// Many grids in one launch: a work queue over the concatenated (tile column, row) units of all
+// grids (prefix[g] = units before grid g), split evenly over the blocks, so every block gets the
+// same number of rows whatever the grids' sizes.  Each grid carries its own sizes, buffers,
+// coefficients and step count for this pass.
+template <int KIND, int T, int V, bool SWAP>
+__global__ void __launch_bounds__(32) k_tb2f_batch(const BatchPass2D bp)
+{
+    using C = TB2F<KIND, T, V, 0>;
+    extern __shared__ __align__(16) float smem[];
+    float A[C::NS][V], B[C::NS][V];
+#pragma unroll
+    for (int s = 0; s < C::NS; s++)
+#pragma unroll
+        for (int j = 0; j < V; j++) A[s][j] = B[s][j] = 0.f;
+    long long f = (long long)blockIdx.x * bp.units_per_cta;
+    const long long fend = min(f + bp.units_per_cta, bp.total_units);
+    int g = 0;
+    while (f < fend) {
+        while (bp.prefix[g + 1] <= f) g++;
+        const Pass2D pg = bp.grids[g];
+        const long long lo = f - bp.prefix[g];
+        const long long hi = min(fend, bp.prefix[g + 1]) - bp.prefix[g];
+        tbf_range<KIND, T, V, SWAP, 0>(pg, lo, hi, A, B, smem);
+        f += hi - lo;
     }
 }
 
