@@ -38,6 +38,8 @@ import synth  # noqa: E402
 FLOPS = {(0, 2): 9, (0, 3): 13, (1, 2): 15, (1, 3): 17}
 BYTES = {0: 8, 1: 12}
 
+BATCH = "batch64"   # 64 2D grids of uneven sizes and step counts in one graph launch
+
 WORKLOADS = {
     "thermal2d_16384": lambda: synth.c2_thermal2d(),
     "diffusion2d_1024": lambda: synth.c1_diffusion2d(),
@@ -217,12 +219,144 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def bench_batch(args):
+    """64 grids (sides log-uniform in [256, 4096], steps uniform in {50..500}, kinds
+    alternating): one step = one replay of the batch's CUDA graph."""
+    ws = synth.c5a_batch()
+    cells_steps = sum(w.cells * w.steps for w in ws)
+    if args.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        import oracle
+        oracle.build()
+        cores = len(os.sched_getaffinity(0))
+        oracle.set_threads(cores)
+        frac = 1.0 / 40          # each grid for 1/40 of its steps (at least one)
+        t0 = time.perf_counter()
+        done = 0
+        for _ in range(args.steps):
+            for w in ws:
+                s = max(1, int(w.steps * frac))
+                oracle.run(w.kind, w.u0, w.coef, s, w.power)
+                done += w.cells * s
+        t = time.perf_counter() - t0
+        v = done / t / 1e9
+        print(json.dumps({"impl": "reference", "metric": "stencil GCell/s & GFLOP/s vs roofline",
+                          "value": v, "unit": "GCell/s", "n_gpus": args.gpus, "steps": args.steps,
+                          "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
+                          "data": "synthetic", "config": {"workload": BATCH},
+                          "cpu_baseline": {"value": v, "unit": "GCell/s", "cores": cores,
+                                           "kind": "oracle",
+                                           "sample": "all 64 grids, 1/40 of each grid's steps"},
+                          "e2e": {"value": v, "unit": "GCell/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
+        return
+    import torch
+    import paper_1802_00438_gb300 as st
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    items = []
+    for w in ws:
+        u = torch.from_numpy(w.u0).to(dev)
+        o = torch.empty_like(u)
+        p = None if w.power is None else torch.from_numpy(w.power).to(dev)
+        items.append({"kind": w.kind, "nx": w.nx, "ny": w.ny, "steps": w.steps, "grid_in": u,
+                      "grid_out": o, "power": p, "coeffs": w.coef})
+    torch.cuda.synchronize()
+    b = st.Batch(items, stream=stream.cuda_stream)
+    for _ in range(args.warmup):
+        b.run()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            b.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * cells_steps * args.steps / (ms * 1e-3) / 1e9
+    # roofline of the mix: sum over grids of cells*steps / R_g(T_g), R = min(ALU, HBM*T/bytes)
+    peaks, src = load_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu = fp32_peak_tflops(sms, float(peaks.get("sm_max_mhz", 2070.0))) * 1e12
+    hbm = float(peaks["hbm_gbs"]) * 1e9
+    ideal = 0.0
+    bytes_moved = 0.0
+    for i, w in enumerate(ws):
+        gi = b.grid_info(i)
+        R = min(alu / FLOPS[(w.kind, 2)], hbm * gi["T"] / BYTES[w.kind])
+        ideal += w.cells * w.steps / R
+        bytes_moved += w.cells * BYTES[w.kind] * gi["passes"]
+    per_step_s = ms * 1e-3 / args.steps
+    gbs = bytes_moved / per_step_s / 1e9
+    roof = {"bound": "hbm", "achieved": gbs, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+            "frac": gbs / float(peaks["hbm_gbs"]), "traffic": None,
+            "frac_of_cell_roofline": ideal / per_step_s,
+            "note": "mix of 64 grids: achieved = algorithmic bytes of all passes / step time; "
+                    "frac_of_cell_roofline = sum_g cells*steps/R_g(T_g) / step time"}
+    # end to end: host inputs in, results out, through the same batch
+    h_in = [torch.from_numpy(w.u0).pin_memory() for w in ws]
+    h_out = [torch.empty_like(h).pin_memory() for h in h_in]
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        a0.record(stream)
+        for _ in range(args.steps):
+            for it, h in zip(items, h_in):
+                it["grid_in"].copy_(h, non_blocking=True)
+            b.run()
+            for it, h in zip(items, h_out):
+                h.copy_(it["grid_out"], non_blocking=True)
+        a1.record(stream)
+    torch.cuda.synchronize()
+    ems = a0.elapsed_time(a1)
+    nb = sum(w.u0.nbytes for w in ws)
+    e2e = {"value": world * cells_steps * args.steps / (ems * 1e-3) / 1e9, "unit": "GCell/s",
+           "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
+    if rank == 0:
+        tv = {}
+        for i in range(len(ws)):
+            gi = b.grid_info(i)
+            k = f"T{gi['T']}V{gi['vec']}"
+            tv[k] = tv.get(k, 0) + 1
+        print(json.dumps({"metric": "stencil GCell/s & GFLOP/s vs roofline", "value": value,
+                          "unit": "GCell/s", "n_gpus": world, "steps": args.steps,
+                          "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                          "dtype": "f32", "data": "synthetic",
+                          "config": {"workload": BATCH, "grids": len(ws),
+                                     "cell_updates_per_step": cells_steps,
+                                     "graph_launches_per_step": b.launches(), "per_grid_T_V": tv,
+                                     "l2": "inputs larger than L2 in total (%.0f MiB)" % (nb / 2**20)},
+                          "roofline": roof, "e2e": e2e, "gpu_launches": b.launches() * args.steps,
+                          "clocks": clk.summary(), "cpu_baseline": None}), flush=True)
+    b.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + [BATCH])
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--T", type=int, default=0, help="force the fused step count")
     ap.add_argument("--bx", type=int, default=0, help="force the 2D tile width")
@@ -238,6 +372,8 @@ def main():
     ap.add_argument("--time-steps", type=int, default=0, help="profiling: override time steps")
     args = ap.parse_args()
 
+    if args.workload == BATCH:
+        return bench_batch(args)
     w = WORKLOADS[args.workload]()
     resized = bool(args.nx or args.ny or args.nz or args.time_steps)
     if resized:

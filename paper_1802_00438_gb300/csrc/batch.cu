@@ -4,9 +4,10 @@
 // (Eqs. 3-9, model.cu) and its own ping-pong scratch, and runs ceil(steps/T) temporally-blocked
 // passes like stencil_run (Sec. 3.2; the last pass fuses the remainder).  Grids that share a
 // kernel instance (stencil kind, T, V) form a group; pass p of a group is one persistent launch
-// over a work queue of all its grids' (tile column, row) units that still have a pass p, split
-// evenly over the blocks, so small and large grids are served in the same launch without
-// idle blocks.  All launches (and the final copies of grids run in place with an odd pass
+// over a work queue of all its grids' (tile column, row) units that run a pass in that launch,
+// split evenly over the blocks, so small and large grids are served in the same launch without
+// idle blocks; each grid's chain of passes starts at the launch slot that levels the work of
+// the group's launches (a grid with few passes fills in where long-running grids leave room).  All launches (and the final copies of grids run in place with an odd pass
 // count) are captured once into a CUDA graph; stencil_batch_run replays it.  The order of
 // passes of one grid is the order of launches in the graph: no device-side waiting.
 #include <cuda_runtime.h>
@@ -139,10 +140,44 @@ int stencil_batch_create(stencil_batch *out, const stencil_batch_grid *grids, in
     std::map<std::tuple<int, int, int>, std::vector<int>> groups;
     for (int g = 0; g < count; g++)
         if (B->passes[g] > 0) groups[std::make_tuple(B->grid[g].kind, B->T[g], B->V[g])].push_back(g);
+    // Level the work of a group's launches: grid g's P_g passes occupy launch slots
+    // [start_g, start_g + P_g) of the group's timeline of max P slots; largest grids first, each
+    // at the start that keeps the heaviest slot it touches lightest.
+    std::vector<int> start(count, 0);
     int maxp = 0;
     for (int g = 0; g < count; g++) maxp = std::max(maxp, B->passes[g]);
+    for (auto &kv : groups) {
+        int S = 0;
+        for (int g : kv.second) S = std::max(S, B->passes[g]);
+        std::vector<double> load(S, 0.0);
+        std::vector<int> order = kv.second;
+        std::sort(order.begin(), order.end(), [&](int a, int b) {
+            return (double)B->grid[a].nx * B->grid[a].ny * B->passes[a] >
+                   (double)B->grid[b].nx * B->grid[b].ny * B->passes[b];
+        });
+        for (int g : order) {
+            const int P = B->passes[g];
+            const double wgt = (double)B->grid[g].nx * B->grid[g].ny;
+            int best_s = 0;
+            double best_m = 1e300, best_sum = 1e300;
+            for (int s0 = 0; s0 + P <= S; s0++) {
+                double m = 0.0, sum = 0.0;
+                for (int k = s0; k < s0 + P; k++) {
+                    m = std::max(m, load[k]);
+                    sum += load[k];
+                }
+                if (m < best_m || (m == best_m && sum < best_sum)) {
+                    best_m = m;
+                    best_sum = sum;
+                    best_s = s0;
+                }
+            }
+            start[g] = best_s;
+            for (int k = best_s; k < best_s + P; k++) load[k] += wgt;
+        }
+    }
     size_t table = 0;
-    for (int p = 0; p < maxp && rc == ST_OK; p++) {
+    for (int slot = 0; slot < maxp && rc == ST_OK; slot++) {
         for (auto &kv : groups) {
             const int kind = std::get<0>(kv.first), T = std::get<1>(kv.first), V = std::get<2>(kv.first);
             LaunchRec r;
@@ -152,7 +187,8 @@ int stencil_batch_create(stencil_batch *out, const stencil_batch_grid *grids, in
             for (int g : kv.second) {
                 const stencil_batch_grid &q = B->grid[g];
                 const int P = B->passes[g];
-                if (p >= P) continue;
+                const int p = slot - start[g];   // this grid's pass in this slot
+                if (p < 0 || p >= P) continue;
                 const int last = q.steps - T * (P - 1);
                 const bool shift = (q.grid_in == q.grid_out) && (P % 2 == 1);
                 auto to_out = [&](int i) { return shift ? ((P - i) % 2 == 0) : ((P - 1 - i) % 2 == 0); };
