@@ -75,7 +75,9 @@ typedef struct {
     int force_T;     /* fused steps per pass (par_time, Sec. 3.2); 0 = the plan chooses */
     int force_bx;    /* tile width in cells incl. halos (bsize_x, Sec. 3.1); 0 = choose */
     int force_by;    /* 3D: tile height in cells incl. halos (bsize_y); 0 = choose */
-    int force_vec;   /* cells per thread along x (par_vec, Sec. 3.1); 0 = choose */
+    int force_vec;   /* 2D: cells per thread along x (par_vec, Sec. 3.1); 3D: cells per thread,
+                        16 (2 x 8 rows, three-plane windows), 8 (2 x 4 rows) or 4 (2 x 2 rows;
+                        8 and 4: partial sums along z, contracted only); 0 = choose */
     int exact;       /* 1: Table 2 order, no fused multiply-add; 0: contracted */
     int strict;      /* 1: reject coefficients that break the explicit stability bound */
     void *stream;    /* cudaStream_t the plan launches on; NULL = the legacy default stream */
@@ -86,7 +88,7 @@ typedef struct {
     int T;              /* fused steps per pass */
     int bx, by;         /* tile size in cells incl. halos (by = 0 for 2D streaming) */
     int halo;           /* halo width per side in cells (>= rad * T, Eq. 2) */
-    int vec;            /* cells per thread along x */
+    int vec;            /* cells per thread (along x in 2D; x times rows in 3D) */
     int warps;          /* warps per block */
     int ctas;           /* blocks per launch (a multiple of the SM count where possible) */
     int sms;            /* streaming multiprocessors on the plan's device */

@@ -51,7 +51,7 @@ struct stencil_plan_s {
     int V = 4, W = 4;
     std::vector<PassCfg2D> cfg2;   // indexed by kernel T
     // 3D
-    int VY = 8, NW = 8;
+    int VY = 8, NW = 8, alg3 = 0;
     std::vector<PassCfg3D> cfg3;
     // timing
     bool timing = false;
@@ -93,7 +93,7 @@ bool available(const stencil_plan_s *p, int T)
 {
     if (p->d.ndim == 2)
         return tb2d_available(Shape2D{p->d.kind, p->d.exact ? 1 : 0, T, p->V, p->W, p->stor});
-    return tb3d_available(Shape3D{p->d.kind, p->d.exact ? 1 : 0, T, p->VY, p->NW});
+    return tb3d_available(Shape3D{p->d.kind, p->d.exact ? 1 : 0, T, p->VY, p->NW, p->alg3});
 }
 
 // ---- parameter choice seeded by the GPU restatement of the paper's model (Eqs. 3-9) -------
@@ -201,7 +201,7 @@ int prepare3(stencil_plan_s *p, int Tk, PassCfg3D **out)
     if ((int)p->cfg3.size() <= Tk) p->cfg3.resize(Tk + 1);
     PassCfg3D &c = p->cfg3[Tk];
     if (!c.ready) {
-        c.shape = Shape3D{p->d.kind, p->d.exact ? 1 : 0, Tk, p->VY, p->NW};
+        c.shape = Shape3D{p->d.kind, p->d.exact ? 1 : 0, Tk, p->VY, p->NW, p->alg3};
         if (!tb3d_available(c.shape)) return ST_ERR_UNSUPPORTED;
         int bps = 0;
         cudaError_t e = tb3d_prepare(c.shape, &bps);
@@ -375,6 +375,7 @@ int run_pass3(stencil_plan_s *p, const float *src, float *dst, const float *pw, 
     a.ctas = c->ctas;
     for (int i = 0; i < 9; i++) a.k[i] = i < ncoef(p->d) ? k[i] : 0.f;
     a.vec = ((uintptr_t)src % 16 == 0) && ((uintptr_t)dst % 16 == 0) && (p->d.nx % 4 == 0);
+    a.vec_pw = pw && ((uintptr_t)pw % 16 == 0) && (p->d.nx % 4 == 0);
     if (p->timing && p->ev_used + 2 > 2 * 1024) {
         rc = flush_timing(p);
         if (rc != ST_OK) return rc;
@@ -516,12 +517,25 @@ int stencil_plan_create(stencil_plan *out, const stencil_desc *desc)
             p->scratch_bytes = (size_t)p->ld_scratch * d.ny * sizeof(float);
         }
     } else {
-        if (d.force_vec && d.force_vec != 2) rc = ST_ERR_UNSUPPORTED;
         if (d.force_bx && d.force_bx != 64) rc = ST_ERR_UNSUPPORTED;
         if (d.force_by && d.force_by != 64) rc = ST_ERR_UNSUPPORTED;
-        p->VY = 8;
-        p->NW = 8;
-        const int want = d.force_T ? d.force_T : 4;
+        // cells per thread: 16 = 8 rows x 2 (three-plane windows, exact or contracted);
+        // 8 = 4 rows x 2 and 4 = 2 rows x 2 (partial sums along z, contracted)
+        const int cells = d.force_vec ? d.force_vec : (d.exact ? 16 : 8);
+        if (cells == 16) {
+            p->VY = 8;
+            p->NW = 8;
+            p->alg3 = 0;
+        } else if (!d.exact && (cells == 8 || cells == 4)) {
+            p->VY = cells / 2;
+            p->NW = 64 / p->VY;
+            p->alg3 = 1;
+        } else {
+            rc = ST_ERR_UNSUPPORTED;
+        }
+        // contracted default: T = 3 (512^3 diffusion and 512^2 x 256 Hotspot measure best at
+        // T = 3 with 4 rows x 2 cells per thread; the x halo is rounded up to 4 anyway)
+        const int want = d.force_T ? d.force_T : (p->alg3 ? 3 : 4);
         p->T = kernel_T_for(p, want);
         if (p->T == 0 || (d.force_T && p->T != d.force_T)) rc = ST_ERR_UNSUPPORTED;
         PassCfg3D *c = nullptr;
@@ -653,10 +667,10 @@ int stencil_plan_get_info(stencil_plan p, stencil_plan_info *info)
         info->bx = 64;
         info->by = p->VY * p->NW;
         info->halo = p->T;
-        info->vec = 2;
+        info->vec = 2 * p->VY;
         info->warps = p->NW;
         info->ctas = c->ctas;
-        info->kernel_id = 3;
+        info->kernel_id = p->alg3 ? 4 : 3;
     }
     return ST_OK;
 }

@@ -7,9 +7,11 @@
 // over a work queue of all its grids' (tile column, row) units that run a pass in that launch,
 // split evenly over the blocks, so small and large grids are served in the same launch without
 // idle blocks; each grid's chain of passes starts at the launch slot that levels the work of
-// the group's launches (a grid with few passes fills in where long-running grids leave room).  All launches (and the final copies of grids run in place with an odd pass
-// count) are captured once into a CUDA graph; stencil_batch_run replays it.  The order of
-// passes of one grid is the order of launches in the graph: no device-side waiting.
+// the group's launches (a grid with few passes fills in where long-running grids leave room).
+// All launches (and the final copies of grids run in place with an odd pass count) are
+// captured once into a CUDA graph with one branch per group; stencil_batch_run replays it.
+// The order of passes of one grid is the order of launches on its branch: no device-side
+// waiting.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -54,6 +56,7 @@ int status(cudaError_t e)
 const int kCand[][2] = {{4, 4}, {8, 4}, {4, 8}, {8, 8}};   // (T, V) compiled for batches
 
 struct LaunchRec {
+    int group;                     // branch of the graph the launch is captured on
     Shape2D shape;
     BatchPass2D bp;
     size_t desc_off, prefix_off;   // byte offsets into the device table
@@ -177,10 +180,21 @@ int stencil_batch_create(stencil_batch *out, const stencil_batch_grid *grids, in
         }
     }
     size_t table = 0;
-    for (int slot = 0; slot < maxp && rc == ST_OK; slot++) {
+    std::vector<int> group_of(count, -1);
+    {
+        int gi = 0;
         for (auto &kv : groups) {
+            for (int g : kv.second) group_of[g] = gi;
+            gi++;
+        }
+    }
+    for (int slot = 0; slot < maxp && rc == ST_OK; slot++) {
+        int gi = -1;
+        for (auto &kv : groups) {
+            gi++;
             const int kind = std::get<0>(kv.first), T = std::get<1>(kv.first), V = std::get<2>(kv.first);
             LaunchRec r;
+            r.group = gi;
             r.shape = Shape2D{kind, 0, T, V, 1};
             const int bx = 32 * V, h = (T + 3) / 4 * 4, cx = bx - 2 * h;
             r.prefix.push_back(0);
@@ -252,13 +266,26 @@ int stencil_batch_create(stencil_batch *out, const stencil_batch_grid *grids, in
         e = cudaMemcpy(B->dev, host.data(), table, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) rc = status(e);
     }
-    // capture every launch (and the in-place copies) into one graph
+    // Capture every launch (and the in-place copies) into one graph.  Each group is a branch
+    // of its own (captured on its own stream, forked from and joined back into B->stream), so
+    // the groups' launches overlap on the GPU and one group's launch tails fill with another's
+    // work; within a branch, launch order is pass order.
     if (rc == ST_OK) {
-        e = cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal);
+        const int ng = (int)groups.size();
+        std::vector<cudaStream_t> gs(ng, nullptr);
+        std::vector<cudaEvent_t> join(ng, nullptr);
+        cudaEvent_t fork = nullptr;
+        e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        for (int i = 0; i < ng && e == cudaSuccess; i++) {
+            e = cudaStreamCreateWithFlags(&gs[i], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t le = cudaSuccess;
+            cudaError_t le = cudaEventRecord(fork, B->stream);
+            for (int i = 0; i < ng && le == cudaSuccess; i++) le = cudaStreamWaitEvent(gs[i], fork, 0);
             for (const LaunchRec &r : recs) {
-                if (le == cudaSuccess) le = tb2d_batch_launch(r.shape, r.bp, B->stream);
+                if (le == cudaSuccess) le = tb2d_batch_launch(r.shape, r.bp, gs[r.group]);
                 B->launches++;
             }
             for (int g = 0; g < count && le == cudaSuccess; g++) {
@@ -271,12 +298,22 @@ int stencil_batch_create(stencil_batch *out, const stencil_batch_grid *grids, in
                     le = cudaMemcpy2DAsync(q.grid_out, (size_t)q.nx * sizeof(float), B->scratch[g],
                                            (size_t)B->ld_scratch[g] * sizeof(float),
                                            (size_t)q.nx * sizeof(float), q.ny,
-                                           cudaMemcpyDeviceToDevice, B->stream);
+                                           cudaMemcpyDeviceToDevice, gs[group_of[g]]);
+            }
+            for (int i = 0; i < ng; i++) {
+                cudaError_t je = cudaEventRecord(join[i], gs[i]);
+                if (je == cudaSuccess) je = cudaStreamWaitEvent(B->stream, join[i], 0);
+                if (le == cudaSuccess) le = je;
             }
             e = cudaStreamEndCapture(B->stream, &B->graph);
             if (le != cudaSuccess) e = le;
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&B->exec, B->graph, 0);
+        for (int i = 0; i < ng; i++) {
+            if (join[i]) cudaEventDestroy(join[i]);
+            if (gs[i]) cudaStreamDestroy(gs[i]);
+        }
+        if (fork) cudaEventDestroy(fork);
         if (e != cudaSuccess) rc = status(e);
     }
     if (rc != ST_OK) {

@@ -78,9 +78,12 @@ struct Pass3D {
     int ctas;
     float k[9];
     int vec;               // 1: rows start on 16-byte boundaries
+    int vec_pw;            // 1: the power map's rows start on 16-byte boundaries
 };
 
-struct Shape3D { int kind, exact, T, VY, NW; };   // tile 64 x (VY*NW) cells
+// tile 64 x (VY*NW) cells; alg 0: three-plane register windows (k_tb3d, exact or contracted),
+// alg 1: partial sums along z (k_tb3f, contracted only)
+struct Shape3D { int kind, exact, T, VY, NW; int alg = 0; };
 
 bool tb3d_available(const Shape3D &s);
 int tb3d_block_threads(const Shape3D &s);

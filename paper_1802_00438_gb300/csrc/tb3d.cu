@@ -3,14 +3,22 @@
 
 namespace stn {
 
-static const Tb3dEntry *tb3d_find(const Shape3D &s)
+static const Tb3dEntry *find_in(const Tb3dEntry *t, int n, const Shape3D &s)
 {
-    for (int i = 0; i < tb3d_table_n; i++) {
-        const Tb3dEntry &e = tb3d_table[i];
-        if (e.kind == s.kind && e.exact == s.exact && e.T == s.T && e.VY == s.VY && e.NW == s.NW)
+    for (int i = 0; i < n; i++) {
+        const Tb3dEntry &e = t[i];
+        if (e.kind == s.kind && e.exact == s.exact && e.T == s.T && e.VY == s.VY &&
+            e.NW == s.NW && e.alg == s.alg)
             return &e;
     }
     return nullptr;
+}
+
+static const Tb3dEntry *tb3d_find(const Shape3D &s)
+{
+    if (s.alg == 0) return find_in(tb3d_table, tb3d_table_n, s);
+    return s.kind == 0 ? find_in(tb3f_table_diff, tb3f_table_diff_n, s)
+                       : find_in(tb3f_table_therm, tb3f_table_therm_n, s);
 }
 
 bool tb3d_available(const Shape3D &s) { return tb3d_find(s) != nullptr; }

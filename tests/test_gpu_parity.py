@@ -31,12 +31,13 @@ def max_rel(g, o):
     return float(np.max(np.abs(g - o) / np.maximum(np.abs(o), floor)))
 
 
-def gpu_run(st, w, steps, exact=False, T=0, bx=0, inplace=False):
+def gpu_run(st, w, steps, exact=False, T=0, bx=0, inplace=False, vec=0):
     import torch
     u = torch.from_numpy(np.ascontiguousarray(w.u0)).cuda()
     p = None if w.power is None else torch.from_numpy(np.ascontiguousarray(w.power)).cuda()
     out = u if inplace else torch.full_like(u, float("nan"))
-    plan = st.Plan(w.kind, w.ndim, w.nx, w.ny, w.nz, exact=exact, force_T=T, force_bx=bx)
+    plan = st.Plan(w.kind, w.ndim, w.nx, w.ny, w.nz, exact=exact, force_T=T, force_bx=bx,
+                   force_vec=vec)
     plan.run(u, out, w.coef, steps, power=p)
     plan.sync()
     info = plan.info()
@@ -86,13 +87,27 @@ def test_contracted_2d(eng, orc, kind, T, bx):
 
 @pytest.mark.parametrize("kind", [0, 1])
 @pytest.mark.parametrize("T", [1, 2, 3, 4])
-def test_contracted_3d(eng, orc, kind, T):
-    for t, (nx, ny, nz) in enumerate(SIZES_3D[2:]):
+@pytest.mark.parametrize("vec", [16, 8, 4])
+def test_contracted_3d(eng, orc, kind, T, vec):
+    # vec 16: three-plane windows; 8 and 4: partial sums along z (2 cells x 4 or 2 rows)
+    for t, (nx, ny, nz) in enumerate(SIZES_3D[:2] + SIZES_3D[3:] + [(203, 150, 37)]):
         w = synth.make(kind, 3, nx, ny, nz, seed=4000 + 43 * t + kind)
         for steps in (1, T + 2, 3 * T + 1):
-            g, _ = gpu_run(eng, w, steps, T=T)
+            g, info = gpu_run(eng, w, steps, T=T, vec=vec)
+            assert info["vec"] == vec and info["T"] == T
             o = orc.run(kind, w.u0, w.coef, steps, w.power)
             assert max_rel(g, o) <= TOL, (nx, ny, nz, steps, max_rel(g, o))
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_contracted_3d_in_place_unaligned(eng, orc, kind):
+    """Rows that do not start on 16-byte boundaries (nx odd) use the scalar staging path, in
+    place, with an odd and an even pass count."""
+    w = synth.make(kind, 3, 67, 45, 23, seed=4500 + kind)
+    for steps in (5, 8):
+        g, _ = gpu_run(eng, w, steps, T=4, vec=8, inplace=True)
+        o = orc.run(kind, w.u0, w.coef, steps, w.power)
+        assert max_rel(g, o) <= TOL, (steps, max_rel(g, o))
 
 
 @pytest.mark.parametrize("ndim", [2, 3])
