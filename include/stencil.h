@@ -173,6 +173,48 @@ int stencil_batch_launch_count(stencil_batch b);
 /* Wait for the batch's stream, free its graph and scratch.  NULL is accepted. */
 int stencil_batch_destroy(stencil_batch b);
 
+/* ---- adjoint (reverse-mode gradient) of a 2D run -------------------------------------------
+ *
+ * One step is affine in the field, u_{t+1} = A u_t + b(coeffs, power) (Sec. 2.1, Table 2,
+ * clamped boundary), so for a scalar loss L with upstream gradient w = dL/du_steps:
+ *   lambda_steps = w,  lambda_t = A^T lambda_{t+1},  dL/du_0 = lambda_0,
+ *   dL/dcoeff_m = sum_{t<steps} sum_i lambda_{t+1}[i] dF_i/dcoeff_m (u_t),
+ *   dL/dpower_i = k_dt * sum_{t=1..steps} lambda_t[i]           (Hotspot 2D only).
+ * The transposed sweep is temporally blocked like the forward one (Sec. 3.2); forward states
+ * are recomputed from checkpoints kept every `ckpt` steps. */
+typedef struct stencil_adjoint_s *stencil_adjoint;
+
+/* Prepare the gradient of a `steps`-step 2D run (kind ST_DIFFUSION or ST_THERMAL, nx x ny
+ * cells).  Allocates ceil(steps/ckpt) checkpoint grids, ckpt state grids, two adjoint grids
+ * and two forward plans on `stream` (cudaStream_t; NULL = legacy default stream).
+ * Errors: ST_ERR_INVALID_ARG (kind, sizes, steps < 0, ckpt < 1), ST_ERR_OOM, ST_ERR_CUDA. */
+int stencil_adjoint_create(stencil_adjoint *out, int kind, int nx, int ny, int steps, int ckpt,
+                           void *stream);
+
+/* Forward run u_out = u_steps (device pointers, nx*ny floats; u_out may equal u0), keeping
+ * the checkpoints and a copy of the 5 host coefficients for stencil_adjoint_backward.
+ * power: device power map for ST_THERMAL (NULL for ST_DIFFUSION); it must be passed unchanged
+ * to the backward call.  Asynchronous on the object's stream. */
+int stencil_adjoint_forward(stencil_adjoint a, const float *u0, const float *power,
+                            const float *coeffs, float *u_out);
+
+/* Gradients of the last forward run (device pointers, all on the object's stream):
+ *   grad_out        : dL/du_steps, nx*ny floats (read only)
+ *   grad_u0         : dL/du_0, nx*ny floats (may not overlap grad_out)
+ *   grad_coeffs     : 5 floats, dL/dcoeffs in the coefficient layout of the kind
+ *   grad_coeffs_abs : 5 floats or NULL: sum over (t, i) of |lambda_{t+1}[i] dF_i/dcoeff_m|,
+ *                     the scale the rounding error of grad_coeffs[m] is relative to
+ *   grad_power      : dL/dpower, nx*ny floats (ST_THERMAL; NULL for ST_DIFFUSION)
+ * Coefficient gradients are float32 error-free-transformation sums in a fixed order:
+ * deterministic for a given size.  Errors: ST_ERR_INVALID_ARG (no forward run yet, missing or
+ * unexpected pointers), ST_ERR_CUDA. */
+int stencil_adjoint_backward(stencil_adjoint a, const float *grad_out, const float *power,
+                             float *grad_u0, float *grad_coeffs, float *grad_coeffs_abs,
+                             float *grad_power);
+
+/* Wait for the object's stream and free everything it owns.  NULL is accepted. */
+int stencil_adjoint_destroy(stencil_adjoint a);
+
 /* ---- float64 verification reductions ----------------------------------------------------- */
 
 /* Bytes of device workspace stencil_reduce needs (caller-allocated, 8-byte aligned). */

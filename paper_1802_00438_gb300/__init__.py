@@ -130,6 +130,10 @@ SIGNATURES = {
                            ctypes.POINTER(stencil_gpu_model_out)], _I),
     "stencil_run_noalloc": ([_I, _P, _P, _P, ctypes.POINTER(ctypes.c_float), _I, _I, _I, _I, _I,
                              _P], _I),
+    "stencil_adjoint_create": ([ctypes.POINTER(_P), _I, _I, _I, _I, _I, _P], _I),
+    "stencil_adjoint_forward": ([_P, _P, _P, ctypes.POINTER(ctypes.c_float), _P], _I),
+    "stencil_adjoint_backward": ([_P, _P, _P, _P, _P, _P, _P], _I),
+    "stencil_adjoint_destroy": ([_P], _I),
 }
 
 
@@ -357,3 +361,106 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+# ---- adjoint (reverse-mode gradient of a 2D run) ------------------------------------------------
+
+def stencil_adjoint_create(kind, nx, ny, steps, ckpt=20, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib.stencil_adjoint_create(ctypes.byref(h), int(kind), int(nx), int(ny), int(steps),
+                                      int(ckpt), current_stream() if stream is None else stream),
+           "stencil_adjoint_create")
+    return h
+
+
+def stencil_adjoint_forward(adj, u0, power, coeffs, u_out):
+    k = _coef_array(coeffs)
+    _check(lib.stencil_adjoint_forward(adj, _addr(u0), _addr(power), k, _addr(u_out)),
+           "stencil_adjoint_forward")
+
+
+def stencil_adjoint_backward(adj, grad_out, power, grad_u0, grad_coeffs, grad_coeffs_abs=None,
+                             grad_power=None):
+    _check(lib.stencil_adjoint_backward(adj, _addr(grad_out), _addr(power), _addr(grad_u0),
+                                        _addr(grad_coeffs), _addr(grad_coeffs_abs),
+                                        _addr(grad_power)), "stencil_adjoint_backward")
+
+
+def stencil_adjoint_destroy(adj):
+    _check(lib.stencil_adjoint_destroy(adj), "stencil_adjoint_destroy")
+
+
+class Adjoint:
+    """Owning wrapper of stencil_adjoint: forward run with checkpoints every `ckpt` steps, then
+    gradients of the last forward run for an upstream gradient dL/du_steps."""
+
+    def __init__(self, kind, nx, ny, steps, ckpt=20, stream=None):
+        self.kind, self.nx, self.ny, self.steps = kind, nx, ny, steps
+        self.h = stencil_adjoint_create(kind, nx, ny, steps, ckpt, stream)
+
+    def forward(self, u0, coeffs, power=None, out=None):
+        import torch
+        out = torch.empty_like(u0) if out is None else out
+        stencil_adjoint_forward(self.h, u0, power, coeffs, out)
+        return out
+
+    def backward(self, grad_out, power=None, with_abs=False):
+        """Returns (dL/du0, dL/dcoeffs, dL/dpower or None, sum|terms| per coefficient or None),
+        all CUDA tensors on grad_out's device."""
+        import torch
+        gu = torch.empty_like(grad_out)
+        gk = torch.empty(5, dtype=torch.float32, device=grad_out.device)
+        ga = torch.empty(5, dtype=torch.float32, device=grad_out.device) if with_abs else None
+        gp = torch.empty_like(grad_out) if self.kind == ST_THERMAL else None
+        stencil_adjoint_backward(self.h, grad_out, power, gu, gk, ga, gp)
+        return gu, gk, gp, ga
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            stencil_adjoint_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _autograd_function():
+    import torch
+
+    class StencilSweep(torch.autograd.Function):
+        """u_steps = sweep(u0, coeffs, power): `steps` Jacobi steps of a 2D stencil; backward by
+        the adjoint sweep (checkpoints every `ckpt` steps)."""
+
+        @staticmethod
+        def forward(ctx, u0, coeffs, power, kind, steps, ckpt):
+            u0c = u0.detach().contiguous()
+            pw = None if power is None else power.detach().contiguous()
+            adj = Adjoint(kind, u0c.shape[1], u0c.shape[0], steps, ckpt)
+            out = adj.forward(u0c, coeffs.detach().cpu(), pw)
+            ctx.adj, ctx.pw = adj, pw
+            ctx.coef_device = coeffs.device
+            return out
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            gu, gk, gp, _ = ctx.adj.backward(grad_out.detach().contiguous(), ctx.pw)
+            ctx.adj.close()
+            return gu, gk.to(ctx.coef_device), gp, None, None, None
+
+    return StencilSweep
+
+
+_SWEEP = None
+
+
+def stencil_sweep(u0, coeffs, steps, kind=ST_DIFFUSION, power=None, ckpt=20):
+    """Differentiable 2D sweep (torch.autograd): u0 (ny, nx) float32 CUDA tensor, coeffs a
+    float32 tensor of 5 (any device), power (ny, nx) CUDA tensor for ST_THERMAL.  Gradients flow
+    to u0, coeffs and power."""
+    global _SWEEP
+    if _SWEEP is None:
+        _SWEEP = _autograd_function()
+    return _SWEEP.apply(u0, coeffs, power, kind, int(steps), int(ckpt))

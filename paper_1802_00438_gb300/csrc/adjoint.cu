@@ -1,0 +1,507 @@
+// Reverse-mode gradient of a 2D run: the adjoint (transposed-stencil) sweep.
+//
+// One Jacobi step (arXiv 1802.00438, Sec. 2.1, Table 2 updates, clamped boundary) is affine in
+// the field: u_{t+1} = A u_t + b(theta, p).  For a scalar loss with upstream gradient
+// w = dL/du_N the adjoint recursion is
+//     lambda_N = w,   lambda_t = A^T lambda_{t+1},   dL/du_0 = lambda_0,
+//     dL/dtheta = sum_{t<N} sum_i lambda_{t+1}[i] dF_i/dtheta(u_t),
+//     dL/dp_i   = k_dt * sum_{t=1..N} lambda_t[i]            (Hotspot: dF_i/dp_i = k_dt).
+// A^T is again a five-point stencil with the forward weights moved to the mirrored neighbours:
+//     (A^T l)_j = wc l_j + ww l_{x+1} + we l_{x-1} + ws l_{y-1} + wn l_{y+1}
+// with out-of-domain l = 0, plus, at the domain edges, the weight of every clamped neighbour
+// that the forward step folded into cell j (x = 0: ww, x = nx-1: we, y = 0: wn, y = ny-1: ws).
+//
+// GPU design.  The reverse sweep is temporally blocked like the forward sweep (Sec. 3.2): a
+// pass loads a 128 x 64 tile of lambda_{t+TA} with a halo of TA cells into shared memory and
+// applies TA transposed steps there (ping-pong buffers, redundant halo work, only the compute
+// block written).  The same pass accumulates the coefficient and power gradients of its compute
+// block from the forward states u_t, which are recomputed from checkpoints every K steps into a
+// K-state buffer (the forward plans of this library, T = 1 per state).  Coefficient gradients
+// are float32 error-free-transformation sums (TwoProd by fma, TwoSum): each thread keeps a
+// (hi, lo) pair per coefficient, blocks combine pairs in a fixed tree, and one final kernel
+// combines all (pass, block) pairs in a fixed order, so results are deterministic and carry
+// roughly twice float32's precision without float64 arithmetic.  Alongside each gradient the
+// same reduction yields sum |term|, the scale its rounding error is relative to.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <new>
+#include <vector>
+
+#include "../../include/stencil.h"
+
+namespace {
+
+constexpr int AX = 128, AY = 64, ANT = 512, ACPT = AX * AY / ANT;   // tile, threads, cells/thread
+constexpr int ATA = 4;                                                // fused adjoint steps
+constexpr int ACX = AX - 2 * ATA, ACY = AY - 2 * ATA;                // compute block
+constexpr int NG = 5;                                                 // coefficients
+constexpr int NPART = 3 * NG;                                         // (hi, lo, |.|) x 5
+
+struct AdjPass {
+    const float *lam_in;     // lambda_{t_hi}
+    float *lam_out;          // lambda_{t_lo}
+    const float *states;     // u_{t0 + k} at states + k * n
+    long long n;             // cells per grid
+    int k_hi;                // index of u_{t_hi - 1} in states
+    int nsteps;              // t_hi - t_lo, 1..ATA
+    const float *pw;         // Hotspot power map
+    float *gpw;              // Hotspot dL/dp (accumulated)
+    int nx, ny, ntx;
+    float wc, ww, we, ws, wn;   // forward weights of c, w, e, s, n
+    float k[5];
+    float *partials;         // this pass's [block][NPART]
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (hi, lo) += x * y, exactly up to the final renormalisation
+__device__ __forceinline__ void acc_prod(float &hi, float &lo, float x, float y)
+{
+    const float p = __fmul_rn(x, y);
+    const float pe = __fmaf_rn(x, y, -p);   // exact error of the product
+    float s, e;
+    two_sum(hi, p, s, e);
+    lo = __fadd_rn(lo, __fadd_rn(e, pe));
+    two_sum(s, lo, hi, lo);
+}
+
+__device__ __forceinline__ void add_pair(float &hi, float &lo, float bhi, float blo)
+{
+    float s, e;
+    two_sum(hi, bhi, s, e);
+    e = __fadd_rn(e, __fadd_rn(lo, blo));
+    two_sum(s, e, hi, lo);
+}
+
+template <int KIND>
+__device__ __forceinline__ void dfdtheta(const AdjPass &a, float c, float w, float e, float s,
+                                         float n, float p, float (&g)[NG])
+{
+    if (KIND == ST_DIFFUSION) {   // [cc, cw, ce, cs, cn]
+        g[0] = c; g[1] = w; g[2] = e; g[3] = s; g[4] = n;
+    } else {                      // [k_dt, Rx, Ry, Rz, amb]
+        const float c2 = __fmul_rn(2.0f, c);
+        const float t1 = __fsub_rn(__fadd_rn(n, s), c2);
+        const float t2 = __fsub_rn(__fadd_rn(e, w), c2);
+        const float t3 = __fsub_rn(a.k[4], c);
+        float q = __fmaf_rn(t1, a.k[2], p);
+        q = __fmaf_rn(t2, a.k[1], q);
+        q = __fmaf_rn(t3, a.k[3], q);
+        g[0] = q;
+        g[1] = __fmul_rn(a.k[0], t2);
+        g[2] = __fmul_rn(a.k[0], t1);
+        g[3] = __fmul_rn(a.k[0], t3);
+        g[4] = __fmul_rn(a.k[0], a.k[3]);
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(ANT) k_adj2d(const AdjPass a)
+{
+    extern __shared__ __align__(16) float sm[];
+    float *buf0 = sm, *buf1 = sm + AX * AY;
+    __shared__ float red[ANT / 32][NPART];
+    const int tid = threadIdx.x;
+    const int tx = blockIdx.x % a.ntx, ty = blockIdx.x / a.ntx;
+    const int x0 = tx * ACX - ATA, y0 = ty * ACY - ATA;
+
+#pragma unroll
+    for (int q = 0; q < ACPT; q++) {
+        const int idx = tid + q * ANT, lx = idx % AX, ly = idx / AX;
+        const int gx = x0 + lx, gy = y0 + ly;
+        const bool in = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny;
+        buf0[idx] = in ? a.lam_in[(long long)gy * a.nx + gx] : 0.f;
+    }
+    __syncthreads();
+
+    float hi[NG], lo[NG], ab[NG], pacc[ACPT];
+#pragma unroll
+    for (int m = 0; m < NG; m++) hi[m] = lo[m] = ab[m] = 0.f;
+#pragma unroll
+    for (int q = 0; q < ACPT; q++) pacc[q] = 0.f;
+
+    float *cur = buf0, *nxt = buf1;
+    for (int j = 0; j < a.nsteps; j++) {
+        const float *u = a.states + (long long)(a.k_hi - j) * a.n;   // u_t, t = t_hi - 1 - j
+#pragma unroll
+        for (int q = 0; q < ACPT; q++) {
+            const int idx = tid + q * ANT, lx = idx % AX, ly = idx / AX;
+            const int gx = x0 + lx, gy = y0 + ly;
+            const bool in = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny;
+            const float l = cur[idx];   // lambda_{t+1}
+            const float le = lx + 1 < AX ? cur[idx + 1] : 0.f;
+            const float lw = lx > 0 ? cur[idx - 1] : 0.f;
+            const float ln = ly > 0 ? cur[idx - AX] : 0.f;
+            const float ls = ly + 1 < AY ? cur[idx + AX] : 0.f;
+            float cs = a.wc;
+            if (gx == 0) cs = __fadd_rn(cs, a.ww);
+            if (gx == a.nx - 1) cs = __fadd_rn(cs, a.we);
+            if (gy == 0) cs = __fadd_rn(cs, a.wn);
+            if (gy == a.ny - 1) cs = __fadd_rn(cs, a.ws);
+            float r = __fmul_rn(cs, l);
+            r = __fmaf_rn(a.ww, le, r);
+            r = __fmaf_rn(a.we, lw, r);
+            r = __fmaf_rn(a.ws, ln, r);
+            r = __fmaf_rn(a.wn, ls, r);
+            nxt[idx] = in ? r : 0.f;
+            const bool own = in && lx >= ATA && lx < ATA + ACX && ly >= ATA && ly < ATA + ACY;
+            if (own) {
+                const long long o = (long long)gy * a.nx;
+                const int xw = gx > 0 ? gx - 1 : 0, xe = gx < a.nx - 1 ? gx + 1 : a.nx - 1;
+                const long long on = (long long)(gy > 0 ? gy - 1 : 0) * a.nx;
+                const long long os = (long long)(gy < a.ny - 1 ? gy + 1 : a.ny - 1) * a.nx;
+                float g[NG];
+                const float p = KIND == ST_THERMAL ? __ldg(a.pw + o + gx) : 0.f;
+                dfdtheta<KIND>(a, __ldg(u + o + gx), __ldg(u + o + xw), __ldg(u + o + xe),
+                               __ldg(u + os + gx), __ldg(u + on + gx), p, g);
+#pragma unroll
+                for (int m = 0; m < NG; m++) {
+                    acc_prod(hi[m], lo[m], l, g[m]);
+                    ab[m] = __fadd_rn(ab[m], fabsf(__fmul_rn(l, g[m])));
+                }
+                if (KIND == ST_THERMAL) pacc[q] = __fadd_rn(pacc[q], l);
+            }
+        }
+        __syncthreads();
+        float *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+
+#pragma unroll
+    for (int q = 0; q < ACPT; q++) {
+        const int idx = tid + q * ANT, lx = idx % AX, ly = idx / AX;
+        const int gx = x0 + lx, gy = y0 + ly;
+        const bool own = gx < a.nx && gy < a.ny && lx >= ATA && lx < ATA + ACX && ly >= ATA &&
+                         ly < ATA + ACY;
+        if (own) {
+            const long long o = (long long)gy * a.nx + gx;
+            a.lam_out[o] = cur[idx];
+            if (KIND == ST_THERMAL) a.gpw[o] = __fmaf_rn(a.k[0], pacc[q], a.gpw[o]);
+        }
+    }
+
+    // block reduction of the (hi, lo) pairs and the magnitudes, fixed order
+    const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int m = 0; m < NG; m++) {
+            const float bh = __shfl_down_sync(0xffffffffu, hi[m], off);
+            const float bl = __shfl_down_sync(0xffffffffu, lo[m], off);
+            const float bb = __shfl_down_sync(0xffffffffu, ab[m], off);
+            add_pair(hi[m], lo[m], bh, bl);
+            ab[m] = __fadd_rn(ab[m], bb);
+        }
+    if (lane == 0)
+#pragma unroll
+        for (int m = 0; m < NG; m++) {
+            red[wid][3 * m + 0] = hi[m];
+            red[wid][3 * m + 1] = lo[m];
+            red[wid][3 * m + 2] = ab[m];
+        }
+    __syncthreads();
+    if (wid == 0) {
+        constexpr int NWP = ANT / 32;
+#pragma unroll
+        for (int m = 0; m < NG; m++) {
+            hi[m] = lane < NWP ? red[lane][3 * m + 0] : 0.f;
+            lo[m] = lane < NWP ? red[lane][3 * m + 1] : 0.f;
+            ab[m] = lane < NWP ? red[lane][3 * m + 2] : 0.f;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int m = 0; m < NG; m++) {
+                const float bh = __shfl_down_sync(0xffffffffu, hi[m], off);
+                const float bl = __shfl_down_sync(0xffffffffu, lo[m], off);
+                const float bb = __shfl_down_sync(0xffffffffu, ab[m], off);
+                add_pair(hi[m], lo[m], bh, bl);
+                ab[m] = __fadd_rn(ab[m], bb);
+            }
+        if (lane == 0)
+#pragma unroll
+            for (int m = 0; m < NG; m++) {
+                a.partials[(long long)blockIdx.x * NPART + 3 * m + 0] = hi[m];
+                a.partials[(long long)blockIdx.x * NPART + 3 * m + 1] = lo[m];
+                a.partials[(long long)blockIdx.x * NPART + 3 * m + 2] = ab[m];
+            }
+    }
+}
+
+// Combine `count` partial triples per coefficient in a fixed order: thread t takes entries
+// t, t + 256, ... sequentially, then a fixed shuffle / shared-memory tree.
+__global__ void __launch_bounds__(256) k_adj_final(const float *partials, long long count,
+                                                   float *grad, float *grad_abs)
+{
+    __shared__ float red[8][NPART];
+    float hi[NG], lo[NG], ab[NG];
+#pragma unroll
+    for (int m = 0; m < NG; m++) hi[m] = lo[m] = ab[m] = 0.f;
+    for (long long i = threadIdx.x; i < count; i += blockDim.x)
+#pragma unroll
+        for (int m = 0; m < NG; m++) {
+            add_pair(hi[m], lo[m], partials[i * NPART + 3 * m], partials[i * NPART + 3 * m + 1]);
+            ab[m] = __fadd_rn(ab[m], partials[i * NPART + 3 * m + 2]);
+        }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int m = 0; m < NG; m++) {
+            const float bh = __shfl_down_sync(0xffffffffu, hi[m], off);
+            const float bl = __shfl_down_sync(0xffffffffu, lo[m], off);
+            const float bb = __shfl_down_sync(0xffffffffu, ab[m], off);
+            add_pair(hi[m], lo[m], bh, bl);
+            ab[m] = __fadd_rn(ab[m], bb);
+        }
+    if (lane == 0)
+#pragma unroll
+        for (int m = 0; m < NG; m++) {
+            red[wid][3 * m] = hi[m];
+            red[wid][3 * m + 1] = lo[m];
+            red[wid][3 * m + 2] = ab[m];
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int m = 0; m < NG; m++) {
+            float h = red[0][3 * m], l = red[0][3 * m + 1], s = red[0][3 * m + 2];
+            for (int w = 1; w < 8; w++) {
+                add_pair(h, l, red[w][3 * m], red[w][3 * m + 1]);
+                s = __fadd_rn(s, red[w][3 * m + 2]);
+            }
+            grad[m] = __fadd_rn(h, l);
+            if (grad_abs) grad_abs[m] = s;
+        }
+    }
+}
+
+int status(cudaError_t e)
+{
+    if (e == cudaSuccess) return ST_OK;
+    if (e == cudaErrorMemoryAllocation) return ST_ERR_OOM;
+    return ST_ERR_CUDA;
+}
+
+}  // namespace
+
+struct stencil_adjoint_s {
+    int kind = 0, nx = 0, ny = 0, steps = 0, ckpt = 0, nseg = 0;
+    cudaStream_t stream = nullptr;
+    stencil_plan fwd = nullptr, step = nullptr;
+    float *ck = nullptr;      // nseg checkpoints: u at 0, K, 2K, ...
+    float *seg = nullptr;     // K recomputed states of one segment
+    float *lam[2] = {nullptr, nullptr};
+    float *partials = nullptr;
+    long long blocks = 0, passes = 0;
+    float coef[5] = {0, 0, 0, 0, 0};
+    bool have_forward = false;
+};
+
+extern "C" {
+
+int stencil_adjoint_create(stencil_adjoint *out, int kind, int nx, int ny, int steps, int ckpt,
+                           void *stream)
+{
+    if (!out) return ST_ERR_INVALID_ARG;
+    *out = nullptr;
+    if ((kind != ST_DIFFUSION && kind != ST_THERMAL) || nx < 1 || ny < 1 || steps < 0 ||
+        ckpt < 1)
+        return ST_ERR_INVALID_ARG;
+    if ((long long)nx * ny > (1LL << 31)) return ST_ERR_INVALID_ARG;
+    stencil_adjoint_s *a = new (std::nothrow) stencil_adjoint_s;
+    if (!a) return ST_ERR_OOM;
+    a->kind = kind;
+    a->nx = nx;
+    a->ny = ny;
+    a->steps = steps;
+    a->ckpt = std::min(ckpt, std::max(steps, 1));
+    a->nseg = steps > 0 ? (steps + a->ckpt - 1) / a->ckpt : 0;
+    a->stream = static_cast<cudaStream_t>(stream);
+    const int ntx = (nx + ACX - 1) / ACX, nty = (ny + ACY - 1) / ACY;
+    a->blocks = (long long)ntx * nty;
+    for (int sg = 0; sg < a->nseg; sg++) {
+        const int len = std::min(steps, (sg + 1) * a->ckpt) - sg * a->ckpt;
+        a->passes += (len + ATA - 1) / ATA;
+    }
+    int rc = ST_OK;
+    stencil_desc d = {};
+    d.kind = kind;
+    d.ndim = 2;
+    d.nx = nx;
+    d.ny = ny;
+    d.nz = 1;
+    d.storage = ST_F32;
+    d.stream = stream;
+    rc = stencil_plan_create(&a->fwd, &d);
+    if (rc == ST_OK) {
+        d.force_T = 1;
+        rc = stencil_plan_create(&a->step, &d);
+    }
+    const size_t n = (size_t)nx * ny * sizeof(float);
+    cudaError_t e = cudaSuccess;
+    if (rc == ST_OK && a->nseg > 0) {
+        e = cudaMalloc(&a->ck, n * a->nseg);
+        if (e == cudaSuccess) e = cudaMalloc(&a->seg, n * a->ckpt);
+        if (e == cudaSuccess) e = cudaMalloc(&a->lam[0], n);
+        if (e == cudaSuccess) e = cudaMalloc(&a->lam[1], n);
+        if (e == cudaSuccess)
+            e = cudaMalloc(&a->partials, sizeof(float) * NPART * (size_t)(a->blocks * a->passes));
+        if (e == cudaSuccess) {
+            const int smem = 2 * AX * AY * (int)sizeof(float);
+            e = cudaFuncSetAttribute(k_adj2d<ST_DIFFUSION>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_adj2d<ST_THERMAL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        }
+        if (e != cudaSuccess) rc = status(e);
+    }
+    if (rc != ST_OK) {
+        stencil_adjoint_destroy(a);
+        return rc;
+    }
+    *out = a;
+    return ST_OK;
+}
+
+int stencil_adjoint_forward(stencil_adjoint a, const float *u0, const float *power,
+                            const float *coeffs, float *u_out)
+{
+    if (!a || !u0 || !coeffs || !u_out) return ST_ERR_INVALID_ARG;
+    if (a->kind == ST_THERMAL && !power) return ST_ERR_INVALID_ARG;
+    if (a->kind == ST_DIFFUSION && power) return ST_ERR_INVALID_ARG;
+    const size_t n = (size_t)a->nx * a->ny * sizeof(float);
+    for (int i = 0; i < 5; i++) a->coef[i] = coeffs[i];
+    a->have_forward = false;
+    if (a->nseg == 0) {
+        if (u_out != u0) {
+            cudaError_t e = cudaMemcpyAsync(u_out, u0, n, cudaMemcpyDeviceToDevice, a->stream);
+            if (e != cudaSuccess) return status(e);
+        }
+        a->have_forward = true;
+        return ST_OK;
+    }
+    cudaError_t e = cudaMemcpyAsync(a->ck, u0, n, cudaMemcpyDeviceToDevice, a->stream);
+    if (e != cudaSuccess) return status(e);
+    const long long cells = (long long)a->nx * a->ny;
+    for (int sg = 0; sg < a->nseg; sg++) {
+        const int len = std::min(a->steps, (sg + 1) * a->ckpt) - sg * a->ckpt;
+        float *dst = sg + 1 < a->nseg ? a->ck + (sg + 1) * cells : u_out;
+        const int rc = stencil_run(a->fwd, a->ck + sg * cells, dst, power, a->coef, a->nx, a->ny,
+                                   1, len);
+        if (rc != ST_OK) return rc;
+    }
+    a->have_forward = true;
+    return ST_OK;
+}
+
+int stencil_adjoint_backward(stencil_adjoint a, const float *grad_out, const float *power,
+                             float *grad_u0, float *grad_coeffs, float *grad_coeffs_abs,
+                             float *grad_power)
+{
+    if (!a || !grad_out || !grad_u0 || !grad_coeffs) return ST_ERR_INVALID_ARG;
+    if (!a->have_forward) return ST_ERR_INVALID_ARG;
+    if (a->kind == ST_THERMAL && (!power || !grad_power)) return ST_ERR_INVALID_ARG;
+    if (a->kind == ST_DIFFUSION && (power || grad_power)) return ST_ERR_INVALID_ARG;
+    const long long cells = (long long)a->nx * a->ny;
+    const size_t n = (size_t)cells * sizeof(float);
+    cudaError_t e = cudaSuccess;
+    if (grad_power) e = cudaMemsetAsync(grad_power, 0, n, a->stream);
+    if (e == cudaSuccess && a->nseg == 0) {
+        e = cudaMemcpyAsync(grad_u0, grad_out, n, cudaMemcpyDeviceToDevice, a->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(grad_coeffs, 0, NG * sizeof(float), a->stream);
+        if (e == cudaSuccess && grad_coeffs_abs)
+            e = cudaMemsetAsync(grad_coeffs_abs, 0, NG * sizeof(float), a->stream);
+        return status(e);
+    }
+    if (e != cudaSuccess) return status(e);
+
+    AdjPass p = {};
+    p.n = cells;
+    p.pw = power;
+    p.gpw = grad_power;
+    p.nx = a->nx;
+    p.ny = a->ny;
+    p.ntx = (a->nx + ACX - 1) / ACX;
+    for (int i = 0; i < 5; i++) p.k[i] = a->coef[i];
+    if (a->kind == ST_DIFFUSION) {
+        p.wc = a->coef[0];
+        p.ww = a->coef[1];
+        p.we = a->coef[2];
+        p.ws = a->coef[3];
+        p.wn = a->coef[4];
+    } else {
+        // Hotspot: F = c + k_dt (p + (n+s-2c) Ry + (e+w-2c) Rx + (amb-c) Rz)
+        const double kdt = a->coef[0], rx = a->coef[1], ry = a->coef[2], rz = a->coef[3];
+        p.wc = (float)(1.0 - kdt * (2.0 * ry + 2.0 * rx + rz));
+        p.ww = p.we = (float)(kdt * rx);
+        p.ws = p.wn = (float)(kdt * ry);
+    }
+    const int smem = 2 * AX * AY * (int)sizeof(float);
+    const float *lin = grad_out;
+    int which = 0;
+    long long pass = 0;
+    for (int sg = a->nseg - 1; sg >= 0 && e == cudaSuccess; sg--) {
+        const int t0 = sg * a->ckpt, t1 = std::min(a->steps, t0 + a->ckpt), len = t1 - t0;
+        // recompute u_{t0} .. u_{t1-1} into the segment buffer
+        e = cudaMemcpyAsync(a->seg, a->ck + sg * cells, n, cudaMemcpyDeviceToDevice, a->stream);
+        for (int k = 1; k < len && e == cudaSuccess; k++) {
+            const int rc = stencil_run(a->step, a->seg + (k - 1) * cells, a->seg + k * cells,
+                                       power, a->coef, a->nx, a->ny, 1, 1);
+            if (rc != ST_OK) return rc;
+        }
+        int t_hi = t1;
+        while (t_hi > t0 && e == cudaSuccess) {
+            const int ns = std::min(ATA, t_hi - t0);
+            p.lam_in = lin;
+            p.lam_out = a->lam[which];
+            p.states = a->seg;
+            p.k_hi = t_hi - 1 - t0;
+            p.nsteps = ns;
+            p.partials = a->partials + (size_t)pass * a->blocks * NPART;
+            if (a->kind == ST_DIFFUSION)
+                k_adj2d<ST_DIFFUSION><<<(unsigned)a->blocks, ANT, smem, a->stream>>>(p);
+            else
+                k_adj2d<ST_THERMAL><<<(unsigned)a->blocks, ANT, smem, a->stream>>>(p);
+            e = cudaGetLastError();
+            lin = a->lam[which];
+            which ^= 1;
+            t_hi -= ns;
+            pass++;
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(grad_u0, lin, n, cudaMemcpyDeviceToDevice, a->stream);
+    if (e == cudaSuccess) {
+        k_adj_final<<<1, 256, 0, a->stream>>>(a->partials, pass * a->blocks, grad_coeffs,
+                                              grad_coeffs_abs);
+        e = cudaGetLastError();
+    }
+    return status(e);
+}
+
+int stencil_adjoint_destroy(stencil_adjoint a)
+{
+    if (!a) return ST_OK;
+    if (a->stream) cudaStreamSynchronize(a->stream);
+    else cudaDeviceSynchronize();
+    if (a->fwd) stencil_plan_destroy(a->fwd);
+    if (a->step) stencil_plan_destroy(a->step);
+    if (a->ck) cudaFree(a->ck);
+    if (a->seg) cudaFree(a->seg);
+    for (float *l : a->lam)
+        if (l) cudaFree(l);
+    if (a->partials) cudaFree(a->partials);
+    delete a;
+    return ST_OK;
+}
+
+}  // extern "C"
