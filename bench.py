@@ -39,6 +39,7 @@ FLOPS = {(0, 2): 9, (0, 3): 13, (1, 2): 15, (1, 3): 17}
 BYTES = {0: 8, 1: 12}
 
 BATCH = "batch64"   # 64 2D grids of uneven sizes and step counts in one graph launch
+ADJOINT = "adjoint2048"   # gradient of a 2048^2, 200-step diffusion run, checkpoints every 20
 
 WORKLOADS = {
     "thermal2d_16384": lambda: synth.c2_thermal2d(),
@@ -351,12 +352,162 @@ def bench_batch(args):
         dist.destroy_process_group()
 
 
+def bench_adjoint(args, ckpt=20):
+    """Gradient of L = sum(w * u_200) for a 2048^2 diffusion run: one step = the checkpointed
+    forward run plus the backward sweep (state recompute, transposed passes, reductions).
+    value = primal cell updates (cells x 200) per second of a whole gradient evaluation."""
+    w = synth.c5b_adjoint2d()
+    wt = synth.loss_weights(6, w.shape)
+    n = w.cells
+    if args.impl == "reference" or not args.no_cpu:
+        import oracle
+        oracle.build()
+        cores = len(os.sched_getaffinity(0))
+        oracle.set_threads(cores)
+        side, s = 512, 20   # bounded sample: a 512^2, 20-step gradient (checkpoints every 20)
+        ws = synth.make(w.kind, 2, side, side, 1, s, seed=w.seed)
+        wts = synth.loss_weights(6, ws.shape)
+        reps = args.steps if args.impl == "reference" else 1
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            oracle.adjoint2d(ws.kind, ws.u0, ws.coef, s, wts, None, ckpt=ckpt)
+        t = (time.perf_counter() - t0) / reps
+        cpu = {"value": side * side * s / t / 1e9, "unit": "GCell/s", "cores": cores,
+               "kind": "oracle", "sample": f"float64 adjoint of a {side}^2, {s}-step diffusion "
+                                             f"run (the transposed sweep is one thread)"}
+        if args.impl == "reference":
+            if int(os.environ.get("RANK", "0")) == 0:
+                print(json.dumps({"impl": "reference", "metric": "stencil GCell/s & GFLOP/s vs roofline",
+                                  "value": cpu["value"], "unit": "GCell/s", "n_gpus": args.gpus,
+                                  "steps": args.steps, "warmup": args.warmup,
+                                  "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                                  "config": {"workload": ADJOINT}, "cpu_baseline": cpu,
+                                  "e2e": {"value": cpu["value"], "unit": "GCell/s",
+                                          "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+                      flush=True)
+            return
+    else:
+        cpu = None
+    import torch
+    import paper_1802_00438_gb300 as st
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    u0 = torch.from_numpy(w.u0).to(dev)
+    g = torch.from_numpy(wt).to(dev)
+    adj = st.Adjoint(w.kind, w.nx, w.ny, w.steps, ckpt, stream=stream.cuda_stream)
+    out = torch.empty_like(u0)
+    gu = torch.empty_like(u0)
+    gk = torch.empty(5, dtype=torch.float32, device=dev)
+
+    def step():
+        st.stencil_adjoint_forward(adj.h, u0, None, w.coef, out)
+        st.stencil_adjoint_backward(adj.h, g, None, gu, gk, None, None)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        # forward alone, for the split
+        e0b = torch.cuda.Event(enable_timing=True)
+        e0b.record(stream)
+        for _ in range(args.steps):
+            st.stencil_adjoint_forward(adj.h, u0, None, w.coef, out)
+        f1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    fms = e0b.elapsed_time(f1)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    per = ms / args.steps
+    bwd = per - fms / args.steps
+    value = world * n * w.steps / (per * 1e-3) / 1e9
+    # algorithmic HBM bytes of the backward: per transposed pass of s steps lambda in + out
+    # (8 B) and the s states (4 B each); per recomputed state one read and one write (8 B); the
+    # checkpoint copy into the state buffer (8 B) per segment; grad_u0 copy (8 B)
+    nseg = -(-w.steps // ckpt)
+    seg_len = [min(w.steps, (k + 1) * ckpt) - k * ckpt for k in range(nseg)]
+    bytes_b = 0
+    for L in seg_len:
+        bytes_b += n * (8 * (L - 1) + 8)
+        left = L
+        while left > 0:
+            s = min(4, left)
+            bytes_b += n * (8 + 4 * s)
+            left -= s
+    bytes_b += 8 * n
+    peaks, src = load_peaks()
+    gbs = bytes_b / (bwd * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": gbs, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+            "frac": gbs / float(peaks["hbm_gbs"]), "traffic": None,
+            "note": "whole backward (state recompute + transposed passes): algorithmic bytes / "
+                    "backward time (step time minus the checkpointed forward run)"}
+    # end to end: initial field and upstream gradient from pinned host memory, gradients back
+    h_u = torch.from_numpy(w.u0).pin_memory()
+    h_g = torch.from_numpy(wt).pin_memory()
+    h_gu = torch.empty_like(h_u).pin_memory()
+    h_gk = torch.empty(5, dtype=torch.float32).pin_memory()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(args.steps):
+        u0.copy_(h_u, non_blocking=True)
+        g.copy_(h_g, non_blocking=True)
+        step()
+        h_gu.copy_(gu, non_blocking=True)
+        h_gk.copy_(gk, non_blocking=True)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ems = a0.elapsed_time(a1)
+    e2e = {"value": world * n * w.steps / (ems / args.steps * 1e-3) / 1e9, "unit": "GCell/s",
+           "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 4 * n + 20}
+    fwd_T = st.Plan(w.kind, 2, w.nx, w.ny).info()["T"]
+    launches = sum(-(-L // fwd_T) for L in seg_len)            # forward passes
+    launches += sum(L - 1 for L in seg_len)                      # recomputed states
+    launches += sum(-(-L // 4) for L in seg_len) + 1             # transposed passes + final sum
+    if rank == 0:
+        print(json.dumps({"metric": "stencil GCell/s & GFLOP/s vs roofline", "value": value,
+                          "unit": "GCell/s", "n_gpus": world, "steps": args.steps,
+                          "warmup": args.warmup, "ms_per_step": per, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                          "data": "synthetic",
+                          "config": {"workload": ADJOINT, "grid": f"{w.nx}x{w.ny}",
+                                     "time_steps": w.steps, "checkpoint_every": ckpt,
+                                     "forward_ms": fms / args.steps, "backward_ms": bwd,
+                                     "l2": "inputs larger than L2 (200-state sweep over 16 MiB "
+                                           "grids; 496 MiB of buffers)"},
+                          "roofline": roof, "e2e": e2e, "gpu_launches": launches * args.steps,
+                          "clocks": clk.summary(), "cpu_baseline": cpu}), flush=True)
+    adj.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + [BATCH])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + [BATCH, ADJOINT])
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--T", type=int, default=0, help="force the fused step count")
     ap.add_argument("--bx", type=int, default=0, help="force the 2D tile width")
@@ -374,6 +525,8 @@ def main():
 
     if args.workload == BATCH:
         return bench_batch(args)
+    if args.workload == ADJOINT:
+        return bench_adjoint(args)
     w = WORKLOADS[args.workload]()
     resized = bool(args.nx or args.ny or args.nz or args.time_steps)
     if resized:

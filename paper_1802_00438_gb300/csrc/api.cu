@@ -51,7 +51,8 @@ struct stencil_plan_s {
     int V = 4, W = 4;
     std::vector<PassCfg2D> cfg2;   // indexed by kernel T
     // 3D
-    int VY = 8, NW = 8, alg3 = 0;
+    int VY = 8, NW = 8, alg3 = 0, VX3 = 2;
+    int *err = nullptr;   // device flag set by a kernel whose bounded wait gave up
     std::vector<PassCfg3D> cfg3;
     // timing
     bool timing = false;
@@ -93,7 +94,7 @@ bool available(const stencil_plan_s *p, int T)
 {
     if (p->d.ndim == 2)
         return tb2d_available(Shape2D{p->d.kind, p->d.exact ? 1 : 0, T, p->V, p->W, p->stor});
-    return tb3d_available(Shape3D{p->d.kind, p->d.exact ? 1 : 0, T, p->VY, p->NW, p->alg3});
+    return tb3d_available(Shape3D{p->d.kind, p->d.exact ? 1 : 0, T, p->VY, p->NW, p->alg3, p->VX3});
 }
 
 // ---- parameter choice seeded by the GPU restatement of the paper's model (Eqs. 3-9) -------
@@ -201,14 +202,14 @@ int prepare3(stencil_plan_s *p, int Tk, PassCfg3D **out)
     if ((int)p->cfg3.size() <= Tk) p->cfg3.resize(Tk + 1);
     PassCfg3D &c = p->cfg3[Tk];
     if (!c.ready) {
-        c.shape = Shape3D{p->d.kind, p->d.exact ? 1 : 0, Tk, p->VY, p->NW, p->alg3};
+        c.shape = Shape3D{p->d.kind, p->d.exact ? 1 : 0, Tk, p->VY, p->NW, p->alg3, p->VX3};
         if (!tb3d_available(c.shape)) return ST_ERR_UNSUPPORTED;
         int bps = 0;
         cudaError_t e = tb3d_prepare(c.shape, &bps);
         if (e != cudaSuccess) return map_cuda(e);
         if (bps < 1) return ST_ERR_UNSUPPORTED;
         const int hx = (Tk + 3) / 4 * 4, hy = Tk;
-        const int cx = 64 - 2 * hx, cy = p->VY * p->NW - 2 * hy;
+        const int cx = 32 * p->VX3 - 2 * hx, cy = p->VY * p->NW - 2 * hy;
         c.ntx = (p->d.nx + cx - 1) / cx;
         c.nty = (p->d.ny + cy - 1) / cy;
         c.cols = (long long)c.ntx * c.nty;
@@ -376,12 +377,22 @@ int run_pass3(stencil_plan_s *p, const float *src, float *dst, const float *pw, 
     for (int i = 0; i < 9; i++) a.k[i] = i < ncoef(p->d) ? k[i] : 0.f;
     a.vec = ((uintptr_t)src % 16 == 0) && ((uintptr_t)dst % 16 == 0) && (p->d.nx % 4 == 0);
     a.vec_pw = pw && ((uintptr_t)pw % 16 == 0) && (p->d.nx % 4 == 0);
+    a.err = p->err;
+    a.use_tma = 0;
+    Tma3D tm;
+    std::memset(&tm, 0, sizeof(tm));
+    if (p->alg3 && a.vec) {
+        const int bx = 32 * p->VX3, by = p->VY * p->NW;
+        bool ok = tma3d_encode(&tm.in, src, p->d.nx, p->d.ny, p->d.nz, bx, by);
+        if (ok && pw) ok = a.vec_pw && tma3d_encode(&tm.pw, pw, p->d.nx, p->d.ny, p->d.nz, bx, by);
+        a.use_tma = ok ? 1 : 0;
+    }
     if (p->timing && p->ev_used + 2 > 2 * 1024) {
         rc = flush_timing(p);
         if (rc != ST_OK) return rc;
     }
     cudaError_t e = record(p, true);
-    if (e == cudaSuccess) e = tb3d_launch(c->shape, a, p->stream);
+    if (e == cudaSuccess) e = tb3d_launch(c->shape, a, tm, p->stream);
     if (e == cudaSuccess) e = record(p, false);
     return map_cuda(e);
 }
@@ -517,21 +528,21 @@ int stencil_plan_create(stencil_plan *out, const stencil_desc *desc)
             p->scratch_bytes = (size_t)p->ld_scratch * d.ny * sizeof(float);
         }
     } else {
-        if (d.force_bx && d.force_bx != 64) rc = ST_ERR_UNSUPPORTED;
-        if (d.force_by && d.force_by != 64) rc = ST_ERR_UNSUPPORTED;
-        // cells per thread: 16 = 8 rows x 2 (three-plane windows, exact or contracted);
-        // 8 = 4 rows x 2 and 4 = 2 rows x 2 (partial sums along z, contracted)
+        // tile width 64 (2 cells per lane) or 128 (4 cells per lane), tile height, cells per
+        // thread; 64 x 64 with 16 cells per thread is the three-plane-window kernel (exact or
+        // contracted), every other shape the partial-sum kernel (contracted)
+        const int bx = d.force_bx ? d.force_bx : 64;
+        const int by = d.force_by ? d.force_by : (bx == 128 ? 32 : 64);
         const int cells = d.force_vec ? d.force_vec : (d.exact ? 16 : 8);
-        if (cells == 16) {
-            p->VY = 8;
-            p->NW = 8;
-            p->alg3 = 0;
-        } else if (!d.exact && (cells == 8 || cells == 4)) {
-            p->VY = cells / 2;
-            p->NW = 64 / p->VY;
-            p->alg3 = 1;
-        } else {
+        if (bx != 64 && bx != 128) rc = ST_ERR_UNSUPPORTED;
+        p->VX3 = bx / 32;
+        if (rc == ST_OK && (cells % p->VX3 != 0 || by % (cells / p->VX3) != 0))
             rc = ST_ERR_UNSUPPORTED;
+        if (rc == ST_OK) {
+            p->VY = cells / p->VX3;
+            p->NW = by / p->VY;
+            p->alg3 = (p->VX3 == 2 && p->VY == 8 && p->NW == 8) ? 0 : 1;
+            if (p->alg3 && d.exact) rc = ST_ERR_UNSUPPORTED;
         }
         // contracted default: T = 3 (512^3 diffusion and 512^2 x 256 Hotspot measure best at
         // T = 3 with 4 rows x 2 cells per thread; the x halo is rounded up to 4 anyway)
@@ -544,6 +555,11 @@ int stencil_plan_create(stencil_plan *out, const stencil_desc *desc)
     }
     if (rc == ST_OK && p->scratch_bytes) {
         e = cudaMalloc(&p->scratch, p->scratch_bytes);
+        if (e != cudaSuccess) rc = map_cuda(e);
+    }
+    if (rc == ST_OK) {
+        e = cudaMalloc(&p->err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(p->err, 0, sizeof(int));
         if (e != cudaSuccess) rc = map_cuda(e);
     }
     if (rc != ST_OK) {
@@ -638,6 +654,15 @@ int stencil_plan_sync(stencil_plan p)
     if (!p) return ST_ERR_INVALID_ARG;
     cudaError_t e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return map_cuda(e);
+    if (p->err) {
+        int flag = 0;
+        e = cudaMemcpy(&flag, p->err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return map_cuda(e);
+        if (flag) {
+            (void)cudaMemset(p->err, 0, sizeof(int));
+            return ST_ERR_TIMEOUT;
+        }
+    }
     return p->sticky;
 }
 
@@ -664,10 +689,10 @@ int stencil_plan_get_info(stencil_plan p, stencil_plan_info *info)
         PassCfg3D *c = nullptr;
         int rc = prepare3(p, p->T, &c);
         if (rc != ST_OK) return rc;
-        info->bx = 64;
+        info->bx = 32 * p->VX3;
         info->by = p->VY * p->NW;
         info->halo = p->T;
-        info->vec = 2 * p->VY;
+        info->vec = p->VX3 * p->VY;
         info->warps = p->NW;
         info->ctas = c->ctas;
         info->kernel_id = p->alg3 ? 4 : 3;
@@ -708,6 +733,7 @@ int stencil_plan_destroy(stencil_plan p)
     }
     if (p->qp) cudaFree(p->qp);
     if (p->qpm) cudaFree(p->qpm);
+    if (p->err) cudaFree(p->err);
     delete p;
     return ST_OK;
 }

@@ -1,5 +1,6 @@
 // Interface between the host runtime (api.cu) and the kernel translation units.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace stn {
@@ -79,17 +80,27 @@ struct Pass3D {
     float k[9];
     int vec;               // 1: rows start on 16-byte boundaries
     int vec_pw;            // 1: the power map's rows start on 16-byte boundaries
+    int use_tma;           // partial-sum kernel: stage planes with tensor-map bulk copies
+    int *err;              // device flag: a bounded wait gave up (set to 1)
 };
 
-// tile 64 x (VY*NW) cells; alg 0: three-plane register windows (k_tb3d, exact or contracted),
-// alg 1: partial sums along z (k_tb3f, contracted only)
-struct Shape3D { int kind, exact, T, VY, NW; int alg = 0; };
+// Tensor maps of the field and power grids (x, y, z; box = one tile plane) for use_tma.
+struct Tma3D {
+    CUtensorMap in, pw;
+};
+
+// tile (32*VX) x (VY*NW) cells; alg 0: three-plane register windows (k_tb3d, VX = 2, exact or
+// contracted), alg 1: partial sums along z (k_tb3f, contracted only)
+struct Shape3D { int kind, exact, T, VY, NW; int alg = 0; int VX = 2; };
 
 bool tb3d_available(const Shape3D &s);
 int tb3d_block_threads(const Shape3D &s);
 int tb3d_halo(const Shape3D &s);
 size_t tb3d_smem_bytes(const Shape3D &s);
 cudaError_t tb3d_prepare(const Shape3D &s, int *blocks_per_sm);
-cudaError_t tb3d_launch(const Shape3D &s, const Pass3D &p, cudaStream_t st);
+cudaError_t tb3d_launch(const Shape3D &s, const Pass3D &p, const Tma3D &t, cudaStream_t st);
+// encode the tensor map of a (nx, ny, nz) float32 grid with a (bx, by, 1) box; false if the
+// driver entry point or the encoding is unavailable
+bool tma3d_encode(CUtensorMap *m, const float *base, int nx, int ny, int nz, int bx, int by);
 
 }  // namespace stn

@@ -170,6 +170,12 @@ def c3b_thermal3d(nx=512, ny=512, nz=256, steps=1000):
     return make(THERMAL, 3, nx, ny, nz, steps, seed=4, name=f"thermal3d_{nx}x{ny}x{nz}_{steps}")
 
 
+def c5b_adjoint2d(n=2048, steps=200):
+    """Adjoint case: 2D diffusion, 2048^2, 200 steps (checkpoints every 20), seed 6; the loss
+    weights come from loss_weights(6, shape)."""
+    return make(DIFFUSION, 2, n, n, 1, steps, seed=6, name=f"adjoint2d_{n}x{n}_{steps}")
+
+
 def c5a_batch_specs(count=64, seed=5):
     """Shapes of the batched workload: per grid (kind, nx, ny, steps, seed).
 

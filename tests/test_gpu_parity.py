@@ -85,16 +85,22 @@ def test_contracted_2d(eng, orc, kind, T, bx):
             assert max_rel(g, o) <= TOL, (nx, ny, steps, max_rel(g, o))
 
 
+SHAPES_3D = [(64, 16, T) for T in (1, 2, 3, 4)] + [(64, 8, T) for T in (1, 2, 3, 4)] + \
+    [(64, 4, T) for T in (2, 3, 4)] + [(128, 8, T) for T in (2, 3, 4)]
+
+
 @pytest.mark.parametrize("kind", [0, 1])
-@pytest.mark.parametrize("T", [1, 2, 3, 4])
-@pytest.mark.parametrize("vec", [16, 8, 4])
-def test_contracted_3d(eng, orc, kind, T, vec):
-    # vec 16: three-plane windows; 8 and 4: partial sums along z (2 cells x 4 or 2 rows)
-    for t, (nx, ny, nz) in enumerate(SIZES_3D[:2] + SIZES_3D[3:] + [(203, 150, 37)]):
+@pytest.mark.parametrize("bx,vec,T", SHAPES_3D)
+def test_contracted_3d(eng, orc, kind, bx, vec, T):
+    # 64 x 64 tiles: vec 16 = three-plane windows; 8 and 4 = partial sums along z (2 cells x
+    # 4 or 2 rows); 128 x 32 tiles: 4 cells x 2 rows, partial sums
+    # rows of a multiple of 4 cells (132, 200) are staged by tensor-map copies, others by cp.async
+    for t, (nx, ny, nz) in enumerate(SIZES_3D[:2] + SIZES_3D[3:] + [(203, 150, 37), (132, 70, 21),
+                                                                    (200, 33, 17)]):
         w = synth.make(kind, 3, nx, ny, nz, seed=4000 + 43 * t + kind)
         for steps in (1, T + 2, 3 * T + 1):
-            g, info = gpu_run(eng, w, steps, T=T, vec=vec)
-            assert info["vec"] == vec and info["T"] == T
+            g, info = gpu_run(eng, w, steps, T=T, vec=vec, bx=bx)
+            assert info["vec"] == vec and info["T"] == T and info["bx"] == bx
             o = orc.run(kind, w.u0, w.coef, steps, w.power)
             assert max_rel(g, o) <= TOL, (nx, ny, nz, steps, max_rel(g, o))
 
@@ -105,9 +111,10 @@ def test_contracted_3d_in_place_unaligned(eng, orc, kind):
     place, with an odd and an even pass count."""
     w = synth.make(kind, 3, 67, 45, 23, seed=4500 + kind)
     for steps in (5, 8):
-        g, _ = gpu_run(eng, w, steps, T=4, vec=8, inplace=True)
         o = orc.run(kind, w.u0, w.coef, steps, w.power)
-        assert max_rel(g, o) <= TOL, (steps, max_rel(g, o))
+        for bx in (64, 128):
+            g, _ = gpu_run(eng, w, steps, T=4, vec=8, bx=bx, inplace=True)
+            assert max_rel(g, o) <= TOL, (steps, bx, max_rel(g, o))
 
 
 @pytest.mark.parametrize("ndim", [2, 3])
