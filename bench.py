@@ -118,7 +118,7 @@ class Clocks:
 def kernel_source_hash(ndim: int) -> str:
     """Hash of the sources of the benchmarked kernel family (2D contracted or 3D)."""
     files = (("tb2f_kernel.cuh", "tb2d_kernel.cuh", "common.cuh") if ndim == 2
-             else ("tb3d_kernel.cuh", "common.cuh"))
+             else ("tb3f_kernel.cuh", "tb3d_kernel.cuh", "common.cuh"))
     h = hashlib.sha1()
     for f in files:
         h.update(open(os.path.join(ROOT, "paper_1802_00438_gb300", "csrc", f), "rb").read())

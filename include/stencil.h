@@ -205,12 +205,17 @@ int stencil_adjoint_forward(stencil_adjoint a, const float *u0, const float *pow
  *   grad_coeffs_abs : 5 floats or NULL: sum over (t, i) of |lambda_{t+1}[i] dF_i/dcoeff_m|,
  *                     the scale the rounding error of grad_coeffs[m] is relative to
  *   grad_power      : dL/dpower, nx*ny floats (ST_THERMAL; NULL for ST_DIFFUSION)
- * Coefficient gradients are float32 error-free-transformation sums in a fixed order:
- * deterministic for a given size.  Errors: ST_ERR_INVALID_ARG (no forward run yet, missing or
+ * Coefficient gradients are float32 sums in a fixed order (per thread at most 64 terms, then
+ * error-free pairwise combination): deterministic for a given size.  Errors: ST_ERR_INVALID_ARG (no forward run yet, missing or
  * unexpected pointers), ST_ERR_CUDA. */
 int stencil_adjoint_backward(stencil_adjoint a, const float *grad_out, const float *power,
                              float *grad_u0, float *grad_coeffs, float *grad_coeffs_abs,
                              float *grad_power);
+
+/* Wait for the object's stream; returns ST_ERR_TIMEOUT if a kernel's bounded wait for staged
+ * data gave up since the last call (the gradients of that backward run are invalid), ST_ERR_CUDA
+ * on an asynchronous CUDA error, else ST_OK. */
+int stencil_adjoint_sync(stencil_adjoint a);
 
 /* Wait for the object's stream and free everything it owns.  NULL is accepted. */
 int stencil_adjoint_destroy(stencil_adjoint a);

@@ -133,6 +133,7 @@ SIGNATURES = {
     "stencil_adjoint_create": ([ctypes.POINTER(_P), _I, _I, _I, _I, _I, _P], _I),
     "stencil_adjoint_forward": ([_P, _P, _P, ctypes.POINTER(ctypes.c_float), _P], _I),
     "stencil_adjoint_backward": ([_P, _P, _P, _P, _P, _P, _P], _I),
+    "stencil_adjoint_sync": ([_P], _I),
     "stencil_adjoint_destroy": ([_P], _I),
 }
 
@@ -386,6 +387,10 @@ def stencil_adjoint_backward(adj, grad_out, power, grad_u0, grad_coeffs, grad_co
                                         _addr(grad_power)), "stencil_adjoint_backward")
 
 
+def stencil_adjoint_sync(adj):
+    _check(lib.stencil_adjoint_sync(adj), "stencil_adjoint_sync")
+
+
 def stencil_adjoint_destroy(adj):
     _check(lib.stencil_adjoint_destroy(adj), "stencil_adjoint_destroy")
 
@@ -414,6 +419,9 @@ class Adjoint:
         gp = torch.empty_like(grad_out) if self.kind == ST_THERMAL else None
         stencil_adjoint_backward(self.h, grad_out, power, gu, gk, ga, gp)
         return gu, gk, gp, ga
+
+    def sync(self):
+        stencil_adjoint_sync(self.h)
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

@@ -14,23 +14,28 @@
 // GPU design.  The reverse sweep is temporally blocked like the forward sweep (Sec. 3.2): a
 // pass loads a 128 x 64 tile of lambda_{t+TA} with a halo of TA cells into shared memory and
 // applies TA transposed steps there (ping-pong buffers, redundant halo work, only the compute
-// block written).  The same pass accumulates the coefficient and power gradients of its compute
-// block from the forward states u_t, which are recomputed from checkpoints every K steps into a
-// K-state buffer (the forward plans of this library, T = 1 per state).  Coefficient gradients
-// are float32 error-free-transformation sums (TwoProd by fma, TwoSum): each thread keeps a
-// (hi, lo) pair per coefficient, blocks combine pairs in a fixed tree, and one final kernel
-// combines all (pass, block) pairs in a fixed order, so results are deterministic and carry
-// roughly twice float32's precision without float64 arithmetic.  Alongside each gradient the
+// block written).  With rows on 16-byte boundaries the lambda tile, the power tile and the
+// state tile u_t of every fused step arrive by tensor-map bulk copies (one elected thread,
+// mbarrier completion, the next state's tile in flight while the current step computes);
+// otherwise the kernel reads them with plain loads.  The same pass accumulates the coefficient
+// and power gradients of its compute block from the forward states u_t, which are recomputed
+// from checkpoints every K steps into a K-state buffer (the forward plans of this library, T = 1 per state).  Coefficient gradients
+// are float32 sums in a fixed order: each thread sums its own cells and steps of a pass (at most
+// 64 terms, fused multiply-adds), then blocks and one final kernel combine those partial sums
+// as (hi, lo) pairs with error-free transformations (TwoSum) in a fixed tree, so results are
+// deterministic and the rounding of the combination is negligible beside the per-thread sums.  Alongside each gradient the
 // same reduction yields sum |term|, the scale its rounding error is relative to.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <new>
 #include <vector>
 
 #include "../../include/stencil.h"
+#include "internal.h"
 
 namespace {
 
@@ -53,24 +58,57 @@ struct AdjPass {
     float wc, ww, we, ws, wn;   // forward weights of c, w, e, s, n
     float k[5];
     float *partials;         // this pass's [block][NPART]
+    int use_tma;             // stage lambda, u and power tiles by tensor-map copies
+    int *err;                // device flag: a bounded wait gave up
 };
+
+__device__ __forceinline__ uint32_t sm32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void bar_init(uint32_t bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void bar_expect(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+// bounded wait for phase `parity` (false: gave up)
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity)
+{
+    for (int n = 0; n < (1 << 22); n++) {
+        uint32_t ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// one (AX x AY) box of plane z of a tensor map into shared memory, completing on `bar`
+__device__ __forceinline__ void tile_copy(uint32_t dst, const CUtensorMap *m, int x, int y, int z,
+                                          uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
 
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
     s = __fadd_rn(a, b);
     const float bb = __fsub_rn(s, a);
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// (hi, lo) += x * y, exactly up to the final renormalisation
-__device__ __forceinline__ void acc_prod(float &hi, float &lo, float x, float y)
-{
-    const float p = __fmul_rn(x, y);
-    const float pe = __fmaf_rn(x, y, -p);   // exact error of the product
-    float s, e;
-    two_sum(hi, p, s, e);
-    lo = __fadd_rn(lo, __fadd_rn(e, pe));
-    two_sum(s, lo, hi, lo);
 }
 
 __device__ __forceinline__ void add_pair(float &hi, float &lo, float bhi, float blo)
@@ -104,23 +142,57 @@ __device__ __forceinline__ void dfdtheta(const AdjPass &a, float c, float w, flo
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(ANT) k_adj2d(const AdjPass a)
+__global__ void __launch_bounds__(ANT) k_adj2d(const AdjPass a, const __grid_constant__ CUtensorMap tl,
+                                               const __grid_constant__ CUtensorMap tu,
+                                               const __grid_constant__ CUtensorMap tp)
 {
-    extern __shared__ __align__(16) float sm[];
+    extern __shared__ __align__(128) float sm[];
+    constexpr uint32_t TILE_B = 4u * AX * AY;
     float *buf0 = sm, *buf1 = sm + AX * AY;
+    float *ubuf = sm + 2 * AX * AY;          // two state tiles
+    float *ptile = sm + 4 * AX * AY;         // power tile (Hotspot)
     __shared__ float red[ANT / 32][NPART];
+    __shared__ __align__(8) uint64_t bars[4];   // lambda, state tile 0, state tile 1, power
     const int tid = threadIdx.x;
     const int tx = blockIdx.x % a.ntx, ty = blockIdx.x / a.ntx;
     const int x0 = tx * ACX - ATA, y0 = ty * ACY - ATA;
+    const bool tma = a.use_tma != 0;
+    const uint32_t b0 = sm32(&bars[0]);
 
+    if (tma) {
+        if (tid == 0) {
+            for (int b = 0; b < 4; b++) bar_init(b0 + 8u * b);
+            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            bar_expect(b0, TILE_B);
+            tile_copy(sm32(buf0), &tl, x0, y0, 0, b0);
+            bar_expect(b0 + 8u, TILE_B);
+            tile_copy(sm32(ubuf), &tu, x0, y0, a.k_hi, b0 + 8u);
+            if (KIND == ST_THERMAL) {
+                bar_expect(b0 + 24u, TILE_B);
+                tile_copy(sm32(ptile), &tp, x0, y0, 0, b0 + 24u);
+            }
+        }
+        __syncthreads();   // barriers initialised before anyone polls them
+        bool ok = bar_wait(b0, 0);
+        if (KIND == ST_THERMAL) ok = bar_wait(b0 + 24u, 0) && ok;
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicExch(a.err, 1);
+                (void)bar_wait(b0 + 8u, 0);   // the first state tile may still be in flight
+            }
+            return;
+        }
+    } else {
 #pragma unroll
-    for (int q = 0; q < ACPT; q++) {
-        const int idx = tid + q * ANT, lx = idx % AX, ly = idx / AX;
-        const int gx = x0 + lx, gy = y0 + ly;
-        const bool in = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny;
-        buf0[idx] = in ? a.lam_in[(long long)gy * a.nx + gx] : 0.f;
+        for (int q = 0; q < ACPT; q++) {
+            const int idx = tid + q * ANT, lx = idx % AX, ly = idx / AX;
+            const int gx = x0 + lx, gy = y0 + ly;
+            const bool in = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny;
+            buf0[idx] = in ? a.lam_in[(long long)gy * a.nx + gx] : 0.f;
+        }
+        __syncthreads();
     }
-    __syncthreads();
 
     float hi[NG], lo[NG], ab[NG], pacc[ACPT];
 #pragma unroll
@@ -131,6 +203,23 @@ __global__ void __launch_bounds__(ANT) k_adj2d(const AdjPass a)
     float *cur = buf0, *nxt = buf1;
     for (int j = 0; j < a.nsteps; j++) {
         const float *u = a.states + (long long)(a.k_hi - j) * a.n;   // u_t, t = t_hi - 1 - j
+        const float *ut = ubuf + (j & 1) * AX * AY;                  // its tile (staged path)
+        if (tma) {
+            if (tid == 0 && j + 1 < a.nsteps) {
+                // the other state tile was last read in step j-1, before the barrier below it
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                const uint32_t bn = b0 + 8u * (1 + ((j + 1) & 1));
+                bar_expect(bn, TILE_B);
+                tile_copy(sm32(ubuf + ((j + 1) & 1) * AX * AY), &tu, x0, y0, a.k_hi - j - 1, bn);
+            }
+            const bool ok = bar_wait(b0 + 8u * (1 + (j & 1)), (j >> 1) & 1);
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) atomicExch(a.err, 1);
+                if (tid == 0 && j + 1 < a.nsteps)
+                    (void)bar_wait(b0 + 8u * (1 + ((j + 1) & 1)), ((j + 1) >> 1) & 1);
+                return;
+            }
+        }
 #pragma unroll
         for (int q = 0; q < ACPT; q++) {
             const int idx = tid + q * ANT, lx = idx % AX, ly = idx / AX;
@@ -154,18 +243,27 @@ __global__ void __launch_bounds__(ANT) k_adj2d(const AdjPass a)
             nxt[idx] = in ? r : 0.f;
             const bool own = in && lx >= ATA && lx < ATA + ACX && ly >= ATA && ly < ATA + ACY;
             if (own) {
-                const long long o = (long long)gy * a.nx;
-                const int xw = gx > 0 ? gx - 1 : 0, xe = gx < a.nx - 1 ? gx + 1 : a.nx - 1;
-                const long long on = (long long)(gy > 0 ? gy - 1 : 0) * a.nx;
-                const long long os = (long long)(gy < a.ny - 1 ? gy + 1 : a.ny - 1) * a.nx;
                 float g[NG];
-                const float p = KIND == ST_THERMAL ? __ldg(a.pw + o + gx) : 0.f;
-                dfdtheta<KIND>(a, __ldg(u + o + gx), __ldg(u + o + xw), __ldg(u + o + xe),
-                               __ldg(u + os + gx), __ldg(u + on + gx), p, g);
+                if (tma) {
+                    // own cells are ATA >= 1 cells inside the tile; clamp at the domain edges
+                    const int dw = gx > 0 ? 1 : 0, de = gx < a.nx - 1 ? 1 : 0;
+                    const int dn = gy > 0 ? AX : 0, dsn = gy < a.ny - 1 ? AX : 0;
+                    const float p = KIND == ST_THERMAL ? ptile[idx] : 0.f;
+                    dfdtheta<KIND>(a, ut[idx], ut[idx - dw], ut[idx + de], ut[idx + dsn],
+                                   ut[idx - dn], p, g);
+                } else {
+                    const long long o = (long long)gy * a.nx;
+                    const int xw = gx > 0 ? gx - 1 : 0, xe = gx < a.nx - 1 ? gx + 1 : a.nx - 1;
+                    const long long on = (long long)(gy > 0 ? gy - 1 : 0) * a.nx;
+                    const long long os = (long long)(gy < a.ny - 1 ? gy + 1 : a.ny - 1) * a.nx;
+                    const float p = KIND == ST_THERMAL ? __ldg(a.pw + o + gx) : 0.f;
+                    dfdtheta<KIND>(a, __ldg(u + o + gx), __ldg(u + o + xw), __ldg(u + o + xe),
+                                   __ldg(u + os + gx), __ldg(u + on + gx), p, g);
+                }
 #pragma unroll
                 for (int m = 0; m < NG; m++) {
-                    acc_prod(hi[m], lo[m], l, g[m]);
-                    ab[m] = __fadd_rn(ab[m], fabsf(__fmul_rn(l, g[m])));
+                    hi[m] = __fmaf_rn(l, g[m], hi[m]);
+                    ab[m] = __fmaf_rn(fabsf(l), fabsf(g[m]), ab[m]);
                 }
                 if (KIND == ST_THERMAL) pacc[q] = __fadd_rn(pacc[q], l);
             }
@@ -304,6 +402,7 @@ struct stencil_adjoint_s {
     long long blocks = 0, passes = 0;
     float coef[5] = {0, 0, 0, 0, 0};
     bool have_forward = false;
+    int *err = nullptr;       // device flag set by a kernel whose bounded wait gave up
 };
 
 extern "C" {
@@ -355,8 +454,10 @@ int stencil_adjoint_create(stencil_adjoint *out, int kind, int nx, int ny, int s
         if (e == cudaSuccess) e = cudaMalloc(&a->lam[1], n);
         if (e == cudaSuccess)
             e = cudaMalloc(&a->partials, sizeof(float) * NPART * (size_t)(a->blocks * a->passes));
+        if (e == cudaSuccess) e = cudaMalloc(&a->err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(a->err, 0, sizeof(int));
         if (e == cudaSuccess) {
-            const int smem = 2 * AX * AY * (int)sizeof(float);
+            const int smem = 5 * AX * AY * (int)sizeof(float);
             e = cudaFuncSetAttribute(k_adj2d<ST_DIFFUSION>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (e == cudaSuccess)
@@ -446,7 +547,19 @@ int stencil_adjoint_backward(stencil_adjoint a, const float *grad_out, const flo
         p.ww = p.we = (float)(kdt * rx);
         p.ws = p.wn = (float)(kdt * ry);
     }
-    const int smem = 2 * AX * AY * (int)sizeof(float);
+    // tensor maps of the adjoint grids, the state buffer and the power map (rows on 16-byte
+    // boundaries only; otherwise the kernel reads with plain loads)
+    stn::Tma3D mo, m0, m1, ms, mp;
+    std::memset(&mo, 0, sizeof(mo));
+    m0 = m1 = ms = mp = mo;
+    bool tma = stn::tma3d_encode(&mo.in, grad_out, a->nx, a->ny, 1, AX, AY) &&
+               stn::tma3d_encode(&m0.in, a->lam[0], a->nx, a->ny, 1, AX, AY) &&
+               stn::tma3d_encode(&m1.in, a->lam[1], a->nx, a->ny, 1, AX, AY) &&
+               stn::tma3d_encode(&ms.in, a->seg, a->nx, a->ny, a->ckpt, AX, AY);
+    if (tma && power) tma = stn::tma3d_encode(&mp.in, power, a->nx, a->ny, 1, AX, AY);
+    p.use_tma = tma ? 1 : 0;
+    p.err = a->err;
+    const int smem = (a->kind == ST_THERMAL ? 5 : 4) * AX * AY * (int)sizeof(float);
     const float *lin = grad_out;
     int which = 0;
     long long pass = 0;
@@ -468,10 +581,13 @@ int stencil_adjoint_backward(stencil_adjoint a, const float *grad_out, const flo
             p.k_hi = t_hi - 1 - t0;
             p.nsteps = ns;
             p.partials = a->partials + (size_t)pass * a->blocks * NPART;
+            const CUtensorMap &tl = lin == grad_out ? mo.in : (lin == a->lam[0] ? m0.in : m1.in);
             if (a->kind == ST_DIFFUSION)
-                k_adj2d<ST_DIFFUSION><<<(unsigned)a->blocks, ANT, smem, a->stream>>>(p);
+                k_adj2d<ST_DIFFUSION><<<(unsigned)a->blocks, ANT, smem, a->stream>>>(p, tl, ms.in,
+                                                                                    mp.in);
             else
-                k_adj2d<ST_THERMAL><<<(unsigned)a->blocks, ANT, smem, a->stream>>>(p);
+                k_adj2d<ST_THERMAL><<<(unsigned)a->blocks, ANT, smem, a->stream>>>(p, tl, ms.in,
+                                                                                  mp.in);
             e = cudaGetLastError();
             lin = a->lam[which];
             which ^= 1;
@@ -488,6 +604,21 @@ int stencil_adjoint_backward(stencil_adjoint a, const float *grad_out, const flo
     return status(e);
 }
 
+int stencil_adjoint_sync(stencil_adjoint a)
+{
+    if (!a) return ST_ERR_INVALID_ARG;
+    cudaError_t e = a->stream ? cudaStreamSynchronize(a->stream) : cudaDeviceSynchronize();
+    if (e != cudaSuccess) return status(e);
+    int flag = 0;
+    e = cudaMemcpy(&flag, a->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return status(e);
+    if (flag) {
+        (void)cudaMemset(a->err, 0, sizeof(int));
+        return ST_ERR_TIMEOUT;
+    }
+    return ST_OK;
+}
+
 int stencil_adjoint_destroy(stencil_adjoint a)
 {
     if (!a) return ST_OK;
@@ -500,6 +631,7 @@ int stencil_adjoint_destroy(stencil_adjoint a)
     for (float *l : a->lam)
         if (l) cudaFree(l);
     if (a->partials) cudaFree(a->partials);
+    if (a->err) cudaFree(a->err);
     delete a;
     return ST_OK;
 }

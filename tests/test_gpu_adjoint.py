@@ -8,8 +8,10 @@ errors stay below the adjoint of |w| entrywise: with lambda' the float64 adjoint
     |d dL/dp|    <= (N R + N + 2) eps dL/dp(|w|)      (float32 sum over steps, Hotspot).
 The forward states satisfy |d u_t| <= N R eps U, U = 2 max|u0| (rows of A sum to at most 1; the
 Hotspot source terms are far below the field).  A coefficient gradient
-g_m = sum_{t,i} lambda_{t+1}[i] g_m(u_t)_i is summed by error-free transformations, so
-    |d g_m| <= N R eps Lam (G_m + D_m U) + 4 eps (S_m + D_m U Lam),
+g_m = sum_{t,i} lambda_{t+1}[i] g_m(u_t)_i is summed in float32 by each thread over at most
+64 terms (its 16 cells x 4 fused steps), the partial sums then combined by error-free
+transformations, so
+    |d g_m| <= N R eps Lam (G_m + D_m U) + 4 eps D_m U Lam + 68 eps S_m,
 with Lam = sum_t ||lambda'_{t+1}||_1 (the oracle's cc gradient of |w| on a field of ones, or its
 amb gradient over k_dt Rz), G_m a bound of |g_m| and D_m the sum of |d g_m / d u| over a cell's
 neighbourhood, S_m = sum |terms| as returned by the engine.
@@ -90,7 +92,7 @@ def _check(orc, w, wt, steps, res):
     G, D = _bounds(kind, w, U)
     for m in range(5):
         assert ga[m] >= abs(gk64[m]) * (1 - 1e-4), (m, ga[m], gk64[m])
-        tol = N * R * EPS * lam * (G[m] + D[m] * U) + 4 * EPS * (ga[m] + D[m] * U * lam)
+        tol = N * R * EPS * lam * (G[m] + D[m] * U) + 4 * EPS * D[m] * U * lam + 68 * EPS * ga[m]
         assert abs(gk[m] - gk64[m]) <= tol, (m, gk[m], gk64[m], tol)
     if kind == 1:
         assert np.all(np.abs(gp - gp64) <= (N * R + N + 2) * EPS * gpa + 1e-30)
@@ -118,7 +120,7 @@ def test_adjoint_no_cancellation_is_tight(eng, orc, kind):
     gk = res[2]
     idx = range(5) if kind == 0 else (3, 4)   # Hotspot: (amb - c) < 0 and the constant term
     for m in idx:
-        assert abs(gk[m] - gk64[m]) <= 2 * (30 * R + 4) * EPS * abs(gk64[m]), m
+        assert abs(gk[m] - gk64[m]) <= 2 * (30 * R + 72) * EPS * abs(gk64[m]), m
 
 
 @pytest.mark.parametrize("kind", [0, 1])
