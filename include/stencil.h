@@ -151,10 +151,12 @@ typedef struct {
 
 /* Prepare `count` grids for repeated batched runs: each grid gets (T, cells per thread) from
  * the GPU restatement of the paper's model (Eqs. 3-9) and its own ping-pong scratch (Sec. 2.1);
- * grids that share a kernel form a group, and pass p of a group is one launch over a work
- * queue spanning all its grids that still have a pass p (Eq. 8: ceil(steps/T) passes per grid,
- * the last fusing the remainder, Sec. 3.2).  All launches are captured into one CUDA graph on
- * `stream` (NULL: an owned stream that synchronises with the legacy default stream).  Buffers
+ * grids that share a kernel form a group, and each launch slot of a group is one persistent
+ * launch over a work queue spanning all its grids that run a pass in that slot (Eq. 8:
+ * ceil(steps/T) passes per grid, the last fusing the remainder, Sec. 3.2; each grid's chain of
+ * passes starts at the slot that levels the group's work).  All launches are captured into one
+ * CUDA graph, one branch per group, on `stream` (NULL: an owned stream that synchronises with
+ * the legacy default stream).  Buffers
  * and coefficients are fixed at creation.  Errors: ST_ERR_INVALID_ARG, ST_ERR_UNSUPPORTED,
  * ST_ERR_OOM, ST_ERR_CUDA. */
 int stencil_batch_create(stencil_batch *out, const stencil_batch_grid *grids, int count,
