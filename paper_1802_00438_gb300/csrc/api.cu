@@ -186,7 +186,7 @@ int prepare2(stencil_plan_s *p, int Tk, PassCfg2D **out)
         c.ntx = (p->d.nx + cx - 1) / cx;
         c.total = (long long)c.ntx * p->d.ny;
         // each block streams at least ~8T rows so the y-halo (2T rows per segment) stays small
-        const long long min_rows = std::max(16, 8 * Tk);
+        const long long min_rows = 4;   // short segments keep small grids parallel
         long long ctas = std::min<long long>((long long)p->sms * bps,
                                              std::max<long long>(1, c.total / min_rows));
         c.rows_per_cta = (c.total + ctas - 1) / ctas;

@@ -239,7 +239,7 @@ int stencil_batch_create(stencil_batch *out, const stencil_batch_grid *grids, in
             }
             r.bp.ngrids = (int)r.desc.size();
             r.bp.total_units = r.prefix.back();
-            const long long min_rows = std::max(16, 8 * T);
+            const long long min_rows = 4;   // short segments keep small grids parallel
             const long long ctas = std::min<long long>((long long)B->sms * bps,
                                                        std::max<long long>(1, r.bp.total_units / min_rows));
             r.bp.units_per_cta = (r.bp.total_units + ctas - 1) / ctas;

@@ -105,7 +105,7 @@ int pass2(const DeviceSlot &dv, int kind, int exact, int V, int W, int T, const 
     a.tsteps = tsteps;
     a.ntx = (nx + cx - 1) / cx;
     a.total_rows = (long long)a.ntx * ny;
-    const long long min_rows = std::max(16, 8 * Tk);
+    const long long min_rows = 4;   // short segments keep small grids parallel
     const long long ctas = std::min<long long>((long long)dv.sms * bps,
                                                std::max<long long>(1, a.total_rows / min_rows));
     a.rows_per_cta = (a.total_rows + ctas - 1) / ctas;
