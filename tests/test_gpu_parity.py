@@ -229,6 +229,10 @@ def test_c2_full_steps_closed_form(eng):
     rows = np.r_[0:4, 8000:8004, ny - 4:ny]
     expect = tstar + eps * lam ** 1000 * np.outer(phy[rows], phx)
     got = g[rows].astype(np.float64)
-    # float32 storage of ~330 K: ulp 3e-5; 1000 steps of rounding stay well under 2e-3 K
-    assert np.max(np.abs(got - expect)) < 2e-3
+    # Rounding bound: each step rounds at most 6 times per cell on terms below 340 K, and the
+    # update is non-expansive, so 1000 float32 steps stay within 1000 * 6 * 2^-24 * 340 = 0.12 K
+    # (worst case, all errors aligned) and near sqrt(1000) times one step's 1.2e-4 K = 4e-3 K
+    # when they are not.  1e-2 K is 0.2 % of the mode's remaining amplitude (~5.5 K): a wrong
+    # eigenvalue, boundary or pass would miss it by far more.
+    assert np.max(np.abs(got - expect)) < 1e-2
     assert np.all(np.isfinite(g))
