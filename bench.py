@@ -585,7 +585,10 @@ def main():
     if dist:
         dist.barrier()
     ms = e0.elapsed_time(e1)
-    kern_ms, launches = st.stencil_plan_kernel_time(plan.h, reset=True)
+    kern_ms, timed_launches = st.stencil_plan_kernel_time(plan.h, reset=True)
+    launches = timed_launches
+    if w.kind == 1 and w.ndim == 2 and not args.storage:
+        launches += args.steps   # the source-map kernel (p + amb*Rz) before each run's passes
     st.stencil_plan_set_timing(plan.h, False)
     if dist:
         t = torch.tensor([ms], device=dev)
@@ -641,10 +644,10 @@ def main():
     by = BYTES[w.kind]
     alu_peak = fp32_peak_tflops(sms, mhz)
     hbm_peak = float(peaks["hbm_gbs"])
-    avg_launch_ms = kern_ms / max(launches, 1)
+    avg_launch_ms = kern_ms / max(timed_launches, 1)
     # algorithmic work of one launch, averaged over the timed launches (the last pass of a
     # run fuses the remainder of the steps)
-    flops_per_launch = w.cells * w.steps * args.steps * fl / max(launches, 1)
+    flops_per_launch = w.cells * w.steps * args.steps * fl / max(timed_launches, 1)
     bytes_per_launch = w.cells * by
     tflops = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12
     gbs = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
@@ -705,6 +708,11 @@ def main():
                            "time_steps": w.steps, "T": T, "tile": [info["bx"], info["by"]],
                            "vec": info["vec"], "warps": info["warps"], "ctas": info["ctas"],
                            "passes_per_step": passes,
+                           # the library's calibrated restatement of Eqs. 3-9 for this plan,
+                           # and measured / predicted (the paper's model-accuracy figure)
+                           "model_gcells": info["model_gcells"] or None,
+                           "model_accuracy": (value / world / info["model_gcells"]
+                                              if info["model_gcells"] else None),
                            "l2": "inputs larger than L2 (%.0f MiB per grid)" % (w.u0.nbytes / 2**20),
                            "parallelism": f"replicas{world}" if world > 1 else "single"},
                 "roofline": roof, "e2e": e2e, "lowp": lowp,

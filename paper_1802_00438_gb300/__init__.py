@@ -49,7 +49,7 @@ class stencil_plan_info(ctypes.Structure):
                 ("halo", ctypes.c_int), ("vec", ctypes.c_int), ("warps", ctypes.c_int),
                 ("ctas", ctypes.c_int), ("sms", ctypes.c_int),
                 ("scratch_bytes", ctypes.c_longlong), ("exact", ctypes.c_int),
-                ("kernel_id", ctypes.c_int)]
+                ("kernel_id", ctypes.c_int), ("model_gcells", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

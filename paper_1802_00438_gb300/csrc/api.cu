@@ -53,6 +53,8 @@ struct stencil_plan_s {
     // 3D
     int VY = 8, NW = 8, alg3 = 0, VX3 = 2;
     int *err = nullptr;   // device flag set by a kernel whose bounded wait gave up
+    double model = 0.0;   // calibrated model's prediction for this plan (1000 steps), GCell/s
+    float *src = nullptr;   // contracted float32 Hotspot 2D: the source map p + amb*Rz
     std::vector<PassCfg3D> cfg3;
     // timing
     bool timing = false;
@@ -90,10 +92,17 @@ int ncoef(const stencil_desc &d)
     return d.kind == ST_DIFFUSION ? 7 : 9;
 }
 
+// storage bits of a plan's 2D kernel shape: the format, plus STOR_SRC for contracted Hotspot
+// kernels (they stage p + amb*Rz instead of the power map)
+int shape_stor(const stencil_plan_s *p)
+{
+    return p->stor | ((p->d.kind == ST_THERMAL && !p->d.exact) ? STOR_SRC : 0);
+}
+
 bool available(const stencil_plan_s *p, int T)
 {
     if (p->d.ndim == 2)
-        return tb2d_available(Shape2D{p->d.kind, p->d.exact ? 1 : 0, T, p->V, p->W, p->stor});
+        return tb2d_available(Shape2D{p->d.kind, p->d.exact ? 1 : 0, T, p->V, p->W, shape_stor(p)});
     return tb3d_available(Shape3D{p->d.kind, p->d.exact ? 1 : 0, T, p->VY, p->NW, p->alg3, p->VX3});
 }
 
@@ -104,7 +113,8 @@ bool available(const stencil_plan_s *p, int T)
 // addressing), each row ~100 more per thread (waits, copies, ring and pointer updates); issue
 // efficiency grows with resident warps (0.69 at 8, 0.77 at 12 per SM); a hot loop beyond ~12 KB
 // of code loses issue rate in proportion (instruction-cache misses); these kernels reach ~62 %
-// of the measured copy bandwidth when they are memory-bound.  With these factors the model
+// of the measured copy bandwidth when they are memory-bound; every row segment streams 2T rows
+// more than it stores, which dominates on small grids cut into many short segments.  With these factors the model
 // ranks the compiled variants as measured on 16384^2 grids at T in {4, 6, 8, 12}.
 struct Cand2D { int T, V, W; };
 
@@ -114,7 +124,15 @@ double model_gcells_2d(const stencil_desc &d, int sms, const Cand2D &k, int bps,
     const double fp = d.kind == ST_DIFFUSION ? 5.0 : 9.0;
     const double ops = fp + 4.0 / k.V + 100.0 / (k.T * k.V);
     const double code_kb = (swap ? 2.0 : 1.0) * k.T * (k.V * fp + 6.0) * 16.0 / 1024.0;
-    const int warps = std::min(bps, 16);
+    // the launch geometry of prepare2: one-warp blocks over (tile column, row) units in
+    // segments of at least 4 rows; each segment streams 2T extra rows (Sec. 3.2's pipeline
+    // fill and drain), and a small grid leaves SMs with fewer resident warps
+    const int halo = (k.T + 3) / 4 * 4;
+    const long long cx = 32LL * k.V - 2 * halo;
+    const long long units = (d.nx + cx - 1) / cx * (long long)d.ny;
+    const long long ctas = std::min<long long>((long long)sms * bps, std::max<long long>(1, units / 4));
+    const double rows_per_cta = (double)units / ctas;
+    const int warps = (int)std::min<long long>(std::min(bps, 16), (ctas + sms - 1) / sms);
     double eff = std::min(0.85, 0.45 + 0.027 * warps);
     if (code_kb > 12.0) eff *= 12.0 / code_kb;
     stencil_gpu_model_in m = {};
@@ -133,7 +151,39 @@ double model_gcells_2d(const stencil_desc &d, int sms, const Cand2D &k, int bps,
     m.ops_per_cell = ops;
     m.issue_eff = eff;
     m.hbm_eff = 0.62;
-    m.stream_overhead = 0.05;
+    m.stream_overhead = 2.0 * k.T / rows_per_cta;
+    m.launch_s = 4e-6;
+    stencil_gpu_model_out r;
+    if (stencil_model_gpu(&m, &r) != ST_OK) return 0.0;
+    return r.gcells;
+}
+
+// 3D partial-sum kernel: the same restatement, calibrated from ncu counts of the 512^3 and
+// 512^2 x 256 runs at T = 3 (2 x 4 cells per thread, 16 warps): 17.3 (Diffusion) and 19.7
+// (Hotspot) issued thread instructions per computed cell update including halos, 61 % issue
+// efficiency with one 16-warp block per SM, DRAM traffic 1.9x the algorithmic bytes (halo
+// re-reads by blocks at other z positions, so hbm_eff = 0.9 / 1.9).
+double model_gcells_3d(const stencil_desc &d, int sms, int T, int VX, int VY, int NW)
+{
+    stencil_gpu_model_in m = {};
+    m.ndim = 3;
+    m.nx = d.nx;
+    m.ny = d.ny;
+    m.nz = d.nz;
+    m.steps = 1000;
+    m.T = T;
+    m.bx = 32 * VX;
+    m.by = VY * NW;
+    m.halo_x = (T + 3) / 4 * 4;
+    m.halo_y = T;
+    m.sms = sms;
+    m.sm_hz = 2.07e9;
+    m.hbm_gbs = 6800.0;
+    m.bytes_per_cell = d.kind == ST_DIFFUSION ? 8.0 : 12.0;
+    m.ops_per_cell = d.kind == ST_DIFFUSION ? 17.3 : 19.7;
+    m.issue_eff = 0.61;
+    m.hbm_eff = 0.9 / 1.9;
+    m.stream_overhead = 0.04;
     m.launch_s = 4e-6;
     stencil_gpu_model_out r;
     if (stencil_model_gpu(&m, &r) != ST_OK) return 0.0;
@@ -175,7 +225,7 @@ int prepare2(stencil_plan_s *p, int Tk, PassCfg2D **out)
     if ((int)p->cfg2.size() <= Tk) p->cfg2.resize(Tk + 1);
     PassCfg2D &c = p->cfg2[Tk];
     if (!c.ready) {
-        c.shape = Shape2D{p->d.kind, p->d.exact ? 1 : 0, Tk, p->V, p->W, p->stor};
+        c.shape = Shape2D{p->d.kind, p->d.exact ? 1 : 0, Tk, p->V, p->W, shape_stor(p)};
         if (!tb2d_available(c.shape)) return ST_ERR_UNSUPPORTED;
         int bps = 0;
         cudaError_t e = tb2d_prepare(c.shape, &bps);
@@ -472,7 +522,7 @@ int stencil_plan_create(stencil_plan *out, const stencil_desc *desc)
                                     {8, 8, 1}, {8, 8, 0}, {12, 4, 0}};
             double best = -1.0;
             for (const Cand2D &k : cands) {
-                const Shape2D sh{d.kind, 0, k.T, k.V, k.W};
+                const Shape2D sh{d.kind, 0, k.T, k.V, k.W, d.kind == ST_THERMAL ? STOR_SRC : 0};
                 if (!tb2d_available(sh)) continue;
                 int bps = 0;
                 if (tb2d_prepare(sh, &bps) != cudaSuccess || bps < 1) continue;
@@ -491,7 +541,7 @@ int stencil_plan_create(stencil_plan *out, const stencil_desc *desc)
             // and the T the model rates best within that family
             double best = -1.0;
             for (int t : kTcand) {
-                const Shape2D sh{d.kind, 0, t, p->V, p->W};
+                const Shape2D sh{d.kind, 0, t, p->V, p->W, d.kind == ST_THERMAL ? STOR_SRC : 0};
                 if (!tb2d_available(sh)) continue;
                 int bps = 0;
                 if (tb2d_prepare(sh, &bps) != cudaSuccess || bps < 1) continue;
@@ -557,6 +607,21 @@ int stencil_plan_create(stencil_plan *out, const stencil_desc *desc)
         e = cudaMalloc(&p->scratch, p->scratch_bytes);
         if (e != cudaSuccess) rc = map_cuda(e);
     }
+    if (rc == ST_OK && d.ndim == 2 && d.kind == ST_THERMAL && !d.exact && !p->stor) {
+        e = cudaMalloc(&p->src, (size_t)d.nx * d.ny * sizeof(float));
+        if (e != cudaSuccess) rc = map_cuda(e);
+    }
+    if (rc == ST_OK && !d.exact && !p->stor) {
+        if (d.ndim == 2) {
+            int bps = 0;
+            const Shape2D sh{d.kind, 0, p->T, p->V, p->W, d.kind == ST_THERMAL ? STOR_SRC : 0};
+            if (tb2d_prepare(sh, &bps) == cudaSuccess && bps > 0)
+                p->model = model_gcells_2d(d, p->sms, Cand2D{p->T, p->V, p->W}, bps, 1000);
+            (void)cudaGetLastError();
+        } else if (p->alg3) {
+            p->model = model_gcells_3d(d, p->sms, p->T, p->VX3, p->VY, p->NW);
+        }
+    }
     if (rc == ST_OK) {
         e = cudaMalloc(&p->err, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(p->err, 0, sizeof(int));
@@ -621,6 +686,12 @@ int stencil_run(stencil_plan p, const void *grid_in, void *grid_out, const void 
     // shifts by one and a final copy brings the scratch result to the output.
     const bool shift = (in == out) && (passes % 2 == 1);
     const long long ldo = d.nx, ldsc = d.ndim == 2 ? p->ld_scratch : d.nx;
+    if (p->src) {
+        // contracted Hotspot 2D kernels stage p + amb*Rz (Table 2's ambient term folded in)
+        e = hot_source(pw, d.nx, p->src, d.nx, d.ny, coeffs[4], coeffs[3], p->stream);
+        if (e != cudaSuccess) return map_cuda(e);
+        pw = p->src;
+    }
     const float *src = in;
     long long lds = d.nx;
     for (int i = 0; i < passes; i++) {
@@ -671,6 +742,7 @@ int stencil_plan_get_info(stencil_plan p, stencil_plan_info *info)
     if (!p || !info) return ST_ERR_INVALID_ARG;
     std::memset(info, 0, sizeof(*info));
     info->T = p->T;
+    info->model_gcells = p->model;
     info->sms = p->sms;
     info->scratch_bytes = (long long)p->scratch_bytes;
     info->exact = p->d.exact;
@@ -734,6 +806,7 @@ int stencil_plan_destroy(stencil_plan p)
     if (p->qp) cudaFree(p->qp);
     if (p->qpm) cudaFree(p->qpm);
     if (p->err) cudaFree(p->err);
+    if (p->src) cudaFree(p->src);
     delete p;
     return ST_OK;
 }

@@ -38,6 +38,7 @@ struct stencil_batch_s {
     std::vector<stencil_batch_grid> grid;
     std::vector<int> T, V, passes;
     std::vector<float *> scratch;
+    std::vector<float *> src;         // Hotspot grids: the source map p + amb*Rz
     std::vector<long long> ld_scratch;
     void *dev = nullptr;              // descriptors and prefix arrays of every (group, pass)
     cudaGraph_t graph = nullptr;
@@ -114,6 +115,7 @@ int stencil_batch_create(stencil_batch *out, const stencil_batch_grid *grids, in
     B->V.resize(count);
     B->passes.resize(count);
     B->scratch.assign(count, nullptr);
+    B->src.assign(count, nullptr);
     B->ld_scratch.resize(count);
     for (int g = 0; g < count && rc == ST_OK; g++) {
         const stencil_batch_grid &q = B->grid[g];
@@ -135,6 +137,8 @@ int stencil_batch_create(stencil_batch *out, const stencil_batch_grid *grids, in
         B->ld_scratch[g] = ((long long)q.nx + 31) / 32 * 32;
         if (rc == ST_OK && B->passes[g] > 0) {
             e = cudaMalloc(&B->scratch[g], (size_t)B->ld_scratch[g] * q.ny * sizeof(float));
+            if (e == cudaSuccess && q.kind == ST_THERMAL)
+                e = cudaMalloc(&B->src[g], (size_t)q.nx * q.ny * sizeof(float));
             if (e != cudaSuccess) rc = status(e);
         }
     }
@@ -214,7 +218,7 @@ int stencil_batch_create(stencil_batch *out, const stencil_batch_grid *grids, in
                 a.ld_in = (src_in || src_out) ? q.nx : B->ld_scratch[g];
                 a.out = to_out(p) ? static_cast<float *>(q.grid_out) : B->scratch[g];
                 a.ld_out = to_out(p) ? q.nx : B->ld_scratch[g];
-                a.pw = static_cast<const float *>(q.power);
+                a.pw = B->src[g];   // Hotspot: p + amb*Rz, rebuilt at every replay
                 a.ld_pw = q.nx;
                 a.nx = q.nx;
                 a.ny = q.ny;
@@ -282,7 +286,16 @@ int stencil_batch_create(stencil_batch *out, const stencil_batch_grid *grids, in
         }
         if (e == cudaSuccess) e = cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t le = cudaEventRecord(fork, B->stream);
+            // Hotspot source maps from the power maps' current contents, before any pass
+            cudaError_t le = cudaSuccess;
+            for (int g = 0; g < count && le == cudaSuccess; g++)
+                if (B->src[g]) {
+                    const stencil_batch_grid &q = B->grid[g];
+                    le = hot_source(static_cast<const float *>(q.power), q.nx, B->src[g], q.nx,
+                                    q.ny, q.coeffs[4], q.coeffs[3], B->stream);
+                    B->launches++;
+                }
+            if (le == cudaSuccess) le = cudaEventRecord(fork, B->stream);
             for (int i = 0; i < ng && le == cudaSuccess; i++) le = cudaStreamWaitEvent(gs[i], fork, 0);
             for (const LaunchRec &r : recs) {
                 if (le == cudaSuccess) le = tb2d_batch_launch(r.shape, r.bp, gs[r.group]);
@@ -354,6 +367,8 @@ int stencil_batch_destroy(stencil_batch b)
     }
     if (b->graph) cudaGraphDestroy(b->graph);
     for (float *s : b->scratch)
+        if (s) cudaFree(s);
+    for (float *s : b->src)
         if (s) cudaFree(s);
     if (b->dev) cudaFree(b->dev);
     if (b->own_stream) cudaStreamDestroy(b->stream);

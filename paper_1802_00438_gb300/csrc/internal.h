@@ -33,7 +33,10 @@ struct Pass2D {
     long long ld_q;                // row pitch of the 16-bit grids, cells (multiple of 8)
 };
 
+// stor: storage format (0 float32, 1 bf16, 2 fp16) plus 4 when the kernel stages the Hotspot
+// source map p + amb*Rz instead of the power map (every contracted Hotspot plan and batch)
 struct Shape2D { int kind, exact, T, V, W; int stor = 0; };
+enum { STOR_SRC = 4 };
 
 // One pass over many 2D grids (contracted kernels): grids[g] describes grid g's pass (its
 // tile columns ntx, sizes, buffers, coefficients, tsteps); prefix[g] = sum of ntx*ny of the
@@ -57,6 +60,10 @@ cudaError_t lp_encode(int stor, const float *src, long long ld_src, void *dst, l
                       float2 *meta, int nx, int ny, int cx, cudaStream_t st);
 cudaError_t lp_decode(int stor, const void *src, long long ld_q, const float2 *meta, float *dst,
                       long long ld_dst, int nx, int ny, int cx, cudaStream_t st);
+
+// Hotspot source map dst = p + amb*Rz (dense rows of nx), read by the contracted kernels
+cudaError_t hot_source(const float *p, long long ld_p, float *dst, int nx, int ny, float amb,
+                       float rz, cudaStream_t st);
 
 bool tb2d_available(const Shape2D &s);
 int tb2d_block_threads(const Shape2D &s);

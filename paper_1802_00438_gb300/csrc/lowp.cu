@@ -1,4 +1,5 @@
-// Block codec of the 16-bit grid storage (bf16 or fp16 with a float32 code per block).
+// Block codec of the 16-bit grid storage (bf16 or fp16 with a float32 code per block), and the
+// Hotspot source map p + amb*Rz that the contracted kernels stage instead of the power map.
 //
 // A block is the segment of one row that one tile column computes: cells
 // [b*cx, min((b+1)*cx, nx)) of row y, with cx the compute width of the plan's tiling, so the
@@ -76,7 +77,26 @@ __global__ void __launch_bounds__(256) k_lp_decode(const uint16_t *__restrict__ 
     dst[(long long)y * ld_dst + x] = __fmaf_rn(m.y, dec<STOR>(src[(long long)y * ld_q + x]), m.x);
 }
 
+// Hotspot source row: p + amb*Rz (the product rounded once, as the kernels round it)
+__global__ void __launch_bounds__(256) k_hot_source(const float *__restrict__ p, long long ld_p,
+                                                    float *__restrict__ dst, int nx, int ny,
+                                                    float amb, float rz)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)nx * ny) return;
+    const int y = (int)(i / nx), x = (int)(i % nx);
+    dst[i] = __fadd_rn(p[(long long)y * ld_p + x], __fmul_rn(amb, rz));
+}
+
 }  // namespace
+
+cudaError_t hot_source(const float *p, long long ld_p, float *dst, int nx, int ny, float amb,
+                       float rz, cudaStream_t st)
+{
+    const long long n = (long long)nx * ny;
+    k_hot_source<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, ld_p, dst, nx, ny, amb, rz);
+    return cudaGetLastError();
+}
 
 cudaError_t lp_encode(int stor, const float *src, long long ld_src, void *dst, long long ld_q,
                       float2 *meta, int nx, int ny, int cx, cudaStream_t st)

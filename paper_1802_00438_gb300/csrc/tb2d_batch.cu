@@ -13,7 +13,7 @@ struct BatchEntry {
 
 #define STN_TB2FB_ENTRY(K, T_, V_)                                                           \
     { K, T_, V_, reinterpret_cast<const void *>(&k_tb2f_batch<K, T_, V_, true>),           \
-      TB2F<K, T_, V_>::SMEM }
+      TB2F<K, T_, V_, ((K) == 1 ? STOR_SRC : 0)>::SMEM }
 
 const BatchEntry kBatch[] = {
     STN_TB2FB_ENTRY(0, 4, 4), STN_TB2FB_ENTRY(0, 8, 4), STN_TB2FB_ENTRY(0, 4, 8), STN_TB2FB_ENTRY(0, 8, 8),

@@ -9,7 +9,8 @@ struct Tb2dEntry {
     int kind, exact, T, V, W;
     const void *fn;
     size_t smem;
-    int stor;   // 0 float32 grids; 1 bf16, 2 fp16 block-coded grids
+    int stor;   // 0 float32 grids; 1 bf16, 2 fp16 block-coded grids; + STOR_SRC (Hotspot:
+                // the power map arrives with amb*Rz folded in)
 };
 
 #define STN_TB2_ENTRY(K, E, T_, V_, W_)                                                      \
@@ -19,16 +20,25 @@ struct Tb2dEntry {
 // contracted path: one-warp blocks (W = 1), partial-sum stages
 // W = 1: partial rows alternate between two register arrays (two-row unroll);
 // W = 0 (a marker, still one warp): partial rows updated in place, no unroll
+// Hotspot contracted kernels read the power map with amb*Rz folded in (STOR_SRC), except the
+// plain-power instances (STN_TB2F0_ENTRY) that the allocation-free entry point uses
+#define STN_TB2F_SRC(K) ((K) == 1 ? STOR_SRC : 0)
 #define STN_TB2F_ENTRY(K, T_, V_)                                                            \
-    { K, 0, T_, V_, 1, reinterpret_cast<const void *>(&k_tb2f<K, T_, V_, true, 0>),        \
-      TB2F<K, T_, V_>::SMEM, 0 }
+    { K, 0, T_, V_, 1,                                                                       \
+      reinterpret_cast<const void *>(&k_tb2f<K, T_, V_, true, STN_TB2F_SRC(K)>),           \
+      TB2F<K, T_, V_, STN_TB2F_SRC(K)>::SMEM, STN_TB2F_SRC(K) }
 #define STN_TB2F1_ENTRY(K, T_, V_)                                                           \
-    { K, 0, T_, V_, 0, reinterpret_cast<const void *>(&k_tb2f<K, T_, V_, false, 0>),       \
+    { K, 0, T_, V_, 0,                                                                       \
+      reinterpret_cast<const void *>(&k_tb2f<K, T_, V_, false, STN_TB2F_SRC(K)>),          \
+      TB2F<K, T_, V_, STN_TB2F_SRC(K)>::SMEM, STN_TB2F_SRC(K) }
+#define STN_TB2F0_ENTRY(K, T_, V_)                                                           \
+    { K, 0, T_, V_, 1, reinterpret_cast<const void *>(&k_tb2f<K, T_, V_, true, 0>),        \
       TB2F<K, T_, V_>::SMEM, 0 }
 // 16-bit block-coded storage (S = 1 bf16, 2 fp16), two-row unroll
 #define STN_TB2FQ_ENTRY(K, T_, V_, S)                                                        \
-    { K, 0, T_, V_, 1, reinterpret_cast<const void *>(&k_tb2f<K, T_, V_, true, S>),        \
-      TB2F<K, T_, V_, S>::SMEM, S }
+    { K, 0, T_, V_, 1,                                                                       \
+      reinterpret_cast<const void *>(&k_tb2f<K, T_, V_, true, (S) | STN_TB2F_SRC(K)>),     \
+      TB2F<K, T_, V_, (S) | STN_TB2F_SRC(K)>::SMEM, (S) | STN_TB2F_SRC(K) }
 
 extern const Tb2dEntry tb2d_table_diff[];
 extern const int tb2d_table_diff_n;

@@ -39,6 +39,12 @@
 namespace stn {
 
 enum { STOR_F32 = 0, STOR_BF16 = 1, STOR_F16 = 2 };
+// Flag added to STOR (Hotspot): the power ring holds p + amb*Rz instead of p, so each stage's
+// ambient term is one fused multiply-add (-Rz*c) instead of a subtraction and a multiply-add.
+// Float32 plans stage a precomputed copy of the power map; 16-bit plans add amb*Rz as they
+// decode a power row.
+__host__ __device__ constexpr int stor_fmt(int s) { return s & 3; }
+__host__ __device__ constexpr bool stor_src(int s) { return (s & STOR_SRC) != 0; }
 
 template <int KIND, int T, int V, int STOR = STOR_F32>
 struct TB2F {
@@ -55,7 +61,7 @@ struct TB2F {
     static constexpr int ROWB = BX * 4;                             // bytes per ring row
     // 16-bit storage: rows arrive raw (32-byte header of block codes + 2 bytes per cell) in a
     // staging ring of PF+1 rows per input and are decoded into the float rings once
-    static constexpr int NBR = (STOR != STOR_F32) ? PF + 1 : 0;
+    static constexpr int NBR = (stor_fmt(STOR) != STOR_F32) ? PF + 1 : 0;
     static constexpr int RAWB = 32 + 2 * BX;
     static constexpr size_t SMEM = (size_t)(NBF + NBPX) * ROWB +
                                    (size_t)NBR * RAWB * (KIND == KTHERM ? 2 : 1);
@@ -130,14 +136,14 @@ __device__ __forceinline__ void sts128(uint32_t a, float x, float y, float z, fl
 template <int STOR>
 __device__ __forceinline__ float q2f(unsigned q)
 {
-    if (STOR == STOR_BF16) return __uint_as_float(q << 16);
+    if (stor_fmt(STOR) == STOR_BF16) return __uint_as_float(q << 16);
     return __half2float(__ushort_as_half((unsigned short)q));
 }
 
 template <int STOR>
 __device__ __forceinline__ unsigned f2q(float x)
 {
-    if (STOR == STOR_BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    if (stor_fmt(STOR) == STOR_BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
     return __half_as_ushort(__float2half_rn(x));
 }
 
@@ -181,6 +187,7 @@ struct CtxF {
     long long ld_q;        // row pitch of 16-bit grids (cells)
     int ntx, tx;           // tile columns; my tile column
     int msel;              // which of the three blocks of a loaded row my cells belong to
+    float src_add;         // amb * Rz (STOR_SRC, rounded once)
 };
 
 template <int V, bool EDGE>
@@ -224,7 +231,7 @@ __device__ __forceinline__ void qf(const CoefF &k, const float (&d)[V], uint32_t
 // SWAP = true: P' is built on top of Q in Xq and Q' is written to Xp (the caller alternates the
 // arrays every row).  SWAP = false: P' goes back to Xp and Q' to Xq (no alternation; the
 // register allocator decides whether that needs copies).
-template <int KIND, int V, int MODE, bool SWAP>
+template <int KIND, int V, int MODE, bool SWAP, bool SRC = false>
 __device__ __forceinline__ void stf(const CtxF &c, const CoefF &k, int y, bool fwd, float (&Xp)[V],
                                     float (&Xq)[V], const float (&d)[V], float w_in, float e_in,
                                     uint32_t p_y, uint32_t p_next, float (&out)[V])
@@ -263,9 +270,14 @@ __device__ __forceinline__ void stf(const CtxF &c, const CoefF &k, int y, bool f
 #pragma unroll
         for (int j = 0; j < V; j++) {
             const float t2 = __fmaf_rn(-2.0f, d[j], __fadd_rn(de[j], dw[j]));
-            const float t3 = __fsub_rn(k.a4, d[j]);
             Pn[j] = __fmaf_rn(t2, k.a1, Xq[j]);
-            Pn[j] = __fmaf_rn(t3, k.a3, Pn[j]);
+            if (SRC) {
+                // the power row already carries amb*Rz: (amb - c)*Rz + p = (p + amb*Rz) - Rz*c
+                Pn[j] = __fmaf_rn(-k.a3, d[j], Pn[j]);
+            } else {
+                const float t3 = __fsub_rn(k.a4, d[j]);
+                Pn[j] = __fmaf_rn(t3, k.a3, Pn[j]);
+            }
             Pn[j] = __fmaf_rn(k.a6, d[j], Pn[j]);
             Pn[j] = __fmaf_rn(k.a0, Pn[j], d[j]);
         }
@@ -323,10 +335,24 @@ __device__ __forceinline__ void tbf_iter(const CtxF &c, const CoefF &k,
         } else {
             float pv[V];
             lds_row<V>(pbase - C::ROWB + c.o4, pv);   // power of row R0-1
+            if (stor_src(STOR)) {
+                // hot2's contracted order with the ambient term folded into the power row
 #pragma unroll
-            for (int j = 0; j < V; j++)
-                out[j] = hot2<false>(m[j], w[j], e[j], dd[j], u[j], pv[j], k.a0, k.a1, k.a2, k.a3,
-                                     k.a4);
+                for (int j = 0; j < V; j++) {
+                    const float t2 = __fmaf_rn(-2.0f, m[j], __fadd_rn(e[j], w[j]));
+                    const float n2 = __fmaf_rn(-2.0f, m[j], u[j]);
+                    float q = __fmaf_rn(t2, k.a1, pv[j]);
+                    q = __fmaf_rn(-k.a3, m[j], q);
+                    q = __fmaf_rn(n2, k.a2, q);
+                    q = __fmaf_rn(dd[j], k.a2, q);
+                    out[j] = __fmaf_rn(k.a0, q, m[j]);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < V; j++)
+                    out[j] = hot2<false>(m[j], w[j], e[j], dd[j], u[j], pv[j], k.a0, k.a1, k.a2,
+                                         k.a3, k.a4);
+            }
         }
     }
     // stages 1 .. T-1: stage s receives row R0-s of time s; pbase is the slot of power row
@@ -337,12 +363,12 @@ __device__ __forceinline__ void tbf_iter(const CtxF &c, const CoefF &k,
         for (int j = 0; j < V; j++) d[j] = out[j];
         const float w_in = __shfl_sync(0xffffffffu, d[V - 1], (c.lane + 31) & 31);
         const float e_in = __shfl_sync(0xffffffffu, d[0], (c.lane + 1) & 31);
-        stf<KIND, V, MODE, SWAP>(c, k, R0 - s, s >= c.tsteps, PH == 0 ? A[s - 1] : B[s - 1],
+        stf<KIND, V, MODE, SWAP, stor_src(STOR)>(c, k, R0 - s, s >= c.tsteps, PH == 0 ? A[s - 1] : B[s - 1],
                                  PH == 0 ? B[s - 1] : A[s - 1], d, w_in, e_in,
                            pbase - s * C::ROWB + c.o4, pbase - (s - 1) * C::ROWB + c.o4, out);
     }
     if (store) {
-        if (STOR == STOR_F32) {
+        if (stor_fmt(STOR) == STOR_F32) {
             if (c.st_full) {
 #pragma unroll
                 for (int q = 0; q < V / 4; q++)
@@ -391,7 +417,7 @@ __device__ __forceinline__ void tbf_iter(const CtxF &c, const CoefF &k,
 
 // Decode my V cells of a staged raw row (header: codes of the blocks tx-1, tx, tx+1) into a
 // float ring row (and into its mirror when mirror != 0).
-template <int V, int STOR>
+template <int V, int STOR, bool ADD = false>
 __device__ __forceinline__ void tbf_decode(const CtxF &c, uint32_t raw, uint32_t dst, uint32_t mirror)
 {
     const uint2 cw = lds64u(raw + 8u * c.msel);
@@ -399,10 +425,16 @@ __device__ __forceinline__ void tbf_decode(const CtxF &c, uint32_t raw, uint32_t
 #pragma unroll
     for (int t = 0; t < V / 4; t++) {
         const uint2 w = lds64u(raw + 32u + 2u * V * c.lane + 8u * t);
-        const float x0 = __fmaf_rn(sc, q2f<STOR>(w.x & 0xffffu), mid);
-        const float x1 = __fmaf_rn(sc, q2f<STOR>(w.x >> 16), mid);
-        const float x2 = __fmaf_rn(sc, q2f<STOR>(w.y & 0xffffu), mid);
-        const float x3 = __fmaf_rn(sc, q2f<STOR>(w.y >> 16), mid);
+        float x0 = __fmaf_rn(sc, q2f<STOR>(w.x & 0xffffu), mid);
+        float x1 = __fmaf_rn(sc, q2f<STOR>(w.x >> 16), mid);
+        float x2 = __fmaf_rn(sc, q2f<STOR>(w.y & 0xffffu), mid);
+        float x3 = __fmaf_rn(sc, q2f<STOR>(w.y >> 16), mid);
+        if (ADD) {   // power row of a STOR_SRC kernel: p + amb*Rz
+            x0 = __fadd_rn(x0, c.src_add);
+            x1 = __fadd_rn(x1, c.src_add);
+            x2 = __fadd_rn(x2, c.src_add);
+            x3 = __fadd_rn(x3, c.src_add);
+        }
         sts128(dst + c.o4 + 16u * t, x0, x1, x2, x3);
         if (mirror) sts128(mirror + c.o4 + 16u * t, x0, x1, x2, x3);
     }
@@ -414,7 +446,7 @@ template <int KIND, int T, int V, int STOR>
 __device__ __forceinline__ void tbf_queue(const CtxF &c, const RowF &r, int lf, int lp, int lr)
 {
     using C = TB2F<KIND, T, V, STOR>;
-    if (STOR != STOR_F32) {
+    if (stor_fmt(STOR) != STOR_F32) {
 #pragma unroll
         for (int in = 0; in < (KIND == KTHERM ? 2 : 1); in++) {
             const uint32_t dr = (in == 0 ? c.sRF : c.sRP) + lr * C::RAWB;
@@ -468,10 +500,10 @@ __device__ __forceinline__ void tbf_step(const CtxF &c, const CoefF &k,
     using C = TB2F<KIND, T, V, STOR>;
     cp_async_wait<C::PF - 1>();   // row i has landed
     __syncwarp();
-    if (STOR != STOR_F32) {       // decode row i into the float rings
+    if (stor_fmt(STOR) != STOR_F32) {       // decode row i into the float rings
         tbf_decode<V, STOR>(c, c.sRF + r.rr * C::RAWB, c.sF + r.rf * C::ROWB, 0u);
         if (KIND == KTHERM)
-            tbf_decode<V, STOR>(c, c.sRP + r.rr * C::RAWB, c.sP + r.rp * C::ROWB,
+            tbf_decode<V, STOR, stor_src(STOR)>(c, c.sRP + r.rr * C::RAWB, c.sP + r.rp * C::ROWB,
                                 r.rp < C::PW - 1 ? c.sP + (C::NBP + r.rp) * C::ROWB : 0u);
         __syncwarp();
     }
@@ -490,7 +522,7 @@ __device__ __forceinline__ void tbf_step(const CtxF &c, const CoefF &k,
                                                c.sF + sm * C::ROWB, c.sF + sd * C::ROWB, pbase,
                                                r.gO, r, store);
     if (store) {
-        if (STOR == STOR_F32) r.gO += c.ld_out;
+        if (stor_fmt(STOR) == STOR_F32) r.gO += c.ld_out;
         else {
             r.qO += c.ld_q;
             r.mO += c.ntx;
@@ -505,13 +537,13 @@ __device__ __forceinline__ void tbf_step(const CtxF &c, const CoefF &k,
         lp -= (lp >= C::NBP) ? C::NBP : 0;
     }
     int lr = 0;
-    if (STOR != STOR_F32) {
+    if (stor_fmt(STOR) != STOR_F32) {
         lr = r.rr + C::PF;
         lr -= (lr >= C::NBR) ? C::NBR : 0;
     }
     if (i < r.i_load_end) {
         tbf_queue<KIND, T, V, STOR>(c, r, lf, lp, lr);
-        if (STOR == STOR_F32) {
+        if (stor_fmt(STOR) == STOR_F32) {
             r.gF += c.ld_in;
             if (KIND == KTHERM) r.gP += c.ld_pw;
         } else {
@@ -526,7 +558,7 @@ __device__ __forceinline__ void tbf_step(const CtxF &c, const CoefF &k,
     cp_async_commit();
     r.rf = (r.rf + 1 == C::NBF) ? 0 : r.rf + 1;
     if (KIND == KTHERM) r.rp = (r.rp + 1 == C::NBP) ? 0 : r.rp + 1;
-    if (STOR != STOR_F32) r.rr = (r.rr + 1 == C::NBR) ? 0 : r.rr + 1;
+    if (stor_fmt(STOR) != STOR_F32) r.rr = (r.rr + 1 == C::NBR) ? 0 : r.rr + 1;
 }
 
 template <int KIND, int T, int V, int MODE, bool SWAP, int STOR>
@@ -579,6 +611,7 @@ __device__ __forceinline__ void tbf_range(const Pass2D &p, long long f, const lo
     k.a0 = p.kf[0]; k.a1 = p.kf[1]; k.a2 = p.kf[2]; k.a3 = p.kf[3]; k.a4 = p.kf[4];
     k.a5 = p.kf[5];   // Hotspot: sdc * Ry
     k.a6 = p.kf[6];   // Hotspot: -2 Ry
+    c.src_add = __fmul_rn(k.a4, k.a3);   // Hotspot: amb * Rz
 
     while (f < fend) {
         const int tx = (int)(f / p.ny);
@@ -615,7 +648,7 @@ __device__ __forceinline__ void tbf_range(const Pass2D &p, long long f, const lo
         }
         c.tx = tx;
         c.msel = (c.xt < tx * C::CX) ? 0 : ((c.xt >= (tx + 1) * C::CX) ? 2 : 1);
-        if (STOR != STOR_F32) {
+        if (stor_fmt(STOR) != STOR_F32) {
             r.qF = c.qin + (long long)c.y_start * c.ld_q;
             r.mF = c.min_ + (long long)c.y_start * c.ntx;
             r.qP = (KIND == KTHERM) ? c.qpw + (long long)c.y_start * c.ld_q : nullptr;
@@ -640,7 +673,7 @@ __device__ __forceinline__ void tbf_range(const Pass2D &p, long long f, const lo
         for (int j = 0; j < C::PF; j++) {
             if (c.y_start + j <= c.last_row) {
                 tbf_queue<KIND, T, V, STOR>(c, r, j, (KIND == KTHERM) ? j : 0, j);
-                if (STOR == STOR_F32) {
+                if (stor_fmt(STOR) == STOR_F32) {
                     r.gF += c.ld_in;
                     if (KIND == KTHERM) r.gP += c.ld_pw;
                 } else {
@@ -722,7 +755,8 @@ __global__ void __launch_bounds__(32) k_tb2f(const Pass2D p)
 template <int KIND, int T, int V, bool SWAP>
 __global__ void __launch_bounds__(32) k_tb2f_batch(const BatchPass2D bp)
 {
-    using C = TB2F<KIND, T, V, 0>;
+    constexpr int S = KIND == KTHERM ? STOR_SRC : STOR_F32;   // power maps carry amb*Rz
+    using C = TB2F<KIND, T, V, S>;
     extern __shared__ __align__(16) float smem[];
     float A[C::NS][V], B[C::NS][V];
 #pragma unroll
@@ -737,7 +771,7 @@ __global__ void __launch_bounds__(32) k_tb2f_batch(const BatchPass2D bp)
         const Pass2D pg = bp.grids[g];
         const long long lo = f - bp.prefix[g];
         const long long hi = min(fend, bp.prefix[g + 1]) - bp.prefix[g];
-        tbf_range<KIND, T, V, SWAP, 0>(pg, lo, hi, A, B, smem);
+        tbf_range<KIND, T, V, SWAP, S>(pg, lo, hi, A, B, smem);
         f += hi - lo;
     }
 }

@@ -3,7 +3,11 @@
 stencil_run_noalloc serves callers that must not allocate device memory where they advance a
 grid (inside a pool they do not own, on latency-bound paths, under a locked-down allocator):
 it runs the same kernels with a fixed buffer the library reserves per device instead of a
-plan-owned one.  This file is collected last so that a failure here leaves every other test run.
+plan-owned one.  The one difference: contracted Hotspot plans stage a precomputed source map
+p + amb*Rz (a plan-owned buffer), while the allocation-free path reads the power map itself, so
+those two contracted results differ in rounding only (both meet the contracted bar against the
+oracle: max relative error <= 1e-5).  This file is collected last so that a failure here leaves
+every other test run.
 """
 import numpy as np
 import pytest
@@ -52,8 +56,15 @@ def test_noalloc_matches_plan_twice(eng, kind, exact):
     for w, steps in zip(cases, (37, 24)):
         ref = _plan_run(eng, w, steps, exact)
         got = _noalloc_run(eng, w, steps, exact)
-        # same kernels, same pass structure: identical results
-        assert np.array_equal(got, ref), (w.nx, w.ny, steps)
+        if exact or kind == 0:
+            # same kernels, same pass structure: identical results
+            assert np.array_equal(got, ref), (w.nx, w.ny, steps)
+        else:
+            # the same Table 2 expression with the ambient term fused differently
+            floor = 1e-6 * np.max(np.abs(ref))
+            rel = np.max(np.abs(got.astype(np.float64) - ref) / np.maximum(np.abs(ref), floor))
+            assert rel <= 1e-5, (w.nx, w.ny, steps, rel)
+            assert np.all(np.isfinite(got))
 
 
 def test_noalloc_in_place_and_limits(eng):
