@@ -12,6 +12,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "internal.h"
@@ -77,15 +78,25 @@ __global__ void __launch_bounds__(256) k_lp_decode(const uint16_t *__restrict__ 
     dst[(long long)y * ld_dst + x] = __fmaf_rn(m.y, dec<STOR>(src[(long long)y * ld_q + x]), m.x);
 }
 
-// Hotspot source row: p + amb*Rz (the product rounded once, as the kernels round it)
+// Hotspot source row: p + amb*Rz (the product rounded once, as the kernels round it); one
+// block row per grid row, four cells per thread (16-byte accesses when rows are aligned)
 __global__ void __launch_bounds__(256) k_hot_source(const float *__restrict__ p, long long ld_p,
-                                                    float *__restrict__ dst, int nx, int ny,
-                                                    float amb, float rz)
+                                                    float *__restrict__ dst, int nx, float amb,
+                                                    float rz, int vec)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)nx * ny) return;
-    const int y = (int)(i / nx), x = (int)(i % nx);
-    dst[i] = __fadd_rn(p[(long long)y * ld_p + x], __fmul_rn(amb, rz));
+    const int y = blockIdx.y;
+    const int x = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (x >= nx) return;
+    const float a = __fmul_rn(amb, rz);
+    const float *src = p + (long long)y * ld_p + x;
+    float *d = dst + (long long)y * nx + x;
+    if (vec) {
+        const float4 v = *reinterpret_cast<const float4 *>(src);
+        *reinterpret_cast<float4 *>(d) =
+            make_float4(__fadd_rn(v.x, a), __fadd_rn(v.y, a), __fadd_rn(v.z, a), __fadd_rn(v.w, a));
+    } else {
+        for (int j = 0; j < 4 && x + j < nx; j++) d[j] = __fadd_rn(src[j], a);
+    }
 }
 
 }  // namespace
@@ -93,9 +104,19 @@ __global__ void __launch_bounds__(256) k_hot_source(const float *__restrict__ p,
 cudaError_t hot_source(const float *p, long long ld_p, float *dst, int nx, int ny, float amb,
                        float rz, cudaStream_t st)
 {
-    const long long n = (long long)nx * ny;
-    k_hot_source<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, ld_p, dst, nx, ny, amb, rz);
-    return cudaGetLastError();
+    if (nx < 1 || ny < 1) return cudaErrorInvalidValue;
+    const int vec = ((uintptr_t)p % 16 == 0) && ((uintptr_t)dst % 16 == 0) && (nx % 4 == 0) &&
+                    (ld_p % 4 == 0);
+    const unsigned bx = (unsigned)((nx + 1023) / 1024);
+    // grid rows beyond the 65535 limit of gridDim.y go in slices
+    for (long long y0 = 0; y0 < ny; y0 += 65535) {
+        const unsigned rows = (unsigned)std::min<long long>(65535, ny - y0);
+        k_hot_source<<<dim3(bx, rows), 256, 0, st>>>(p + y0 * ld_p, ld_p, dst + y0 * nx, nx, amb,
+                                                     rz, vec);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t lp_encode(int stor, const float *src, long long ld_src, void *dst, long long ld_q,
