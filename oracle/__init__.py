@@ -51,6 +51,10 @@ def _load():
                 fn = getattr(lib, name)
                 fn.argtypes = [I, I, P, P, P, P, L, L, L, I]
                 fn.restype = I
+            for name in ("orc_run_star_f32", "orc_run_star_f64"):
+                fn = getattr(lib, name)
+                fn.argtypes = [I, I, P, P, P, L, L, L, I]
+                fn.restype = I
             lib.orc_adjoint2d_f64.argtypes = [I, P, P, P, L, L, I, I, P, P, P, P]
             lib.orc_adjoint2d_f64.restype = I
             lib.orc_set_threads.argtypes = [I]
@@ -100,6 +104,30 @@ def run(kind: int, u0: np.ndarray, coef, steps: int, power: np.ndarray | None = 
     out = np.empty_like(u)
     fn = lib.orc_run_f32 if dtype == np.float32 else lib.orc_run_f64
     rc = fn(kind, ndim, _ptr(u), _ptr(out), _ptr(p), _ptr(k), nx, ny, nz, int(steps))
+    if rc != 0:
+        raise RuntimeError(f"oracle failed ({rc})")
+    return out
+
+
+def run_star(R: int, u0: np.ndarray, coef, steps: int, dtype=np.float32) -> np.ndarray:
+    """`steps` Jacobi iterations of the radius-R star diffusion (Eqs. 1-2 with rad = R): 2D for
+    a (ny, nx) array, 3D for (nz, ny, nx); coef = [cc, per distance d = 1..R: cw, ce, cs, cn
+    (, cb, ca in 3D)], evaluated from the centre outwards, every operation rounded."""
+    lib = _load()
+    dtype = np.dtype(dtype)
+    u = np.ascontiguousarray(u0, dtype=dtype)
+    if u.ndim == 2:
+        (ny, nx), nz = u.shape, 1
+    elif u.ndim == 3:
+        nz, ny, nx = u.shape
+    else:
+        raise ValueError("2D or 3D arrays only")
+    k = np.ascontiguousarray(coef, dtype=dtype)
+    if k.size != 1 + (4 if u.ndim == 2 else 6) * R:
+        raise ValueError("coefficient count does not match the radius")
+    out = np.empty_like(u)
+    fn = lib.orc_run_star_f32 if dtype == np.float32 else lib.orc_run_star_f64
+    rc = fn(u.ndim, int(R), _ptr(u), _ptr(out), _ptr(k), nx, ny, nz, int(steps))
     if rc != 0:
         raise RuntimeError(f"oracle failed ({rc})")
     return out

@@ -8,6 +8,8 @@
  *   - Table 2: the four update equations (Diffusion 2D/3D, Hotspot 2D/3D), evaluated in the
  *     printed order with every operation rounded separately (built with -ffp-contract=off).
  *   - Sec. 5.1: out-of-bound neighbours fall back on the boundary cell itself.
+ *   - Eqs. 1-2 with rad > 1 (the paper's named extension): star diffusion of radius R, the
+ *     first-order diffusion order extended outwards one distance at a time.
  * The spatial and temporal blocking of Sec. 3 reorganise this computation without changing
  * a single cell's arithmetic, so the blocked engine must reproduce these values exactly
  * when it evaluates the same operations in the same order.

@@ -129,6 +129,67 @@ static void CAT(thermal3d_step, SFX)(const REAL *in, REAL *out, const REAL *pw, 
     }
 }
 
+/* Star diffusion of radius R (the rad of Eqs. 1-2 above 1, the paper's named extension to
+ * higher-order stencils), 2D: 4R+1 points, 3D: 6R+1 points.  k = [cc, then for d = 1..R:
+ * cw_d, ce_d, cs_d, cn_d (2D) or cw_d, ce_d, cs_d, cn_d, cb_d, ca_d (3D)], where the d-suffixed
+ * neighbour lies d cells away in that direction.  Evaluated as Table 2 evaluates the first-order
+ * diffusion, extended outwards: r = cc*c, then distance 1 in the order w, e, s, n (b, a), then
+ * distance 2 in the same order, and so on, every product and sum rounded on its own.  Each
+ * neighbour index is clamped to the grid on its own axis (Sec. 5.1's fallback on the boundary
+ * cell, applied at every distance).  For R = 1 this is exactly the Table 2 update. */
+static void CAT(star_step, SFX)(const REAL *in, REAL *out, int ndim, int R, long nx, long ny,
+                                long nz, const REAL *k)
+{
+    long pl = nx * ny;
+    long planes = ndim == 3 ? nz : 1;
+    int per = ndim == 3 ? 6 : 4;
+#pragma omp parallel for schedule(static)
+    for (long zy = 0; zy < planes * ny; zy++) {
+        long z = zy / ny, y = zy % ny;
+        for (long x = 0; x < nx; x++) {
+            long i = z * pl + y * nx + x;
+            REAL r = k[0] * in[i];
+            for (int d = 1; d <= R; d++) {
+                long xw = x - d >= 0 ? x - d : 0, xe = x + d <= nx - 1 ? x + d : nx - 1;
+                long ys = y + d <= ny - 1 ? y + d : ny - 1, yn = y - d >= 0 ? y - d : 0;
+                const REAL *kd = k + 1 + (long)per * (d - 1);
+                r = r + kd[0] * in[z * pl + y * nx + xw];
+                r = r + kd[1] * in[z * pl + y * nx + xe];
+                r = r + kd[2] * in[z * pl + ys * nx + x];
+                r = r + kd[3] * in[z * pl + yn * nx + x];
+                if (ndim == 3) {
+                    long zb = z - d >= 0 ? z - d : 0, za = z + d <= nz - 1 ? z + d : nz - 1;
+                    r = r + kd[4] * in[zb * pl + y * nx + x];
+                    r = r + kd[5] * in[za * pl + y * nx + x];
+                }
+            }
+            out[i] = r;
+        }
+    }
+}
+
+/* `steps` Jacobi iterations of the radius-R star diffusion (ndim 2 or 3, R >= 1). */
+int CAT(orc_run_star, SFX)(int ndim, int R, const REAL *u0, REAL *out, const REAL *coef,
+                           long nx, long ny, long nz, int steps)
+{
+    if (!u0 || !out || !coef || nx < 1 || ny < 1 || nz < 1 || steps < 0 || R < 1) return -1;
+    if (ndim == 2) nz = 1;
+    else if (ndim != 3) return -1;
+    size_t n = (size_t)nx * ny * nz;
+    REAL *a = (REAL *)malloc(n * sizeof(REAL));
+    REAL *b = (REAL *)malloc(n * sizeof(REAL));
+    if (!a || !b) { free(a); free(b); return -1; }
+    memcpy(a, u0, n * sizeof(REAL));
+    for (int s = 0; s < steps; s++) {
+        CAT(star_step, SFX)(a, b, ndim, R, nx, ny, nz, coef);
+        REAL *t = a; a = b; b = t;
+    }
+    memcpy(out, a, n * sizeof(REAL));
+    free(a);
+    free(b);
+    return 0;
+}
+
 /* `steps` Jacobi iterations of stencil (kind, ndim) from u0 into out (Sec. 2.1: read one
  * buffer, write the other, swap).  steps == 0 copies.  Returns 0, or -1 on a bad argument or
  * a failed allocation. */

@@ -98,6 +98,33 @@ def diffusion_coefficients(seed: int, ndim: int, offset: int) -> np.ndarray:
     return (u / u.sum()).astype(np.float32)
 
 
+def star_coefficients(seed: int, ndim: int, R: int, offset: int) -> np.ndarray:
+    """Radius-R star diffusion: 1 + 4R (2D) or 1 + 6R (3D) positive coefficients normalised to
+    sum 1, in the layout [cc, per distance d = 1..R: cw, ce, cs, cn (, cb, ca)]; u_k ~ U[0.05, 1)
+    with the distance-d draws divided by d (weights fall off outwards), normalised in float64,
+    rounded to float32."""
+    per = 4 if ndim == 2 else 6
+    m = 1 + per * R
+    u = 0.05 + 0.95 * uniform01(seed, m, offset)
+    for d in range(1, R + 1):
+        u[1 + per * (d - 1):1 + per * d] /= d
+    return (u / u.sum()).astype(np.float32)
+
+
+def make_star(ndim: int, R: int, nx: int, ny: int, nz: int = 1, steps: int = 1, seed: int = 1,
+              name: str = "") -> Workload:
+    """Radius-R star diffusion problem: field ~ U[0, 1) then the coefficients, from stream
+    `seed` (kind DIFFUSION, no power map)."""
+    if ndim == 2:
+        nz = 1
+    n = nx * ny * nz
+    shape = (ny, nx) if ndim == 2 else (nz, ny, nx)
+    u0 = uniform_f32(seed, n, 0.0, 1.0, 0).reshape(shape)
+    coef = star_coefficients(seed, ndim, R, n)
+    return Workload(name or f"star{R}_{ndim}d", DIFFUSION, ndim, nx, ny, nz, steps, seed, u0,
+                    None, coef)
+
+
 def thermal_scalars(seed: int, offset: int):
     """k_dt ~ U[0.5,1), Rx, Ry ~ U[0.05,0.2), Rz ~ U[1e-4,1e-3), redrawn until the explicit
     stability bound k_dt * (2 Rx + 2 Ry + Rz) <= 1 holds (it always holds for these ranges)."""

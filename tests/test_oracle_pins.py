@@ -395,3 +395,111 @@ def test_adjoint_finite_differences(orc, kind):
     if kind == 1:
         fd = (L(u0, coef, pw + h * d) - L(u0, coef, pw - h * d)) / (2 * h)
         assert fd == pytest.approx(np.sum(gp * d), rel=1e-7)
+
+
+# --- star diffusion of radius R (Eqs. 1-2 with rad > 1) ------------------------------------
+
+def _dense_star(ndim, R, nx, ny, nz, coef):
+    """One step of the radius-R star as a matrix, from the definition: cell i gets weight
+    c_{dir,d} on the cell d steps away in direction dir, each axis clamped into the grid."""
+    coef = np.asarray(coef, np.float64)
+    per = 4 if ndim == 2 else 6
+    N = nx * ny * nz
+    A = np.zeros((N, N))
+    clamp = lambda v, n: min(max(v, 0), n - 1)
+    idx = lambda x, y, z: (z * ny + y) * nx + x
+    for z, y, x in itertools.product(range(nz), range(ny), range(nx)):
+        i = idx(x, y, z)
+        A[i, i] += coef[0]
+        for d in range(1, R + 1):
+            k = coef[1 + per * (d - 1):1 + per * d]
+            A[i, idx(clamp(x - d, nx), y, z)] += k[0]
+            A[i, idx(clamp(x + d, nx), y, z)] += k[1]
+            A[i, idx(x, clamp(y + d, ny), z)] += k[2]
+            A[i, idx(x, clamp(y - d, ny), z)] += k[3]
+            if ndim == 3:
+                A[i, idx(x, y, clamp(z - d, nz))] += k[4]
+                A[i, idx(x, y, clamp(z + d, nz))] += k[5]
+    return A
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_star_radius1_is_table2(orc, ndim):
+    for t, shape in enumerate([(1, 1, 1), (7, 5, 3), (40, 33, 9)]):
+        nx, ny, nz = shape
+        w = synth.make(0, ndim, nx, ny, nz, seed=600 + t)
+        for dt in (np.float32, np.float64):
+            a = orc.run(0, w.u0, w.coef, 9, dtype=dt)
+            b = orc.run_star(1, w.u0, w.coef, 9, dtype=dt)
+            assert np.array_equal(a, b), (shape, dt)
+
+
+@pytest.mark.parametrize("ndim,R", [(2, 2), (2, 3), (3, 2)])
+def test_star_impulse(orc, ndim, R):
+    """Interior impulse: after one step each coefficient sits d cells away on the opposite
+    side of its direction (the cell whose west-d neighbour is the impulse gets cw_d)."""
+    per = 4 if ndim == 2 else 6
+    w = synth.make_star(ndim, R, 19, 17, 15, seed=700 + R)
+    k = w.coef.astype(np.float64)
+    u = np.zeros(w.shape)
+    c = (7, 8, 9) if ndim == 3 else (8, 9)
+    u[c] = 1.0
+    o = orc.run_star(R, u, k, 1, dtype=np.float64)
+    expect = np.zeros_like(u)
+    expect[c] = k[0]
+    for d in range(1, R + 1):
+        kd = k[1 + per * (d - 1):1 + per * d]
+        def at(dz, dy, dx):
+            return (c[0] + dz, c[1] + dy, c[2] + dx) if ndim == 3 else (c[0] + dy, c[1] + dx)
+        expect[at(0, 0, d)] = kd[0]    # its west-d neighbour is the impulse
+        expect[at(0, 0, -d)] = kd[1]   # east-d
+        expect[at(0, -d, 0)] = kd[2]   # south-d (y + d)
+        expect[at(0, d, 0)] = kd[3]    # north-d (y - d)
+        if ndim == 3:
+            expect[at(d, 0, 0)] = kd[4]    # below-d (z - d)
+            expect[at(-d, 0, 0)] = kd[5]   # above-d (z + d)
+    assert np.array_equal(o, expect)
+
+
+def test_star_clamp_at_every_distance(orc):
+    """Impulse on the x = 0 edge: cell j (1 <= j <= R) sees it as every west neighbour at a
+    distance d >= j (clamped to x = 0), cell 0 as all R of them."""
+    R = 3
+    w = synth.make_star(2, R, 12, 9, seed=710)
+    k = w.coef.astype(np.float64)
+    u = np.zeros(w.shape)
+    u[4, 0] = 1.0
+    o = orc.run_star(R, u, k, 1, dtype=np.float64)
+    cw = [k[1 + 4 * (d - 1)] for d in range(1, R + 1)]
+    assert o[4, 0] == pytest.approx(k[0] + sum(cw), rel=1e-15)
+    for j in range(1, R + 1):
+        assert o[4, j] == pytest.approx(sum(cw[j - 1:]), rel=1e-15), j
+    assert np.all(o[4, R + 1:] == 0)
+
+
+@pytest.mark.parametrize("ndim,R", [(2, 2), (2, 3), (3, 2)])
+def test_star_dense_matrix_brute_force(orc, ndim, R):
+    sizes = ([(nx, ny, 1) for nx in (1, 2, 3, 5, 8) for ny in (1, 4, 7)] if ndim == 2 else
+             [(1, 1, 1), (2, 3, 4), (5, 2, 3), (4, 4, 4), (3, 6, 5)])
+    for t, (nx, ny, nz) in enumerate(sizes):
+        w = synth.make_star(ndim, R, nx, ny, nz, seed=800 + t)
+        steps = (t * 5) % 13
+        A = _dense_star(ndim, R, nx, ny, nz, w.coef)
+        v = w.u0.astype(np.float64).ravel()
+        for _ in range(steps):
+            v = A @ v
+        o = orc.run_star(R, w.u0, w.coef, steps, dtype=np.float64).ravel()
+        assert np.allclose(o, v, rtol=1e-13, atol=1e-15), (nx, ny, nz, steps)
+
+
+def test_star_constant_field_and_max_principle(orc):
+    # dyadic coefficients summing exactly to 1: a constant field is kept exactly
+    k = np.array([0.5] + [0.0625] * 8, np.float64)     # 2D, R = 2: 1 + 8 coefficients
+    u = np.full((13, 21), 0.375)
+    for dt in (np.float32, np.float64):
+        assert np.all(orc.run_star(2, u, k, 25, dtype=dt) == 0.375)
+    # positive coefficients summing to 1: the range of the field never grows
+    w = synth.make_star(2, 3, 64, 48, seed=820)
+    o = orc.run_star(3, w.u0, w.coef, 40, dtype=np.float64)
+    lo, hi = float(w.u0.min()), float(w.u0.max())
+    assert o.min() >= lo - 1e-12 and o.max() <= hi + 1e-12
