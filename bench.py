@@ -46,6 +46,9 @@ WORKLOADS = {
     "diffusion2d_1024": lambda: synth.c1_diffusion2d(),
     "diffusion3d_512": lambda: synth.c3a_diffusion3d(),
     "thermal3d_512x512x256": lambda: synth.c3b_thermal3d(),
+    # radius-2 star diffusion (9 points; Eqs. 1-2 with rad = 2), the 2D diffusion grid size
+    "star2_2d_16384": lambda: synth.make_star(2, 2, 16384, 16384, steps=1000, seed=7,
+                                              name="star2_2d_16384x16384_1000"),
 }
 DEFAULT = "thermal2d_16384"
 
@@ -138,6 +141,19 @@ def profiled_traffic(workload: str, ndim: int):
     return None
 
 
+def _oracle_run(w, steps, dtype=np.float32):
+    import oracle
+    if w.rad > 1:
+        return oracle.run_star(w.rad, w.u0, w.coef, steps, dtype=dtype)
+    return oracle.run(w.kind, w.u0, w.coef, steps, w.power, dtype=dtype)
+
+
+def _flops(w):
+    """Counted flops per cell update: Table 2's for the first-order stencils, 8R + 1 for the
+    radius-R star (one multiply and 4R multiply-adds counted as two flops each)."""
+    return 8 * w.rad + 1 if w.rad > 1 else FLOPS[(w.kind, w.ndim)]
+
+
 def _oracle_sample_steps(w, budget_s: float):
     """Time steps of the full grid that take about budget_s seconds on the host cores (from
     the difference of a 1-step and a 3-step run, so set-up costs do not count)."""
@@ -148,7 +164,7 @@ def _oracle_sample_steps(w, budget_s: float):
     t = []
     for s in (1, 3):
         t0 = time.perf_counter()
-        oracle.run(w.kind, w.u0, w.coef, s, w.power)
+        _oracle_run(w, s)
         t.append(time.perf_counter() - t0)
     per_step = max((t[1] - t[0]) / 2, 1e-5)
     return max(1, min(w.steps, int(budget_s / per_step))), cores
@@ -160,7 +176,7 @@ def cpu_baseline(w, budget_s: float = 15.0):
     import oracle
     steps, cores = _oracle_sample_steps(w, budget_s)
     t0 = time.perf_counter()
-    oracle.run(w.kind, w.u0, w.coef, steps, w.power)
+    _oracle_run(w, steps)
     t = time.perf_counter() - t0
     return {"value": w.cells * steps / t / 1e9, "unit": "GCell/s", "cores": cores,
             "kind": "oracle",
@@ -200,10 +216,10 @@ def run_reference(args, w):
     per_step = max(2.0, 150.0 / max(1, args.steps + args.warmup))
     steps, cores = _oracle_sample_steps(w, per_step)
     for _ in range(args.warmup):
-        oracle.run(w.kind, w.u0, w.coef, steps, w.power)
+        _oracle_run(w, steps)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.run(w.kind, w.u0, w.coef, steps, w.power)
+        _oracle_run(w, steps)
     t = time.perf_counter() - t0
     value = w.cells * steps * args.steps / t / 1e9
     sample = (f"full {'x'.join(map(str, w.shape[::-1]))} grid, {steps} of {w.steps} time steps "
@@ -529,7 +545,11 @@ def main():
         return bench_adjoint(args)
     w = WORKLOADS[args.workload]()
     resized = bool(args.nx or args.ny or args.nz or args.time_steps)
-    if resized:
+    if resized and w.rad > 1:
+        w = synth.make_star(w.ndim, w.rad, args.nx or w.nx, args.ny or w.ny, args.nz or w.nz,
+                            steps=args.time_steps or w.steps, seed=w.seed,
+                            name=f"{w.name.split('_')[0]}_resized")
+    elif resized:
         w = synth.make(w.kind, w.ndim, args.nx or w.nx, args.ny or w.ny, args.nz or w.nz,
                        steps=args.time_steps or w.steps, seed=w.seed,
                        name=f"{w.name.split('_')[0]}_resized")
@@ -556,7 +576,7 @@ def main():
     out = torch.empty_like(u0)
     plan = st.Plan(w.kind, w.ndim, w.nx, w.ny, w.nz, force_T=args.T, force_bx=args.bx,
                    force_vec=args.vec, force_by=args.by, storage=args.storage,
-                   stream=stream.cuda_stream)
+                   stream=stream.cuda_stream, rad=w.rad if w.rad > 1 else 0)
     info = plan.info()
     T = info["T"]
     passes = -(-w.steps // T)
@@ -640,7 +660,7 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    fl = FLOPS[(w.kind, w.ndim)]
+    fl = _flops(w)
     by = BYTES[w.kind]
     alu_peak = fp32_peak_tflops(sms, mhz)
     hbm_peak = float(peaks["hbm_gbs"])
@@ -673,7 +693,7 @@ def main():
 
     # ---- 16-bit storage: speed on the same workload, error vs the float64 oracle ------------
     lowp = None
-    if w.ndim == 2 and not resized and not args.no_lowp and not args.storage:
+    if w.ndim == 2 and w.rad <= 1 and not resized and not args.no_lowp and not args.storage:
         lowp = {}
         for name, stor in (("bf16", st.ST_BF16), ("fp16", st.ST_F16)):
             qplan = st.Plan(w.kind, 2, w.nx, w.ny, storage=stor, stream=stream.cuda_stream)

@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define ST_ABI_VERSION 1
+#define ST_ABI_VERSION 2
 
 /* status codes */
 #define ST_OK                    0
@@ -81,6 +81,10 @@ typedef struct {
     int exact;       /* 1: Table 2 order, no fused multiply-add; 0: contracted */
     int strict;      /* 1: reject coefficients that break the explicit stability bound */
     void *stream;    /* cudaStream_t the plan launches on; NULL = the legacy default stream */
+    int rad;         /* stencil radius (rad of Eqs. 1-2): 0 or 1 = the Table 2 stencils; 2..4 =
+                        star diffusion of that radius (4*rad+1 points; ST_DIFFUSION, 2D, float32
+                        storage), coefficients [cc, then per distance d = 1..rad: cw_d, ce_d,
+                        cs_d, cn_d], each neighbour clamped to the grid on its axis (Sec. 5.1) */
 } stencil_desc;
 
 /* What a plan chose (for reports and tests). */
@@ -95,6 +99,9 @@ typedef struct {
     long long scratch_bytes;   /* device scratch the plan owns */
     int exact;          /* as requested */
     int kernel_id;      /* internal kernel family (diagnostics) */
+    double model_gcells;   /* the GPU restatement of Eqs. 3-9 with the library's calibration,
+                              for this plan at 1000 steps, in 10^9 cell updates/s; 0 where no
+                              calibration exists (exact and 16-bit plans) */
 } stencil_plan_info;
 
 /* Create a plan for one problem shape on the current CUDA device.  Allocates one grid-sized

@@ -41,7 +41,7 @@ class stencil_desc(ctypes.Structure):
                 ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("storage", ctypes.c_int),
                 ("force_T", ctypes.c_int), ("force_bx", ctypes.c_int), ("force_by", ctypes.c_int),
                 ("force_vec", ctypes.c_int), ("exact", ctypes.c_int), ("strict", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("rad", ctypes.c_int)]
 
 
 class stencil_plan_info(ctypes.Structure):
@@ -189,10 +189,10 @@ def current_stream():
 
 def stencil_plan_create(kind: int, ndim: int, nx: int, ny: int, nz: int = 1, *, storage=ST_F32,
                         force_T=0, force_bx=0, force_by=0, force_vec=0, exact=False,
-                        strict=False, stream=None):
+                        strict=False, stream=None, rad=0):
     d = stencil_desc(kind, ndim, nx, ny, nz if ndim == 3 else 1, storage, force_T, force_bx,
                      force_by, force_vec, 1 if exact else 0, 1 if strict else 0,
-                     current_stream() if stream is None else stream)
+                     current_stream() if stream is None else stream, rad)
     h = ctypes.c_void_p()
     _check(lib.stencil_plan_create(ctypes.byref(h), ctypes.byref(d)), "stencil_plan_create")
     return h

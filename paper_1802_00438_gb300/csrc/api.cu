@@ -55,6 +55,7 @@ struct stencil_plan_s {
     int *err = nullptr;   // device flag set by a kernel whose bounded wait gave up
     double model = 0.0;   // calibrated model's prediction for this plan (1000 steps), GCell/s
     float *src = nullptr;   // contracted float32 Hotspot 2D: the source map p + amb*Rz
+    int ntx_star = 0, nty_star = 0;   // star diffusion (rad > 1): tiles along x and y
     std::vector<PassCfg3D> cfg3;
     // timing
     bool timing = false;
@@ -88,6 +89,7 @@ long long cells_of(const stencil_desc &d) { return (long long)d.nx * d.ny * d.nz
 
 int ncoef(const stencil_desc &d)
 {
+    if (d.rad > 1) return 1 + (d.ndim == 2 ? 4 : 6) * d.rad;
     if (d.ndim == 2) return 5;
     return d.kind == ST_DIFFUSION ? 7 : 9;
 }
@@ -405,6 +407,34 @@ int run_pass2q(stencil_plan_s *p, int src, int dst, const float *k, int tsteps)
     return map_cuda(e);
 }
 
+int run_pass_star(stencil_plan_s *p, const float *src, float *dst, const float *k, int tsteps)
+{
+    PassStar2D a = {};
+    a.in = src;
+    a.out = dst;
+    a.ld_in = p->d.nx;
+    a.ld_out = p->d.nx;
+    a.nx = p->d.nx;
+    a.ny = p->d.ny;
+    a.tsteps = tsteps;
+    a.ntx = p->ntx_star;
+    a.nty = p->nty_star;
+    for (int i = 0; i < ncoef(p->d) && i < 17; i++) a.k[i] = k[i];
+    a.vec_out = ((uintptr_t)dst % 16 == 0) && (p->d.nx % 4 == 0);
+    a.err = p->err;
+    CUtensorMap tm;
+    std::memset(&tm, 0, sizeof(tm));
+    a.use_tma = tma3d_encode(&tm, src, p->d.nx, p->d.ny, 1, 128, 128) ? 1 : 0;
+    if (p->timing && p->ev_used + 2 > 2 * 1024) {
+        const int rc = flush_timing(p);
+        if (rc != ST_OK) return rc;
+    }
+    cudaError_t e = record(p, true);
+    if (e == cudaSuccess) e = star2d_launch(p->d.rad, p->d.exact, p->T, a, tm, p->stream);
+    if (e == cudaSuccess) e = record(p, false);
+    return map_cuda(e);
+}
+
 int run_pass3(stencil_plan_s *p, const float *src, float *dst, const float *pw, const float *k,
               int tsteps)
 {
@@ -487,6 +517,11 @@ int stencil_plan_create(stencil_plan *out, const stencil_desc *desc)
     if (d.storage != ST_F32 && (d.ndim != 2 || d.exact)) return ST_ERR_UNSUPPORTED;
     if (d.force_T < 0 || d.force_bx < 0 || d.force_by < 0 || d.force_vec < 0)
         return ST_ERR_INVALID_ARG;
+    if (d.rad < 0) return ST_ERR_INVALID_ARG;
+    if (d.rad > 1 && (d.kind != ST_DIFFUSION || d.ndim != 2 || d.storage != ST_F32 || d.rad > 4 ||
+                      (d.force_bx && d.force_bx != 128) || (d.force_by && d.force_by != 128) ||
+                      (d.force_vec && d.force_vec != 4)))
+        return ST_ERR_UNSUPPORTED;
 
     stencil_plan_s *p = new (std::nothrow) stencil_plan_s();
     if (!p) return ST_ERR_OOM;
@@ -501,7 +536,31 @@ int stencil_plan_create(stencil_plan *out, const stencil_desc *desc)
     }
 
     p->stor = d.storage == ST_BF16 ? 1 : (d.storage == ST_F16 ? 2 : 0);
-    if (d.ndim == 2) {
+    if (d.rad > 1) {
+        // star diffusion: 128 x 128 tiles, T from {1, 2, 4} (default: the largest whose halos
+        // leave at least 70 % of the tile's cells in its compute block)
+        int T = d.force_T;
+        if (!T) {
+            T = 1;
+            for (int t : {2, 4}) {
+                const double cx = 128 - 2 * ((d.rad * t + 3) / 4 * 4), cy = 128 - 2 * d.rad * t;
+                if (cx > 0 && cy > 0 && cx * cy >= 0.7 * 128 * 128) T = t;
+            }
+        }
+        if (!star2d_available(d.rad, d.exact, T)) rc = ST_ERR_UNSUPPORTED;
+        if (rc == ST_OK) {
+            e = star2d_prepare(d.rad, d.exact, T);
+            if (e != cudaSuccess) rc = map_cuda(e);
+        }
+        if (rc == ST_OK) {
+            p->T = T;
+            const int cx = 128 - 2 * star2d_halo_x(d.rad, T), cy = 128 - 2 * star2d_halo_y(d.rad, T);
+            p->ntx_star = (d.nx + cx - 1) / cx;
+            p->nty_star = (d.ny + cy - 1) / cy;
+            p->ld_scratch = d.nx;   // dense rows: the tensor map of a grid uses the grid's pitch
+            p->scratch_bytes = (size_t)d.nx * d.ny * sizeof(float);
+        }
+    } else if (d.ndim == 2) {
         // Contracted plans run one-warp tiles of V = 8 cells per thread (bsize_x = 256) with
         // partial-sum stages; exact plans run the rotating-window kernel, V = 4, with W warps
         // per tile (bsize_x = 128 W).
@@ -611,7 +670,7 @@ int stencil_plan_create(stencil_plan *out, const stencil_desc *desc)
         e = cudaMalloc(&p->src, (size_t)d.nx * d.ny * sizeof(float));
         if (e != cudaSuccess) rc = map_cuda(e);
     }
-    if (rc == ST_OK && !d.exact && !p->stor) {
+    if (rc == ST_OK && !d.exact && !p->stor && d.rad <= 1) {
         if (d.ndim == 2) {
             int bps = 0;
             const Shape2D sh{d.kind, 0, p->T, p->V, p->W, d.kind == ST_THERMAL ? STOR_SRC : 0};
@@ -699,8 +758,9 @@ int stencil_run(stencil_plan p, const void *grid_in, void *grid_out, const void 
         const bool to_out = shift ? ((passes - i) % 2 == 0) : ((passes - 1 - i) % 2 == 0);
         float *dst = to_out ? out : p->scratch;
         const long long ldd = to_out ? ldo : ldsc;
-        int rc = d.ndim == 2 ? run_pass2(p, src, lds, dst, ldd, pw, coeffs, ts)
-                             : run_pass3(p, src, dst, pw, coeffs, ts);
+        int rc = d.rad > 1     ? run_pass_star(p, src, dst, coeffs, ts)
+                 : d.ndim == 2 ? run_pass2(p, src, lds, dst, ldd, pw, coeffs, ts)
+                               : run_pass3(p, src, dst, pw, coeffs, ts);
         if (rc != ST_OK) {
             p->sticky = rc;
             return rc;
@@ -746,7 +806,15 @@ int stencil_plan_get_info(stencil_plan p, stencil_plan_info *info)
     info->sms = p->sms;
     info->scratch_bytes = (long long)p->scratch_bytes;
     info->exact = p->d.exact;
-    if (p->d.ndim == 2) {
+    if (p->d.rad > 1) {
+        info->bx = 128;
+        info->by = 128;
+        info->halo = star2d_halo_x(p->d.rad, p->T);
+        info->vec = 4;
+        info->warps = 16;
+        info->ctas = p->ntx_star * p->nty_star;
+        info->kernel_id = 5;
+    } else if (p->d.ndim == 2) {
         PassCfg2D *c = nullptr;
         int rc = prepare2(p, p->T, &c);
         if (rc != ST_OK) return rc;

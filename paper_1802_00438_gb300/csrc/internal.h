@@ -73,6 +73,27 @@ size_t tb2d_smem_bytes(const Shape2D &s);
 cudaError_t tb2d_prepare(const Shape2D &s, int *blocks_per_sm);   // smem opt-in + occupancy
 cudaError_t tb2d_launch(const Shape2D &s, const Pass2D &p, cudaStream_t st);
 
+// One pass of the radius-R star diffusion in 2D (star2d.cu): 128 x 128 tiles, halos R*T.
+struct PassStar2D {
+    const float *in;
+    float *out;
+    long long ld_in, ld_out;   // row pitches in floats
+    int nx, ny;
+    int tsteps;                // steps fused in this pass, 1..T
+    int ntx, nty;              // tiles along x and y
+    float k[17];               // cc, then cw, ce, cs, cn per distance 1..R
+    int use_tma;               // stage the tile by one tensor-map copy
+    int vec_out;               // output rows start on 16-byte boundaries
+    int *err;                  // device flag: a bounded wait gave up
+};
+
+bool star2d_available(int R, int exact, int T);
+int star2d_halo_x(int R, int T);
+int star2d_halo_y(int R, int T);
+cudaError_t star2d_prepare(int R, int exact, int T);
+cudaError_t star2d_launch(int R, int exact, int T, const PassStar2D &p, const CUtensorMap &tin,
+                          cudaStream_t st);
+
 // One pass of the 3D sweep (tb3d.cu).
 struct Pass3D {
     const float *in;

@@ -80,6 +80,7 @@ class Workload:
     u0: np.ndarray = field(repr=False)
     power: np.ndarray | None = field(repr=False)
     coef: np.ndarray = field(repr=False)
+    rad: int = 1    # stencil radius: 1 = the Table 2 stencils, > 1 = star diffusion
 
     @property
     def shape(self):
@@ -122,7 +123,7 @@ def make_star(ndim: int, R: int, nx: int, ny: int, nz: int = 1, steps: int = 1, 
     u0 = uniform_f32(seed, n, 0.0, 1.0, 0).reshape(shape)
     coef = star_coefficients(seed, ndim, R, n)
     return Workload(name or f"star{R}_{ndim}d", DIFFUSION, ndim, nx, ny, nz, steps, seed, u0,
-                    None, coef)
+                    None, coef, R)
 
 
 def thermal_scalars(seed: int, offset: int):
