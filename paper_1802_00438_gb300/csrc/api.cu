@@ -94,6 +94,8 @@ int ncoef(const stencil_desc &d)
     return d.kind == ST_DIFFUSION ? 7 : 9;
 }
 
+bool stor_src_bits(int stor) { return (stor & STOR_SRC) != 0; }
+
 // storage bits of a plan's 2D kernel shape: the format, plus STOR_SRC for contracted Hotspot
 // kernels (they stage p + amb*Rz instead of the power map)
 int shape_stor(const stencil_plan_s *p)
@@ -361,6 +363,7 @@ int run_pass2(stencil_plan_s *p, const float *src, long long lds, float *dst, lo
     for (int i = 0; i < 5; i++) a.k[i] = a.kf[i] = k[i];
     a.kf[5] = k[0] * k[2];    // Hotspot: sdc * Ry, rounded once (float32)
     a.kf[6] = -2.0f * k[2];   // Hotspot: -2 Ry (exact)
+    if (stor_src_bits(c->shape.stor)) hot_coeffs_src(k, a.kf);
     a.vec_in = ((uintptr_t)src % 16 == 0) && (lds % 4 == 0);
     a.vec_out = ((uintptr_t)dst % 16 == 0) && (ldd % 4 == 0);
     a.vec_pw = pw ? (((uintptr_t)pw % 16 == 0) && (p->d.nx % 4 == 0)) : 0;
@@ -392,6 +395,7 @@ int run_pass2q(stencil_plan_s *p, int src, int dst, const float *k, int tsteps)
     for (int i = 0; i < 5; i++) a.k[i] = a.kf[i] = k[i];
     a.kf[5] = k[0] * k[2];
     a.kf[6] = -2.0f * k[2];
+    if (stor_src_bits(c->shape.stor)) hot_coeffs_src(k, a.kf);
     a.vec_in = a.vec_out = a.vec_pw = 1;
     a.stor = p->stor;
     a.qin = p->q[src];

@@ -228,6 +228,7 @@ int stencil_batch_create(stencil_batch *out, const stencil_batch_grid *grids, in
                 for (int i = 0; i < 5; i++) a.k[i] = a.kf[i] = q.coeffs[i];
                 a.kf[5] = q.coeffs[0] * q.coeffs[2];
                 a.kf[6] = -2.0f * q.coeffs[2];
+                if (q.kind == ST_THERMAL) hot_coeffs_src(q.coeffs, a.kf);   // source-map kernels
                 a.vec_in = ((uintptr_t)a.in % 16 == 0) && (a.ld_in % 4 == 0);
                 a.vec_out = ((uintptr_t)a.out % 16 == 0) && (a.ld_out % 4 == 0);
                 a.vec_pw = a.pw ? (((uintptr_t)a.pw % 16 == 0) && (q.nx % 4 == 0)) : 0;

@@ -61,6 +61,10 @@ cudaError_t lp_encode(int stor, const float *src, long long ld_src, void *dst, l
 cudaError_t lp_decode(int stor, const void *src, long long ld_q, const float2 *meta, float *dst,
                       long long ld_dst, int nx, int ny, int cx, cudaStream_t st);
 
+// Contracted Hotspot coefficients of the source-map kernels (STOR_SRC) from [sdc, Rx, Ry, Rz,
+// amb]: kf = [sdc, Rx', Ry', Rz, amb, fl(sdc*Ry'), -(2Rx' + 2Ry')] with 2Rx' + 2Ry' exact
+void hot_coeffs_src(const float *k, float *kf);
+
 // Hotspot source map dst = p + amb*Rz (dense rows of nx), read by the contracted kernels
 cudaError_t hot_source(const float *p, long long ld_p, float *dst, int nx, int ny, float amb,
                        float rz, cudaStream_t st);

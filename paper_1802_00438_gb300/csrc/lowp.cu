@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 
 #include "internal.h"
@@ -100,6 +101,31 @@ __global__ void __launch_bounds__(256) k_hot_source(const float *__restrict__ p,
 }
 
 }  // namespace
+
+void hot_coeffs_src(const float *k, float *kf)
+{
+    // kf = [sdc, Rx', Ry', Rz, amb, fl(sdc*Ry'), -(2Rx' + 2Ry')] where Rx', Ry' are Rx, Ry with
+    // the bits below half an ulp of 2Rx + 2Ry cleared, so that 2Rx' + 2Ry' is exact in float32:
+    // the centre weight then cancels the four neighbour weights exactly on a uniform field and
+    // the folded constant moves no fixed point (Rx', Ry' differ from Rx, Ry by < 1e-7 relative)
+    const double rx = k[1], ry = k[2];
+    double ul = std::ldexp(1.0, std::ilogb((float)(2.0 * rx + 2.0 * ry)) - 23);
+    double rxq = 0, ryq = 0;
+    for (int i = 0; i < 3; i++) {
+        rxq = std::nearbyint(rx / (ul / 2)) * (ul / 2);
+        ryq = std::nearbyint(ry / (ul / 2)) * (ul / 2);
+        const double sum = 2 * rxq + 2 * ryq;
+        if ((double)(float)sum == sum) break;
+        ul *= 2;   // the sum crossed into the next binade
+    }
+    kf[0] = k[0];
+    kf[1] = (float)rxq;
+    kf[2] = (float)ryq;
+    kf[3] = k[3];
+    kf[4] = k[4];
+    kf[5] = kf[0] * kf[2];
+    kf[6] = -(float)(2 * rxq + 2 * ryq);
+}
 
 cudaError_t hot_source(const float *p, long long ld_p, float *dst, int nx, int ny, float amb,
                        float rz, cudaStream_t st)

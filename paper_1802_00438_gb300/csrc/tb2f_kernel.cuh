@@ -70,7 +70,8 @@ struct TB2F {
 };
 
 struct CoefF {
-    // diffusion: cc, cw, ce, cs, cn; Hotspot: sdc, Rx, Ry, Rz, amb, sdc*Ry, -2*Ry
+    // diffusion: cc, cw, ce, cs, cn; Hotspot: sdc, Rx, Ry, Rz, amb, sdc*Ry, -2*Ry; source-map
+    // Hotspot kernels (STOR_SRC): sdc, Rx', Ry', Rz, amb, sdc*Ry', -(2Rx' + 2Ry') (host-made)
     float a0, a1, a2, a3, a4, a5, a6;
 };
 
@@ -269,16 +270,20 @@ __device__ __forceinline__ void stf(const CtxF &c, const CoefF &k, int y, bool f
     } else {
 #pragma unroll
         for (int j = 0; j < V; j++) {
-            const float t2 = __fmaf_rn(-2.0f, d[j], __fadd_rn(de[j], dw[j]));
-            Pn[j] = __fmaf_rn(t2, k.a1, Xq[j]);
             if (SRC) {
-                // the power row already carries amb*Rz: (amb - c)*Rz + p = (p + amb*Rz) - Rz*c
+                // the power row carries amb*Rz: (amb - c)*Rz + p = (p + amb*Rz) - Rz*c; and
+                // (e + w - 2c)*Rx - 2c*Ry = (e + w)*Rx' - (2Rx' + 2Ry')*c with the folded weight
+                // exact (a1 = Rx', a6 = -(2Rx' + 2Ry'))
+                Pn[j] = __fmaf_rn(k.a1, __fadd_rn(de[j], dw[j]), Xq[j]);
+                Pn[j] = __fmaf_rn(k.a6, d[j], Pn[j]);
                 Pn[j] = __fmaf_rn(-k.a3, d[j], Pn[j]);
             } else {
+                const float t2 = __fmaf_rn(-2.0f, d[j], __fadd_rn(de[j], dw[j]));
+                Pn[j] = __fmaf_rn(t2, k.a1, Xq[j]);
                 const float t3 = __fsub_rn(k.a4, d[j]);
                 Pn[j] = __fmaf_rn(t3, k.a3, Pn[j]);
+                Pn[j] = __fmaf_rn(k.a6, d[j], Pn[j]);
             }
-            Pn[j] = __fmaf_rn(k.a6, d[j], Pn[j]);
             Pn[j] = __fmaf_rn(k.a0, Pn[j], d[j]);
         }
     }
@@ -336,15 +341,14 @@ __device__ __forceinline__ void tbf_iter(const CtxF &c, const CoefF &k,
             float pv[V];
             lds_row<V>(pbase - C::ROWB + c.o4, pv);   // power of row R0-1
             if (stor_src(STOR)) {
-                // hot2's contracted order with the ambient term folded into the power row
+                // the source-map form of the Hotspot update (see stf): folded ambient term and
+                // folded centre weight
 #pragma unroll
                 for (int j = 0; j < V; j++) {
-                    const float t2 = __fmaf_rn(-2.0f, m[j], __fadd_rn(e[j], w[j]));
-                    const float n2 = __fmaf_rn(-2.0f, m[j], u[j]);
-                    float q = __fmaf_rn(t2, k.a1, pv[j]);
+                    float q = __fmaf_rn(k.a1, __fadd_rn(e[j], w[j]), pv[j]);
+                    q = __fmaf_rn(k.a2, __fadd_rn(u[j], dd[j]), q);
+                    q = __fmaf_rn(k.a6, m[j], q);
                     q = __fmaf_rn(-k.a3, m[j], q);
-                    q = __fmaf_rn(n2, k.a2, q);
-                    q = __fmaf_rn(dd[j], k.a2, q);
                     out[j] = __fmaf_rn(k.a0, q, m[j]);
                 }
             } else {
@@ -610,7 +614,7 @@ __device__ __forceinline__ void tbf_range(const Pass2D &p, long long f, const lo
     CoefF k;
     k.a0 = p.kf[0]; k.a1 = p.kf[1]; k.a2 = p.kf[2]; k.a3 = p.kf[3]; k.a4 = p.kf[4];
     k.a5 = p.kf[5];   // Hotspot: sdc * Ry
-    k.a6 = p.kf[6];   // Hotspot: -2 Ry
+    k.a6 = p.kf[6];   // Hotspot: -2 Ry (source-map kernels: -(2Rx' + 2Ry'))
     c.src_add = __fmul_rn(k.a4, k.a3);   // Hotspot: amb * Rz
 
     while (f < fend) {
