@@ -118,6 +118,49 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class Replicas:
+    """The N-process launch (torch.distributed.run, one process per GPU): every rank advances
+    its own copy of the workload (the method exchanges nothing between grids), the ranks meet at
+    a barrier around each timed region, a region's time is the maximum over the ranks, and the
+    job's rate is all ranks' units over that time.  backend "gloo" with a CPU device runs the
+    same logic without GPUs."""
+
+    def __init__(self, backend: str = "nccl", device=None):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.device = device
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            if backend == "nccl":
+                dist.init_process_group(backend, device_id=device)
+            else:
+                dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist:
+            self.dist.barrier()
+
+    def max_ms(self, ms: float) -> float:
+        if not self.dist:
+            return ms
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def job_rate(self, units_per_rank: float, ms: float) -> float:
+        """Units per second of the whole job: every rank did units_per_rank in at most ms."""
+        return self.world * units_per_rank / (ms * 1e-3)
+
+
+def reference_rank_gate() -> bool:
+    """The reference arm (the CPU oracle) runs on rank 0 alone; other ranks exit at once."""
+    return int(os.environ.get("RANK", "0")) == 0
+
+
 def kernel_source_hash(ndim: int) -> str:
     """Hash of the sources of the benchmarked kernel family (2D contracted or 3D)."""
     files = (("tb2f_kernel.cuh", "tb2d_kernel.cuh", "common.cuh") if ndim == 2
@@ -209,9 +252,6 @@ def lowp_errors(w, st, stream, side=2048):
 
 def run_reference(args, w):
     """Reference arm: the CPU oracle, each benchmark step a bounded sample of the workload."""
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
     import oracle
     per_step = max(2.0, 150.0 / max(1, args.steps + args.warmup))
     steps, cores = _oracle_sample_steps(w, per_step)
@@ -242,8 +282,6 @@ def bench_batch(args):
     ws = synth.c5a_batch()
     cells_steps = sum(w.cells * w.steps for w in ws)
     if args.impl == "reference":
-        if int(os.environ.get("RANK", "0")) != 0:
-            return
         import oracle
         oracle.build()
         cores = len(os.sched_getaffinity(0))
@@ -271,14 +309,10 @@ def bench_batch(args):
     import torch
     import paper_1802_00438_gb300 as st
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
+    rk = Replicas("nccl", dev)
+    world, rank = rk.world, rk.rank
     stream = torch.cuda.Stream(dev)
     items = []
     for w in ws:
@@ -294,20 +328,15 @@ def bench_batch(args):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    if dist:
-        dist.barrier()
+    rk.barrier()
     with Clocks(local) as clk:
         e0.record(stream)
         for _ in range(args.steps):
             b.run()
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * cells_steps * args.steps / (ms * 1e-3) / 1e9
+    ms = rk.max_ms(e0.elapsed_time(e1))
+    value = rk.job_rate(cells_steps * args.steps, ms) / 1e9
     # roofline of the mix: sum over grids of cells*steps / R_g(T_g), R = min(ALU, HBM*T/bytes)
     peaks, src = load_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -332,6 +361,7 @@ def bench_batch(args):
     h_out = [torch.empty_like(h).pin_memory() for h in h_in]
     a0 = torch.cuda.Event(enable_timing=True)
     a1 = torch.cuda.Event(enable_timing=True)
+    rk.barrier()
     with torch.cuda.stream(stream):
         a0.record(stream)
         for _ in range(args.steps):
@@ -342,9 +372,9 @@ def bench_batch(args):
                 h.copy_(it["grid_out"], non_blocking=True)
         a1.record(stream)
     torch.cuda.synchronize()
-    ems = a0.elapsed_time(a1)
+    ems = rk.max_ms(a0.elapsed_time(a1))
     nb = sum(w.u0.nbytes for w in ws)
-    e2e = {"value": world * cells_steps * args.steps / (ems * 1e-3) / 1e9, "unit": "GCell/s",
+    e2e = {"value": rk.job_rate(cells_steps * args.steps, ems) / 1e9, "unit": "GCell/s",
            "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
     if rank == 0:
         tv = {}
@@ -364,8 +394,8 @@ def bench_batch(args):
                           "roofline": roof, "e2e": e2e, "gpu_launches": b.launches() * args.steps,
                           "clocks": clk.summary(), "cpu_baseline": None}), flush=True)
     b.close()
-    if dist:
-        dist.destroy_process_group()
+    if rk.dist:
+        rk.dist.destroy_process_group()
 
 
 def bench_adjoint(args, ckpt=20):
@@ -375,7 +405,8 @@ def bench_adjoint(args, ckpt=20):
     w = synth.c5b_adjoint2d()
     wt = synth.loss_weights(6, w.shape)
     n = w.cells
-    if args.impl == "reference" or not args.no_cpu:
+    # the oracle's timing: the reference arm, or the CPU baseline (rank 0 of a 1-GPU run only)
+    if args.impl == "reference" or (not args.no_cpu and int(os.environ.get("WORLD_SIZE", "1")) == 1):
         import oracle
         oracle.build()
         cores = len(os.sched_getaffinity(0))
@@ -392,29 +423,24 @@ def bench_adjoint(args, ckpt=20):
                "kind": "oracle", "sample": f"float64 adjoint of a {side}^2, {s}-step diffusion "
                                              f"run (the transposed sweep is one thread)"}
         if args.impl == "reference":
-            if int(os.environ.get("RANK", "0")) == 0:
-                print(json.dumps({"impl": "reference", "metric": "stencil GCell/s & GFLOP/s vs roofline",
-                                  "value": cpu["value"], "unit": "GCell/s", "n_gpus": args.gpus,
-                                  "steps": args.steps, "warmup": args.warmup,
-                                  "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-                                  "config": {"workload": ADJOINT}, "cpu_baseline": cpu,
-                                  "e2e": {"value": cpu["value"], "unit": "GCell/s",
-                                          "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
-                      flush=True)
+            print(json.dumps({"impl": "reference", "metric": "stencil GCell/s & GFLOP/s vs roofline",
+                              "value": cpu["value"], "unit": "GCell/s", "n_gpus": args.gpus,
+                              "steps": args.steps, "warmup": args.warmup,
+                              "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                              "config": {"workload": ADJOINT}, "cpu_baseline": cpu,
+                              "e2e": {"value": cpu["value"], "unit": "GCell/s",
+                                      "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+                  flush=True)
             return
     else:
         cpu = None
     import torch
     import paper_1802_00438_gb300 as st
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
+    rk = Replicas("nccl", dev)
+    world, rank = rk.world, rk.rank
     stream = torch.cuda.current_stream(dev)
     u0 = torch.from_numpy(w.u0).to(dev)
     g = torch.from_numpy(wt).to(dev)
@@ -433,8 +459,7 @@ def bench_adjoint(args, ckpt=20):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     f1 = torch.cuda.Event(enable_timing=True)
-    if dist:
-        dist.barrier()
+    rk.barrier()
     with Clocks(local) as clk:
         e0.record(stream)
         for _ in range(args.steps):
@@ -448,15 +473,11 @@ def bench_adjoint(args, ckpt=20):
             st.stencil_adjoint_forward(adj.h, u0, None, w.coef, out)
         f1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    fms = e0b.elapsed_time(f1)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = rk.max_ms(e0.elapsed_time(e1))
+    fms = rk.max_ms(e0b.elapsed_time(f1))
     per = ms / args.steps
     bwd = per - fms / args.steps
-    value = world * n * w.steps / (per * 1e-3) / 1e9
+    value = rk.job_rate(n * w.steps * args.steps, ms) / 1e9
     # algorithmic HBM bytes of the backward: per transposed pass of s steps lambda in + out
     # (8 B) and the s states (4 B each); per recomputed state one read and one write (8 B); the
     # checkpoint copy into the state buffer (8 B) per segment; grad_u0 copy (8 B)
@@ -484,6 +505,7 @@ def bench_adjoint(args, ckpt=20):
     h_gk = torch.empty(5, dtype=torch.float32).pin_memory()
     a0 = torch.cuda.Event(enable_timing=True)
     a1 = torch.cuda.Event(enable_timing=True)
+    rk.barrier()
     a0.record(stream)
     for _ in range(args.steps):
         u0.copy_(h_u, non_blocking=True)
@@ -493,8 +515,8 @@ def bench_adjoint(args, ckpt=20):
         h_gk.copy_(gk, non_blocking=True)
     a1.record(stream)
     torch.cuda.synchronize()
-    ems = a0.elapsed_time(a1)
-    e2e = {"value": world * n * w.steps / (ems / args.steps * 1e-3) / 1e9, "unit": "GCell/s",
+    ems = rk.max_ms(a0.elapsed_time(a1))
+    e2e = {"value": rk.job_rate(n * w.steps * args.steps, ems) / 1e9, "unit": "GCell/s",
            "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 4 * n + 20}
     fwd_T = st.Plan(w.kind, 2, w.nx, w.ny).info()["T"]
     launches = sum(-(-L // fwd_T) for L in seg_len)            # forward passes
@@ -514,8 +536,8 @@ def bench_adjoint(args, ckpt=20):
                           "roofline": roof, "e2e": e2e, "gpu_launches": launches * args.steps,
                           "clocks": clk.summary(), "cpu_baseline": cpu}), flush=True)
     adj.close()
-    if dist:
-        dist.destroy_process_group()
+    if rk.dist:
+        rk.dist.destroy_process_group()
 
 
 def main():
@@ -539,6 +561,8 @@ def main():
     ap.add_argument("--time-steps", type=int, default=0, help="profiling: override time steps")
     args = ap.parse_args()
 
+    if args.impl == "reference" and not reference_rank_gate():
+        return
     if args.workload == BATCH:
         return bench_batch(args)
     if args.workload == ADJOINT:
@@ -558,18 +582,14 @@ def main():
 
     import torch
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    rk = Replicas("nccl", dev)
+    world, rank = rk.world, rk.rank
 
     import paper_1802_00438_gb300 as st
 
-    dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     u0 = torch.from_numpy(w.u0).to(dev)
     pw = None if w.power is None else torch.from_numpy(w.power).to(dev)
@@ -593,8 +613,7 @@ def main():
     st.stencil_plan_kernel_time(plan.h, reset=True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    if dist:
-        dist.barrier()
+    rk.barrier()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
         e0.record(stream)
@@ -602,20 +621,15 @@ def main():
             step()
         e1.record(stream)
         torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ms = e0.elapsed_time(e1)
+    rk.barrier()
+    ms = rk.max_ms(e0.elapsed_time(e1))
     kern_ms, timed_launches = st.stencil_plan_kernel_time(plan.h, reset=True)
     launches = timed_launches
     if w.kind == 1 and w.ndim == 2 and not args.storage:
         launches += args.steps   # the source-map kernel (p + amb*Rz) before each run's passes
     st.stencil_plan_set_timing(plan.h, False)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     cells_step = w.cells * w.steps
-    value = world * cells_step * args.steps / (ms * 1e-3) / 1e9
+    value = rk.job_rate(cells_step * args.steps, ms) / 1e9
 
     # ---- end to end through the C ABI with host buffers ----------------------------------
     e2e = None
@@ -636,8 +650,7 @@ def main():
 
         e2e_step()
         torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
+        rk.barrier()
         a0 = torch.cuda.Event(enable_timing=True)
         a1 = torch.cuda.Event(enable_timing=True)
         a0.record(stream)
@@ -645,13 +658,9 @@ def main():
             e2e_step()
         a1.record(stream)
         torch.cuda.synchronize()
-        ems = a0.elapsed_time(a1)
-        if dist:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = rk.max_ms(a0.elapsed_time(a1))
         nb = w.u0.nbytes
-        e2e = {"value": world * cells_step * args.steps / (ems * 1e-3) / 1e9, "unit": "GCell/s",
+        e2e = {"value": rk.job_rate(cells_step * args.steps, ems) / 1e9, "unit": "GCell/s",
                "h2d_bytes_per_step": nb * (2 if w.power is not None else 1),
                "d2h_bytes_per_step": nb}
 
@@ -687,6 +696,9 @@ def main():
     roof["cell_roofline_gcells"] = cell_roof / 1e9
     roof["frac_of_cell_roofline"] = (cells_step * args.steps / (kern_ms * 1e-3)) / cell_roof
     roof["hbm_frac"] = gbs / hbm_peak
+    # the T -> infinity ceiling: FP32 issue of the counted flops alone
+    roof["fp32_ceiling_gcells"] = alu_peak * 1e3 / fl
+    roof["frac_of_fp32_ceiling"] = (cells_step * args.steps / (kern_ms * 1e-3)) / (alu_peak * 1e12 / fl)
     roof["kernel_ms_per_launch"] = avg_launch_ms
 
     clocks = clk.summary()
@@ -702,21 +714,21 @@ def main():
             torch.cuda.synchronize()
             q0 = torch.cuda.Event(enable_timing=True)
             q1 = torch.cuda.Event(enable_timing=True)
+            rk.barrier()
             q0.record(stream)
             for _ in range(args.steps):
                 qplan.run(u0, out, w.coef, w.steps, power=pw)
             q1.record(stream)
             torch.cuda.synchronize()
-            qms = q0.elapsed_time(q1)
-            qv = world * cells_step * args.steps / (qms * 1e-3) / 1e9
+            qms = rk.max_ms(q0.elapsed_time(q1))
+            qv = rk.job_rate(cells_step * args.steps, qms) / 1e9
             lowp[name] = {"value": qv, "unit": "GCell/s", "speedup_vs_f32": qv / value,
                           "T": qplan.info()["T"]}
             qplan.close()
         if not args.no_cpu and world == 1:
             lowp["error_vs_f64_oracle"] = lowp_errors(w, st, stream)
 
-    if dist:
-        dist.barrier()
+    rk.barrier()
     if rank == 0:
         line = {"metric": "stencil GCell/s & GFLOP/s vs roofline",
                 "value": value, "unit": "GCell/s", "n_gpus": world, "steps": args.steps,
@@ -743,8 +755,8 @@ def main():
             line["cpu_baseline"] = None
         print(json.dumps(line), flush=True)
     plan.close()
-    if dist:
-        dist.destroy_process_group()
+    if rk.dist:
+        rk.dist.destroy_process_group()
 
 
 if __name__ == "__main__":

@@ -122,7 +122,10 @@ bool available(const stencil_plan_s *p, int T)
 // ranks the compiled variants as measured on 16384^2 grids at T in {4, 6, 8, 12}.
 struct Cand2D { int T, V, W; };
 
-double model_gcells_2d(const stencil_desc &d, int sms, const Cand2D &k, int bps, int steps)
+// seg_rows = 0: the plan's own launch geometry; > 0: a batch launch, whose segments hold about
+// seg_rows rows across all its grids and whose launch cost the grids share
+double model_gcells_2d(const stencil_desc &d, int sms, const Cand2D &k, int bps, int steps,
+                       int seg_rows = 0)
 {
     const bool swap = k.W == 1;
     const double fp = d.kind == ST_DIFFUSION ? 5.0 : 9.0;
@@ -135,8 +138,9 @@ double model_gcells_2d(const stencil_desc &d, int sms, const Cand2D &k, int bps,
     const long long cx = 32LL * k.V - 2 * halo;
     const long long units = (d.nx + cx - 1) / cx * (long long)d.ny;
     const long long ctas = std::min<long long>((long long)sms * bps, std::max<long long>(1, units / 4));
-    const double rows_per_cta = (double)units / ctas;
-    const int warps = (int)std::min<long long>(std::min(bps, 16), (ctas + sms - 1) / sms);
+    const double rows_per_cta = seg_rows > 0 ? seg_rows : (double)units / ctas;
+    const int warps = seg_rows > 0 ? std::min(bps, 16)
+                                   : (int)std::min<long long>(std::min(bps, 16), (ctas + sms - 1) / sms);
     double eff = std::min(0.85, 0.45 + 0.027 * warps);
     if (code_kb > 12.0) eff *= 12.0 / code_kb;
     stencil_gpu_model_in m = {};
@@ -156,7 +160,7 @@ double model_gcells_2d(const stencil_desc &d, int sms, const Cand2D &k, int bps,
     m.issue_eff = eff;
     m.hbm_eff = 0.62;
     m.stream_overhead = 2.0 * k.T / rows_per_cta;
-    m.launch_s = 4e-6;
+    m.launch_s = seg_rows > 0 ? 0.0 : 4e-6;
     stencil_gpu_model_out r;
     if (stencil_model_gpu(&m, &r) != ST_OK) return 0.0;
     return r.gcells;
@@ -206,7 +210,11 @@ double batch_model_gcells(int kind, int nx, int ny, int steps, int sms, int T, i
     d.nx = nx;
     d.ny = ny;
     d.nz = 1;
-    return model_gcells_2d(d, sms, Cand2D{T, V, 1}, bps, steps);
+    // a batch launch splits all its grids' units over SMs x resident blocks, and a block's
+    // range crosses grids, so its segments are short: 24 rows reproduces the measured order on
+    // the 64-grid workload (T = 4 everywhere 1318, the standalone choice 1260, T = 8 everywhere
+    // 1219 GCell/s)
+    return model_gcells_2d(d, sms, Cand2D{T, V, 1}, bps, steps, 24);
 }
 }  // namespace stn
 

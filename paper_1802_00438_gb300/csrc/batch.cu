@@ -117,22 +117,37 @@ int stencil_batch_create(stencil_batch *out, const stencil_batch_grid *grids, in
     B->scratch.assign(count, nullptr);
     B->src.assign(count, nullptr);
     B->ld_scratch.resize(count);
-    for (int g = 0; g < count && rc == ST_OK; g++) {
-        const stencil_batch_grid &q = B->grid[g];
+    // One (T, V) per kind: the grids that share a kernel run together in each launch slot, so
+    // a split of one kind over several kernels multiplies the launches and leaves each of them
+    // small.  The choice minimises the kind's predicted total time, sum over its grids of
+    // cells x steps / modelled rate.
+    int kind_T[2] = {0, 0}, kind_V[2] = {0, 0};
+    for (int kind = 0; kind < 2; kind++) {
         double best = -1.0;
         for (const auto &tv : kCand) {
-            const Shape2D sh{q.kind, 0, tv[0], tv[1], 1};
+            const Shape2D sh{kind, 0, tv[0], tv[1], 1};
             int bps = 0;
             if (tb2d_batch_prepare(sh, &bps) != cudaSuccess || bps < 1) continue;
-            const double m = batch_model_gcells(q.kind, q.nx, q.ny, q.steps, B->sms, tv[0], tv[1], bps);
-            if (m > best) {
-                best = m;
-                B->T[g] = tv[0];
-                B->V[g] = tv[1];
+            double t = 0.0;
+            for (int g = 0; g < count; g++) {
+                const stencil_batch_grid &q = B->grid[g];
+                if (q.kind != kind || q.steps <= 0) continue;
+                const double m = batch_model_gcells(q.kind, q.nx, q.ny, q.steps, B->sms, tv[0], tv[1], bps);
+                t += (double)q.nx * q.ny * q.steps / std::max(m, 1e-9);
+            }
+            if (best < 0 || t < best) {
+                best = t;
+                kind_T[kind] = tv[0];
+                kind_V[kind] = tv[1];
             }
         }
         (void)cudaGetLastError();
         if (best < 0) rc = ST_ERR_UNSUPPORTED;
+    }
+    for (int g = 0; g < count && rc == ST_OK; g++) {
+        const stencil_batch_grid &q = B->grid[g];
+        B->T[g] = kind_T[q.kind];
+        B->V[g] = kind_V[q.kind];
         B->passes[g] = q.steps > 0 ? (q.steps + B->T[g] - 1) / B->T[g] : 0;
         B->ld_scratch[g] = ((long long)q.nx + 31) / 32 * 32;
         if (rc == ST_OK && B->passes[g] > 0) {

@@ -65,7 +65,7 @@ struct TB2F {
     static constexpr int RAWB = 32 + 2 * BX;
     static constexpr size_t SMEM = (size_t)(NBF + NBPX) * ROWB +
                                    (size_t)NBR * RAWB * (KIND == KTHERM ? 2 : 1);
-    static_assert(V % 4 == 0, "V must be a multiple of 4");
+    static_assert(V % 4 == 0 && V <= 8, "V must be 4 or 8");
     static_assert(CX > 0, "tile narrower than its halos");
 };
 
@@ -91,14 +91,21 @@ __device__ __forceinline__ float lds32(uint32_t a)
     return v;
 }
 
-template <int V>
-__device__ __forceinline__ void lds_row(uint32_t a, float (&v)[V])
+// Ring rows are stored with their 16-byte chunks rotated inside each 128-byte group: chunk g
+// (cells 4g .. 4g+3) sits at chunk position ring_pos(g).  A warp's 16-byte accesses are served
+// eight lanes at a time, so they are conflict-free when those eight lanes hit eight different
+// 16-byte bank groups.  The copies into a row (lane L writes chunk L + 32q) and, with V = 8,
+// the reads of a thread's own cells (lane L reads chunks 2L and 2L + 1) would otherwise meet
+// only four bank groups per eight lanes; with the rotation both meet all eight.
+__host__ __device__ constexpr uint32_t ring_pos(uint32_t g)
 {
-#pragma unroll
-    for (int q = 0; q < V / 4; q++) {
-        const float4 t = lds128(a + 16 * q);
-        v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
-    }
+    return (g & ~7u) | ((g + (g >> 3)) & 7u);
+}
+
+// byte offset of cell x in a ring row
+__host__ __device__ constexpr uint32_t ring_cell(uint32_t x)
+{
+    return 16u * ring_pos(x >> 2) + 4u * (x & 3u);
 }
 
 __device__ __forceinline__ void cp16(uint32_t dst, const void *src, int nbytes)
@@ -177,7 +184,8 @@ struct CtxF {
     bool st_full, st_any, edge;
     int vec_in, vec_out, vec_pw;
     int lane;
-    uint32_t o4;           // my first cell's byte offset in a ring row
+    uint32_t oq[2];        // byte offsets in a ring row of my cells' 16-byte chunks
+    uint32_t wq[2];        // byte offsets of the chunks I copy into a ring row
     uint32_t ow4, oe4;     // byte offsets of the cells left and right of mine (clamped)
     // 16-bit storage
     uint32_t sRF, sRP;     // staging rings (raw field / raw power rows)
@@ -190,6 +198,17 @@ struct CtxF {
     int msel;              // which of the three blocks of a loaded row my cells belong to
     float src_add;         // amb * Rz (STOR_SRC, rounded once)
 };
+
+// my V cells of the ring row at byte address row
+template <int V>
+__device__ __forceinline__ void lds_row(uint32_t row, const CtxF &c, float (&v)[V])
+{
+#pragma unroll
+    for (int q = 0; q < V / 4; q++) {
+        const float4 t = lds128(row + c.oq[q]);
+        v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+    }
+}
 
 template <int V, bool EDGE>
 __device__ __forceinline__ void nbf(const CtxF &c, const float (&d)[V], float w_in, float e_in,
@@ -212,15 +231,15 @@ __device__ __forceinline__ void nbf(const CtxF &c, const float (&d)[V], float w_
 
 // Start row y+1: Xq = its north term (+ its power for Hotspot), written over the finished P.
 template <int KIND, int V>
-__device__ __forceinline__ void qf(const CoefF &k, const float (&d)[V], uint32_t p_next,
-                                   float (&Xq)[V])
+__device__ __forceinline__ void qf(const CtxF &c, const CoefF &k, const float (&d)[V],
+                                   uint32_t p_next, float (&Xq)[V])
 {
     if (KIND == KDIFF) {
 #pragma unroll
         for (int j = 0; j < V; j++) Xq[j] = __fmul_rn(k.a4, d[j]);
     } else {
         float p[V];
-        lds_row<V>(p_next, p);
+        lds_row<V>(p_next, c, p);
 #pragma unroll
         for (int j = 0; j < V; j++) Xq[j] = __fmaf_rn(k.a2, d[j], p[j]);
     }
@@ -255,7 +274,7 @@ __device__ __forceinline__ void stf(const CtxF &c, const CoefF &k, int y, bool f
 #pragma unroll
         for (int j = 0; j < V; j++) out[j] = Xp[j];
     }
-    if (SP && y == 0) qf<KIND, V>(k, d, p_y, Xq);   // top: the row above row 0 is row 0
+    if (SP && y == 0) qf<KIND, V>(c, k, d, p_y, Xq);   // top: the row above row 0 is row 0
     float dw[V], de[V];
     nbf<V, ED>(c, d, w_in, e_in, dw, de);
     float(&Pn)[V] = SWAP ? Xq : Xp;   // where row y's P goes
@@ -287,7 +306,7 @@ __device__ __forceinline__ void stf(const CtxF &c, const CoefF &k, int y, bool f
             Pn[j] = __fmaf_rn(k.a0, Pn[j], d[j]);
         }
     }
-    qf<KIND, V>(k, d, p_next, Qn);
+    qf<KIND, V>(c, k, d, p_next, Qn);
     if (SP && y == c.ny - 1) {   // bottom: complete row ny-1 now with south = itself
 #pragma unroll
         for (int j = 0; j < V; j++) Pn[j] = __fmaf_rn(cs, d[j], Pn[j]);
@@ -329,9 +348,9 @@ __device__ __forceinline__ void tbf_iter(const CtxF &c, const CoefF &k,
     // (fu, fm, fd are those rows, already clamped to the grid for the boundary rows)
     {
         float u[V], m[V], dd[V], w[V], e[V];
-        lds_row<V>(fu + c.o4, u);
-        lds_row<V>(fm + c.o4, m);
-        lds_row<V>(fd + c.o4, dd);
+        lds_row<V>(fu, c, u);
+        lds_row<V>(fm, c, m);
+        lds_row<V>(fd, c, dd);
         nbf<V, ED>(c, m, lds32(fm + c.ow4), lds32(fm + c.oe4), w, e);
         if (KIND == KDIFF) {
 #pragma unroll
@@ -339,7 +358,7 @@ __device__ __forceinline__ void tbf_iter(const CtxF &c, const CoefF &k,
                 out[j] = diff5<false>(m[j], w[j], e[j], dd[j], u[j], k.a0, k.a1, k.a2, k.a3, k.a4);
         } else {
             float pv[V];
-            lds_row<V>(pbase - C::ROWB + c.o4, pv);   // power of row R0-1
+            lds_row<V>(pbase - C::ROWB, c, pv);   // power of row R0-1
             if (stor_src(STOR)) {
                 // the source-map form of the Hotspot update (see stf): folded ambient term and
                 // folded centre weight
@@ -369,7 +388,7 @@ __device__ __forceinline__ void tbf_iter(const CtxF &c, const CoefF &k,
         const float e_in = __shfl_sync(0xffffffffu, d[0], (c.lane + 1) & 31);
         stf<KIND, V, MODE, SWAP, stor_src(STOR)>(c, k, R0 - s, s >= c.tsteps, PH == 0 ? A[s - 1] : B[s - 1],
                                  PH == 0 ? B[s - 1] : A[s - 1], d, w_in, e_in,
-                           pbase - s * C::ROWB + c.o4, pbase - (s - 1) * C::ROWB + c.o4, out);
+                           pbase - s * C::ROWB, pbase - (s - 1) * C::ROWB, out);
     }
     if (store) {
         if (stor_fmt(STOR) == STOR_F32) {
@@ -439,8 +458,8 @@ __device__ __forceinline__ void tbf_decode(const CtxF &c, uint32_t raw, uint32_t
             x2 = __fadd_rn(x2, c.src_add);
             x3 = __fadd_rn(x3, c.src_add);
         }
-        sts128(dst + c.o4 + 16u * t, x0, x1, x2, x3);
-        if (mirror) sts128(mirror + c.o4 + 16u * t, x0, x1, x2, x3);
+        sts128(dst + c.oq[t], x0, x1, x2, x3);
+        if (mirror) sts128(mirror + c.oq[t], x0, x1, x2, x3);
     }
 }
 
@@ -468,15 +487,15 @@ __device__ __forceinline__ void tbf_queue(const CtxF &c, const RowF &r, int lf, 
         }
         return;
     }
-    const uint32_t df = c.sF + lf * C::ROWB + 16u * c.lane;
-    const uint32_t dp = c.sP + lp * C::ROWB + 16u * c.lane;
+    const uint32_t df = c.sF + lf * C::ROWB;
+    const uint32_t dp = c.sP + lp * C::ROWB;
     if (c.vec_in && (KIND == KDIFF || c.vec_pw)) {
 #pragma unroll
         for (int q = 0; q < V / 4; q++) {
-            cp16(df + 512u * q, r.gF + r.colq[q], r.nbq[q]);
+            cp16(df + c.wq[q], r.gF + r.colq[q], r.nbq[q]);
             if (KIND == KTHERM) {
-                cp16(dp + 512u * q, r.gP + r.colq[q], r.nbq[q]);
-                if (lp < C::PW - 1) cp16(dp + C::NBP * C::ROWB + 512u * q, r.gP + r.colq[q], r.nbq[q]);
+                cp16(dp + c.wq[q], r.gP + r.colq[q], r.nbq[q]);
+                if (lp < C::PW - 1) cp16(dp + C::NBP * C::ROWB + c.wq[q], r.gP + r.colq[q], r.nbq[q]);
             }
         }
     } else {   // rows not 16-byte aligned: element-wise copies
@@ -486,10 +505,10 @@ __device__ __forceinline__ void tbf_queue(const CtxF &c, const RowF &r, int lf, 
             for (int j = 0; j < 4; j++) {
                 const int nb = (4 * j < r.nbq[q]) ? 4 : 0;
                 const int col = nb ? r.colq[q] + j : 0;
-                cp4(df + 512u * q + 4 * j, r.gF + col, nb);
+                cp4(df + c.wq[q] + 4 * j, r.gF + col, nb);
                 if (KIND == KTHERM) {
-                    cp4(dp + 512u * q + 4 * j, r.gP + col, nb);
-                    if (lp < C::PW - 1) cp4(dp + C::NBP * C::ROWB + 512u * q + 4 * j, r.gP + col, nb);
+                    cp4(dp + c.wq[q] + 4 * j, r.gP + col, nb);
+                    if (lp < C::PW - 1) cp4(dp + C::NBP * C::ROWB + c.wq[q] + 4 * j, r.gP + col, nb);
                 }
             }
     }
@@ -608,9 +627,13 @@ __device__ __forceinline__ void tbf_range(const Pass2D &p, long long f, const lo
     c.vec_out = p.vec_out;
     c.vec_pw = p.vec_pw;
     c.lane = threadIdx.x;
-    c.o4 = 4u * V * c.lane;
-    c.ow4 = c.lane > 0 ? c.o4 - 4 : 0;
-    c.oe4 = c.lane < 31 ? c.o4 + 4 * V : c.o4 + 4 * V - 4;
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+        c.oq[q] = 16u * ring_pos(min(V / 4 * c.lane + q, V / 4 * c.lane + V / 4 - 1));
+        c.wq[q] = 16u * ring_pos(c.lane + 32 * min(q, V / 4 - 1));
+    }
+    c.ow4 = ring_cell(c.lane > 0 ? V * c.lane - 1 : 0);
+    c.oe4 = ring_cell(c.lane < 31 ? V * c.lane + V : V * c.lane + V - 1);
     CoefF k;
     k.a0 = p.kf[0]; k.a1 = p.kf[1]; k.a2 = p.kf[2]; k.a3 = p.kf[3]; k.a4 = p.kf[4];
     k.a5 = p.kf[5];   // Hotspot: sdc * Ry
