@@ -559,6 +559,9 @@ def main():
     ap.add_argument("--ny", type=int, default=0)
     ap.add_argument("--nz", type=int, default=0)
     ap.add_argument("--time-steps", type=int, default=0, help="profiling: override time steps")
+    ap.add_argument("--tune", type=int, default=0,
+                    help="before timing, run the model's top-K configurations on the workload and "
+                         "use the fastest (stencil_tune); 0 = the model's own choice")
     args = ap.parse_args()
 
     if args.impl == "reference" and not reference_rank_gate():
@@ -594,6 +597,11 @@ def main():
     u0 = torch.from_numpy(w.u0).to(dev)
     pw = None if w.power is None else torch.from_numpy(w.power).to(dev)
     out = torch.empty_like(u0)
+    tuned = None
+    if args.tune > 0:
+        tuned = st.stencil_tune(w.kind, w.ndim, w.nx, w.ny, w.nz, u0, out, w.coef, w.steps, pw,
+                                top_k=args.tune, storage=args.storage, stream=stream.cuda_stream,
+                                rad=w.rad if w.rad > 1 else 0)
     plan = st.Plan(w.kind, w.ndim, w.nx, w.ny, w.nz, force_T=args.T, force_bx=args.bx,
                    force_vec=args.vec, force_by=args.by, storage=args.storage,
                    stream=stream.cuda_stream, rad=w.rad if w.rad > 1 else 0)
@@ -746,7 +754,8 @@ def main():
                            "model_accuracy": (value / world / info["model_gcells"]
                                               if info["model_gcells"] else None),
                            "l2": "inputs larger than L2 (%.0f MiB per grid)" % (w.u0.nbytes / 2**20),
-                           "parallelism": f"replicas{world}" if world > 1 else "single"},
+                           "parallelism": f"replicas{world}" if world > 1 else "single",
+                           "tuned": tuned},
                 "roofline": roof, "e2e": e2e, "lowp": lowp,
                 "gpu_launches": launches, "clocks": clocks}
         if not args.no_cpu and world == 1:

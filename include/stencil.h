@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define ST_ABI_VERSION 2
+#define ST_ABI_VERSION 3
 
 /* status codes */
 #define ST_OK                    0
@@ -140,6 +140,47 @@ int stencil_plan_kernel_time(stencil_plan plan, double *ms, long long *launches,
 
 /* Free the plan and its scratch.  NULL is accepted. */
 int stencil_plan_destroy(stencil_plan plan);
+
+/* ---- measured parameter choice (Sec. 5.3 and 5.4.2) --------------------------------------
+ * The plan's own choice comes from the model alone (Eqs. 3-9 restated for this GPU).  The
+ * paper narrows the configurations with its model and then builds and measures the few it
+ * rates best; stencil_tune does the same on the caller's data and remembers the winner for the
+ * problem key (kind, ndim, nx, ny, nz, storage, exact, rad) in a process-wide cache, which
+ * stencil_plan_create consults whenever its desc forces nothing. */
+typedef struct {
+    int force_T, force_bx, force_by, force_vec;   /* the fastest configuration, as desc forces */
+    double gcells;        /* its measured rate, 10^9 cell updates/s */
+    double model_gcells;  /* the model's rate for it (0 where the family has no calibration) */
+    int candidates;       /* configurations this build provides for the problem */
+    int timed;            /* how many of them were run and timed */
+} stencil_tune_result;
+
+/* Rank every configuration the build provides for *desc by the model, run the top_k of them
+ * (top_k = 0: all) once untimed and once timed (CUDA events on desc->stream) on the caller's
+ * grids, and cache the fastest.
+ * desc     : as for stencil_plan_create, with every force_* field 0 (else ST_ERR_INVALID_ARG).
+ * grid_in, power, coeffs : as for stencil_run (device, device or NULL, host); not modified.
+ * grid_out : device scratch of the grid's size, distinct from grid_in; its contents afterwards
+ *            are the result of a `steps`-step run of the last configuration timed.
+ * steps    : >= 1 Jacobi steps per timed run (a short but representative count).
+ * result   : receives the winner.  Synchronous: returns after the last timed run.
+ * Errors: ST_ERR_INVALID_ARG, ST_ERR_UNSUPPORTED (no configuration for the problem),
+ * ST_ERR_OOM, ST_ERR_CUDA, ST_ERR_TIMEOUT, and stencil_run's own checks. */
+int stencil_tune(const stencil_desc *desc, const void *grid_in, void *grid_out, const void *power,
+                 const float *coeffs, int steps, int top_k, stencil_tune_result *result);
+
+/* 1 when the plan took its configuration from the tuning cache, 0 otherwise (or for NULL). */
+int stencil_plan_tuned(stencil_plan plan);
+
+/* The cache: clear it; count its entries; write it to a text file (one entry per line:
+ * kind ndim nx ny nz storage exact rad T bx by vec gcells); merge a file written that way into
+ * it (a malformed line rejects the whole file with ST_ERR_INVALID_ARG and changes nothing).
+ * An entry whose configuration this build cannot make is ignored by stencil_plan_create.
+ * Host-only calls; safe to call from several threads. */
+int stencil_tune_cache_clear(void);
+int stencil_tune_cache_size(void);
+int stencil_tune_cache_save(const char *path);
+int stencil_tune_cache_load(const char *path);
 
 /* ---- many grids in one graph launch ----------------------------------------------------- */
 

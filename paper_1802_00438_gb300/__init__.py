@@ -103,6 +103,16 @@ class stencil_batch_grid(ctypes.Structure):
                 ("coeffs", ctypes.c_float * 5)]
 
 
+class stencil_tune_result(ctypes.Structure):
+    _fields_ = [("force_T", ctypes.c_int), ("force_bx", ctypes.c_int), ("force_by", ctypes.c_int),
+                ("force_vec", ctypes.c_int), ("gcells", ctypes.c_double),
+                ("model_gcells", ctypes.c_double), ("candidates", ctypes.c_int),
+                ("timed", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 # C ABI symbols, with their argument types
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -135,6 +145,13 @@ SIGNATURES = {
     "stencil_adjoint_backward": ([_P, _P, _P, _P, _P, _P, _P], _I),
     "stencil_adjoint_sync": ([_P], _I),
     "stencil_adjoint_destroy": ([_P], _I),
+    "stencil_tune": ([ctypes.POINTER(stencil_desc), _P, _P, _P, ctypes.POINTER(ctypes.c_float), _I,
+                      _I, ctypes.POINTER(stencil_tune_result)], _I),
+    "stencil_plan_tuned": ([_P], _I),
+    "stencil_tune_cache_clear": ([], _I),
+    "stencil_tune_cache_size": ([], _I),
+    "stencil_tune_cache_save": ([ctypes.c_char_p], _I),
+    "stencil_tune_cache_load": ([ctypes.c_char_p], _I),
 }
 
 
@@ -187,12 +204,18 @@ def current_stream():
     return torch.cuda.current_stream().cuda_stream
 
 
+def _desc(kind, ndim, nx, ny, nz, storage, force_T, force_bx, force_by, force_vec, exact, strict,
+          stream, rad):
+    return stencil_desc(kind, ndim, nx, ny, nz if ndim == 3 else 1, storage, force_T, force_bx,
+                        force_by, force_vec, 1 if exact else 0, 1 if strict else 0,
+                        current_stream() if stream is None else stream, rad)
+
+
 def stencil_plan_create(kind: int, ndim: int, nx: int, ny: int, nz: int = 1, *, storage=ST_F32,
                         force_T=0, force_bx=0, force_by=0, force_vec=0, exact=False,
                         strict=False, stream=None, rad=0):
-    d = stencil_desc(kind, ndim, nx, ny, nz if ndim == 3 else 1, storage, force_T, force_bx,
-                     force_by, force_vec, 1 if exact else 0, 1 if strict else 0,
-                     current_stream() if stream is None else stream, rad)
+    d = _desc(kind, ndim, nx, ny, nz, storage, force_T, force_bx, force_by, force_vec, exact,
+              strict, stream, rad)
     h = ctypes.c_void_p()
     _check(lib.stencil_plan_create(ctypes.byref(h), ctypes.byref(d)), "stencil_plan_create")
     return h
@@ -211,7 +234,39 @@ def stencil_plan_sync(plan):
 def stencil_plan_get_info(plan) -> dict:
     info = stencil_plan_info()
     _check(lib.stencil_plan_get_info(plan, ctypes.byref(info)), "stencil_plan_get_info")
-    return info.as_dict()
+    d = info.as_dict()
+    d["tuned"] = bool(lib.stencil_plan_tuned(plan))
+    return d
+
+
+def stencil_tune(kind: int, ndim: int, nx: int, ny: int, nz: int, grid_in, grid_out, coeffs,
+                 steps: int, power=None, *, top_k: int = 5, storage=ST_F32, exact=False,
+                 strict=False, stream=None, rad=0) -> dict:
+    """Time the model's top_k configurations on these grids and cache the fastest for the
+    problem (kind, ndim, sizes, storage, exact, rad); later plans of that problem with nothing
+    forced use it.  top_k = 5 follows the paper's fewer-than-six candidates per stencil."""
+    d = _desc(kind, ndim, nx, ny, nz, storage, 0, 0, 0, 0, exact, strict, stream, rad)
+    r = stencil_tune_result()
+    _check(lib.stencil_tune(ctypes.byref(d), _addr(grid_in), _addr(grid_out), _addr(power),
+                            _coef_array(coeffs), int(steps), int(top_k), ctypes.byref(r)),
+           "stencil_tune")
+    return r.as_dict()
+
+
+def stencil_tune_cache_clear():
+    _check(lib.stencil_tune_cache_clear(), "stencil_tune_cache_clear")
+
+
+def stencil_tune_cache_size() -> int:
+    return int(lib.stencil_tune_cache_size())
+
+
+def stencil_tune_cache_save(path: str):
+    _check(lib.stencil_tune_cache_save(os.fsencode(path)), "stencil_tune_cache_save")
+
+
+def stencil_tune_cache_load(path: str):
+    _check(lib.stencil_tune_cache_load(os.fsencode(path)), "stencil_tune_cache_load")
 
 
 def stencil_plan_set_timing(plan, enable: bool):

@@ -54,6 +54,7 @@ struct stencil_plan_s {
     int VY = 8, NW = 8, alg3 = 0, VX3 = 2;
     int *err = nullptr;   // device flag set by a kernel whose bounded wait gave up
     double model = 0.0;   // calibrated model's prediction for this plan (1000 steps), GCell/s
+    int tuned = 0;        // configuration taken from the tuning cache
     float *src = nullptr;   // contracted float32 Hotspot 2D: the source map p + amb*Rz
     int ntx_star = 0, nty_star = 0;   // star diffusion (rad > 1): tiles along x and y
     std::vector<PassCfg3D> cfg3;
@@ -513,7 +514,29 @@ const char *stencil_strerror(int code)
 
 int stencil_plan_destroy(stencil_plan p);
 
+static int plan_create(stencil_plan *out, const stencil_desc *desc);
+
 int stencil_plan_create(stencil_plan *out, const stencil_desc *desc)
+{
+    // nothing forced and a measured choice cached for this problem: take it (an entry this
+    // build cannot make falls back to the model's choice)
+    if (out && desc && !desc->force_T && !desc->force_bx && !desc->force_by && !desc->force_vec) {
+        stencil_desc t = *desc;
+        if (tune_cache_lookup(t, &t.force_T, &t.force_bx, &t.force_by, &t.force_vec)) {
+            const int rc = plan_create(out, &t);
+            if (rc == ST_OK) {
+                (*out)->tuned = 1;
+                return rc;
+            }
+            if (rc != ST_ERR_UNSUPPORTED) return rc;
+        }
+    }
+    return plan_create(out, desc);
+}
+
+int stencil_plan_tuned(stencil_plan p) { return p ? p->tuned : 0; }
+
+static int plan_create(stencil_plan *out, const stencil_desc *desc)
 {
     if (!out) return ST_ERR_INVALID_ARG;
     *out = nullptr;
@@ -830,11 +853,12 @@ int stencil_plan_get_info(stencil_plan p, stencil_plan_info *info)
         PassCfg2D *c = nullptr;
         int rc = prepare2(p, p->T, &c);
         if (rc != ST_OK) return rc;
-        info->bx = 32 * p->V * p->W;
+        const int warps = std::max(p->W, 1);   // W = 0 marks the one-warp in-place variant
+        info->bx = 32 * p->V * warps;
         info->by = 0;
         info->halo = (p->T + 3) / 4 * 4;
         info->vec = p->V;
-        info->warps = p->W;
+        info->warps = warps;
         info->ctas = c->ctas;
         info->kernel_id = 2;
     } else {

@@ -3,6 +3,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "../../include/stencil.h"
+
 namespace stn {
 
 // One pass of the 2D temporally-blocked sweep (tb2d.cu).
@@ -134,5 +136,8 @@ cudaError_t tb3d_launch(const Shape3D &s, const Pass3D &p, const Tma3D &t, cudaS
 // encode the tensor map of a (nx, ny, nz) float32 grid with a (bx, by, 1) box; false if the
 // driver entry point or the encoding is unavailable
 bool tma3d_encode(CUtensorMap *m, const float *base, int nx, int ny, int nz, int bx, int by);
+
+// tuning cache (tune.cu): the measured configuration for the desc's problem key, if any
+bool tune_cache_lookup(const stencil_desc &d, int *T, int *bx, int *by, int *vec);
 
 }  // namespace stn

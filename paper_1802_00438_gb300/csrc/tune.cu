@@ -1,0 +1,258 @@
+// Measured refinement of the model's parameter choice (arXiv 1802.00438, Sec. 5.3 and 5.4.2):
+// the performance model (Eqs. 3-9, restated for this GPU and calibrated in api.cu) ranks every
+// configuration the build provides; only the few it rates best are run and timed on the
+// caller's data, and the fastest is kept.  The choice is cached per problem key (kind, ndim,
+// nx, ny, nz, storage, exact, rad) for the life of the process, and stencil_plan_create with
+// nothing forced takes it from there.  The cache can be written to and read from a text file.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "../../include/stencil.h"
+#include "internal.h"
+
+namespace {
+
+using Key = std::tuple<int, int, int, int, int, int, int, int>;
+
+struct Choice {
+    int T, bx, by, vec;
+    double gcells;
+};
+
+std::mutex g_mu;
+std::map<Key, Choice> g_cache;
+
+Key key_of(const stencil_desc &d)
+{
+    return Key{d.kind, d.ndim, d.nx, d.ny, d.ndim == 2 ? 1 : d.nz, d.storage, d.exact ? 1 : 0,
+               d.rad > 1 ? d.rad : 0};
+}
+
+// Every configuration a plan can be forced to, as (force_T, force_bx, force_by, force_vec);
+// those this build does not compile are refused by stencil_plan_create and skipped.
+std::vector<std::array<int, 4>> candidates(const stencil_desc &d)
+{
+    std::vector<std::array<int, 4>> c;
+    const int Ts[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16};
+    if (d.rad > 1) {
+        for (int T : Ts) c.push_back({T, 0, 0, 0});
+    } else if (d.ndim == 2) {
+        for (int V : {4, 8})
+            for (int T : Ts) {
+                if (d.exact) {
+                    if (V != 4) continue;
+                    for (int bx : {128, 512}) c.push_back({T, bx, 0, 4});
+                } else {
+                    c.push_back({T, 0, 0, V});
+                    if (d.storage == ST_F32) c.push_back({T, 0, 1, V});   // in-place rows
+                }
+            }
+    } else {
+        const int shapes[][3] = {{64, 64, 16}, {64, 64, 8}, {64, 64, 4}, {128, 32, 8}};
+        for (const auto &s : shapes)
+            for (int T : Ts) c.push_back({T, s[0], s[1], s[2]});
+    }
+    return c;
+}
+
+struct Events {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~Events()
+    {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
+int status(cudaError_t e)
+{
+    if (e == cudaSuccess) return ST_OK;
+    return e == cudaErrorMemoryAllocation ? ST_ERR_OOM : ST_ERR_CUDA;
+}
+
+}  // namespace
+
+namespace stn {
+
+bool tune_cache_lookup(const stencil_desc &d, int *T, int *bx, int *by, int *vec)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_cache.find(key_of(d));
+    if (it == g_cache.end()) return false;
+    *T = it->second.T;
+    *bx = it->second.bx;
+    *by = it->second.by;
+    *vec = it->second.vec;
+    return true;
+}
+
+}  // namespace stn
+
+extern "C" {
+
+int stencil_tune(const stencil_desc *desc, const void *grid_in, void *grid_out, const void *power,
+                 const float *coeffs, int steps, int top_k, stencil_tune_result *result)
+{
+    if (!desc || !grid_in || !grid_out || !coeffs || !result || steps < 1 || top_k < 0 ||
+        grid_in == grid_out)   // the timed runs must leave the input as it was
+        return ST_ERR_INVALID_ARG;
+    if (desc->force_T || desc->force_bx || desc->force_by || desc->force_vec)
+        return ST_ERR_INVALID_ARG;   // the tuner chooses these
+    if (desc->ndim != 2 && desc->ndim != 3) return ST_ERR_INVALID_ARG;
+    const stencil_desc base = *desc;
+    const int nz = base.ndim == 2 ? 1 : base.nz;
+
+    // rank the compiled configurations by the model (stable: build order breaks ties, and
+    // families without a calibration keep it)
+    struct Cand {
+        std::array<int, 4> f;
+        double model;
+    };
+    std::vector<Cand> ranked;
+    for (const auto &f : candidates(base)) {
+        stencil_desc d = base;
+        d.force_T = f[0];
+        d.force_bx = f[1];
+        d.force_by = f[2];
+        d.force_vec = f[3];
+        stencil_plan p = nullptr;
+        const int rc = stencil_plan_create(&p, &d);
+        if (rc == ST_ERR_UNSUPPORTED) continue;
+        if (rc != ST_OK) return rc;
+        stencil_plan_info info;
+        const int ri = stencil_plan_get_info(p, &info);
+        stencil_plan_destroy(p);
+        if (ri != ST_OK) return ri;
+        ranked.push_back({f, info.model_gcells});
+    }
+    if (ranked.empty()) return ST_ERR_UNSUPPORTED;
+    std::stable_sort(ranked.begin(), ranked.end(),
+                     [](const Cand &a, const Cand &b) { return a.model > b.model; });
+    const size_t n = top_k > 0 ? std::min<size_t>(top_k, ranked.size()) : ranked.size();
+
+    // time the leaders: one warm-up run, one timed run each, on the desc's stream
+    Events ev;
+    cudaError_t e = cudaEventCreate(&ev.a);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev.b);
+    if (e != cudaSuccess) return status(e);
+    const cudaStream_t st = static_cast<cudaStream_t>(base.stream);
+    const double updates = (double)base.nx * base.ny * nz * steps;
+    int best = -1;
+    double best_ms = 0.0;
+    for (size_t i = 0; i < n; i++) {
+        stencil_desc d = base;
+        d.force_T = ranked[i].f[0];
+        d.force_bx = ranked[i].f[1];
+        d.force_by = ranked[i].f[2];
+        d.force_vec = ranked[i].f[3];
+        stencil_plan p = nullptr;
+        int rc = stencil_plan_create(&p, &d);
+        if (rc != ST_OK) return rc;
+        rc = stencil_run(p, grid_in, grid_out, power, coeffs, base.nx, base.ny, nz, steps);
+        if (rc == ST_OK) rc = status(cudaEventRecord(ev.a, st));
+        if (rc == ST_OK) rc = stencil_run(p, grid_in, grid_out, power, coeffs, base.nx, base.ny, nz, steps);
+        if (rc == ST_OK) rc = status(cudaEventRecord(ev.b, st));
+        if (rc == ST_OK) rc = stencil_plan_sync(p);
+        float ms = 0.f;
+        if (rc == ST_OK) rc = status(cudaEventElapsedTime(&ms, ev.a, ev.b));
+        stencil_plan_destroy(p);
+        if (rc != ST_OK) return rc;
+        if (best < 0 || ms < best_ms) {
+            best = (int)i;
+            best_ms = ms;
+        }
+    }
+    const Cand &w = ranked[best];
+    result->force_T = w.f[0];
+    result->force_bx = w.f[1];
+    result->force_by = w.f[2];
+    result->force_vec = w.f[3];
+    result->gcells = updates / (best_ms * 1e-3) / 1e9;
+    result->model_gcells = w.model;
+    result->candidates = (int)ranked.size();
+    result->timed = (int)n;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_cache[key_of(base)] = Choice{w.f[0], w.f[1], w.f[2], w.f[3], result->gcells};
+    return ST_OK;
+}
+
+int stencil_tune_cache_clear(void)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_cache.clear();
+    return ST_OK;
+}
+
+int stencil_tune_cache_size(void)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    return (int)g_cache.size();
+}
+
+// One line per entry: kind ndim nx ny nz storage exact rad T bx by vec gcells
+int stencil_tune_cache_save(const char *path)
+{
+    if (!path) return ST_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    FILE *f = std::fopen(path, "w");
+    if (!f) return ST_ERR_INVALID_ARG;
+    for (const auto &kv : g_cache) {
+        const Key &k = kv.first;
+        const Choice &c = kv.second;
+        std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %.6g\n", std::get<0>(k),
+                     std::get<1>(k), std::get<2>(k), std::get<3>(k), std::get<4>(k),
+                     std::get<5>(k), std::get<6>(k), std::get<7>(k), c.T, c.bx, c.by, c.vec,
+                     c.gcells);
+    }
+    const bool ok = std::fclose(f) == 0;
+    return ok ? ST_OK : ST_ERR_INVALID_ARG;
+}
+
+// Entries of the file are added to (or replace those of) the cache; a malformed line rejects
+// the whole file and leaves the cache as it was.
+int stencil_tune_cache_load(const char *path)
+{
+    if (!path) return ST_ERR_INVALID_ARG;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return ST_ERR_INVALID_ARG;
+    std::vector<std::pair<Key, Choice>> got;
+    char line[512];
+    bool ok = true;
+    while (ok && std::fgets(line, sizeof(line), f)) {
+        int v[12];
+        double g = 0.0;
+        int used = 0;
+        const int n = std::sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %d %lf %n", &v[0],
+                                  &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7], &v[8], &v[9],
+                                  &v[10], &v[11], &g, &used);
+        if (n == EOF) continue;   // blank line
+        if (n != 13 || line[used] != '\0') {
+            ok = false;
+            break;
+        }
+        const bool valid = (v[0] == ST_DIFFUSION || v[0] == ST_THERMAL) && (v[1] == 2 || v[1] == 3) &&
+                           v[2] >= 1 && v[3] >= 1 && v[4] >= 1 && (v[1] == 3 || v[4] == 1) &&
+                           v[5] >= ST_F32 && v[5] <= ST_F16 && (v[6] == 0 || v[6] == 1) &&
+                           v[7] >= 0 && v[8] >= 1 && v[9] >= 0 && v[10] >= 0 && v[11] >= 0;
+        if (!valid) {
+            ok = false;
+            break;
+        }
+        got.push_back({Key{v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7]},
+                       Choice{v[8], v[9], v[10], v[11], g}});
+    }
+    std::fclose(f);
+    if (!ok) return ST_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (const auto &kv : got) g_cache[kv.first] = kv.second;
+    return ST_OK;
+}
+
+}  // extern "C"

@@ -43,7 +43,7 @@ def test_binding_covers_header(lib_path):
 
 def test_host_only_calls(lib_path):
     import paper_1802_00438_gb300 as st
-    assert st.lib.stencil_abi_version() == 2
+    assert st.lib.stencil_abi_version() == 3
     assert st.strerror(0) == "ok"
     assert "dimensions" in st.strerror(st.ST_ERR_DIMS_MISMATCH)
     assert st.strerror(12345) == "unknown status"
