@@ -55,6 +55,10 @@ def _load():
                 fn = getattr(lib, name)
                 fn.argtypes = [I, I, P, P, P, L, L, L, I]
                 fn.restype = I
+            for name in ("orc_run_vdiff2d_f32", "orc_run_vdiff2d_f64"):
+                fn = getattr(lib, name)
+                fn.argtypes = [P, P, P, L, L, I]
+                fn.restype = I
             lib.orc_adjoint2d_f64.argtypes = [I, P, P, P, L, L, I, I, P, P, P, P]
             lib.orc_adjoint2d_f64.restype = I
             lib.orc_set_threads.argtypes = [I]
@@ -128,6 +132,27 @@ def run_star(R: int, u0: np.ndarray, coef, steps: int, dtype=np.float32) -> np.n
     out = np.empty_like(u)
     fn = lib.orc_run_star_f32 if dtype == np.float32 else lib.orc_run_star_f64
     rc = fn(u.ndim, int(R), _ptr(u), _ptr(out), _ptr(k), nx, ny, nz, int(steps))
+    if rc != 0:
+        raise RuntimeError(f"oracle failed ({rc})")
+    return out
+
+
+def run_vdiff2d(u0: np.ndarray, coef: np.ndarray, steps: int, dtype=np.float32) -> np.ndarray:
+    """`steps` Jacobi iterations of diffusion 2D with per-cell coefficients: coef has shape
+    (5, ny, nx), the planes [cc, cw, ce, cs, cn]; each cell is updated in Table 2's order with
+    its own coefficients, every operation rounded."""
+    lib = _load()
+    dtype = np.dtype(dtype)
+    u = np.ascontiguousarray(u0, dtype=dtype)
+    if u.ndim != 2:
+        raise ValueError("u0 must be 2D")
+    ny, nx = u.shape
+    k = np.ascontiguousarray(coef, dtype=dtype)
+    if k.shape != (5, ny, nx):
+        raise ValueError("coef must have shape (5, ny, nx)")
+    out = np.empty_like(u)
+    fn = lib.orc_run_vdiff2d_f32 if dtype == np.float32 else lib.orc_run_vdiff2d_f64
+    rc = fn(_ptr(u), _ptr(out), _ptr(k), nx, ny, int(steps))
     if rc != 0:
         raise RuntimeError(f"oracle failed ({rc})")
     return out

@@ -168,6 +168,49 @@ static void CAT(star_step, SFX)(const REAL *in, REAL *out, int ndim, int R, long
     }
 }
 
+/* Diffusion 2D with per-cell coefficients: Table 2 row 1 with every coefficient an array
+ * (Sec. 5.1 passes the kernel's variables as values or arrays), evaluated in the same order:
+ * cc_i*c + cw_i*w + ce_i*e + cs_i*s + cn_i*n, the coefficients those of the cell being updated.
+ * k holds five planar grids [cc | cw | ce | cs | cn], each nx*ny, row-major. */
+static void CAT(vdiff2d_step, SFX)(const REAL *in, REAL *out, long nx, long ny, const REAL *k)
+{
+    long pl = nx * ny;
+#pragma omp parallel for schedule(static)
+    for (long y = 0; y < ny; y++) {
+        long yn = y > 0 ? y - 1 : 0, ys = y < ny - 1 ? y + 1 : ny - 1;
+        for (long x = 0; x < nx; x++) {
+            long xw = x > 0 ? x - 1 : 0, xe = x < nx - 1 ? x + 1 : nx - 1;
+            long i = y * nx + x;
+            REAL r = k[i] * in[i];
+            r = r + k[pl + i] * in[y * nx + xw];
+            r = r + k[2 * pl + i] * in[y * nx + xe];
+            r = r + k[3 * pl + i] * in[ys * nx + x];
+            r = r + k[4 * pl + i] * in[yn * nx + x];
+            out[i] = r;
+        }
+    }
+}
+
+/* `steps` Jacobi iterations of the per-cell-coefficient diffusion 2D. */
+int CAT(orc_run_vdiff2d, SFX)(const REAL *u0, REAL *out, const REAL *k, long nx, long ny,
+                              int steps)
+{
+    if (!u0 || !out || !k || nx < 1 || ny < 1 || steps < 0) return -1;
+    size_t n = (size_t)nx * ny;
+    REAL *a = (REAL *)malloc(n * sizeof(REAL));
+    REAL *b = (REAL *)malloc(n * sizeof(REAL));
+    if (!a || !b) { free(a); free(b); return -1; }
+    memcpy(a, u0, n * sizeof(REAL));
+    for (int s = 0; s < steps; s++) {
+        CAT(vdiff2d_step, SFX)(a, b, nx, ny, k);
+        REAL *t = a; a = b; b = t;
+    }
+    memcpy(out, a, n * sizeof(REAL));
+    free(a);
+    free(b);
+    return 0;
+}
+
 /* `steps` Jacobi iterations of the radius-R star diffusion (ndim 2 or 3, R >= 1). */
 int CAT(orc_run_star, SFX)(int ndim, int R, const REAL *u0, REAL *out, const REAL *coef,
                            long nx, long ny, long nz, int steps)

@@ -81,6 +81,7 @@ class Workload:
     power: np.ndarray | None = field(repr=False)
     coef: np.ndarray = field(repr=False)
     rad: int = 1    # stencil radius: 1 = the Table 2 stencils, > 1 = star diffusion
+    var: bool = False   # diffusion with per-cell coefficients: coef has shape (5, ny, nx)
 
     @property
     def shape(self):
@@ -124,6 +125,30 @@ def make_star(ndim: int, R: int, nx: int, ny: int, nz: int = 1, steps: int = 1, 
     coef = star_coefficients(seed, ndim, R, n)
     return Workload(name or f"star{R}_{ndim}d", DIFFUSION, ndim, nx, ny, nz, steps, seed, u0,
                     None, coef, R)
+
+
+def vdiff_coefficients(seed: int, nx: int, ny: int, offset: int) -> np.ndarray:
+    """Per-cell diffusion coefficients, shape (5, ny, nx), planes [cc, cw, ce, cs, cn]: for
+    every cell five draws u_k ~ U[0.05, 1) (cell-major, in layout order), divided by their
+    float64 sum and rounded to float32, so each cell's weights are positive and sum to 1."""
+    out = np.empty((5, ny, nx), dtype=np.float32)
+    rows = max(1, _CHUNK // (5 * nx))
+    for y0 in range(0, ny, rows):
+        y1 = min(ny, y0 + rows)
+        m = (y1 - y0) * nx
+        u = 0.05 + 0.95 * uniform01(seed, 5 * m, offset + 5 * y0 * nx).reshape(y1 - y0, nx, 5)
+        out[:, y0:y1, :] = np.moveaxis(u / u.sum(axis=2, keepdims=True), 2, 0).astype(np.float32)
+    return out
+
+
+def make_vdiff(nx: int, ny: int, steps: int = 1, seed: int = 1, name: str = "") -> Workload:
+    """Diffusion 2D with per-cell coefficients: field ~ U[0, 1), then the coefficient planes,
+    from stream `seed`.  The planes travel in `coef`; `var` marks the workload."""
+    n = nx * ny
+    u0 = uniform_f32(seed, n, 0.0, 1.0, 0).reshape(ny, nx)
+    coef = vdiff_coefficients(seed, nx, ny, n)
+    return Workload(name or "vardiff2d", DIFFUSION, 2, nx, ny, 1, steps, seed, u0, None, coef,
+                    1, True)
 
 
 def thermal_scalars(seed: int, offset: int):

@@ -503,3 +503,79 @@ def test_star_constant_field_and_max_principle(orc):
     o = orc.run_star(3, w.u0, w.coef, 40, dtype=np.float64)
     lo, hi = float(w.u0.min()), float(w.u0.max())
     assert o.min() >= lo - 1e-12 and o.max() <= hi + 1e-12
+
+
+# --- diffusion 2D with per-cell coefficients (Table 2 row 1, coefficients as arrays) --------
+
+def _dense_vdiff(nx, ny, k):
+    """One step as a dense matrix from the definition: cell i gives its own weights cc_i, cw_i,
+    ce_i, cs_i, cn_i to itself and to the cells one step west, east, south, north, each axis
+    clamped into the grid."""
+    k = np.asarray(k, np.float64)
+    N = nx * ny
+    A = np.zeros((N, N))
+    ax, ay = _axis_neighbours(nx), _axis_neighbours(ny)
+    for y, x in itertools.product(range(ny), range(nx)):
+        i = y * nx + x
+        for j, v in ((i, k[0, y, x]), (y * nx + ax[x][0], k[1, y, x]),
+                     (y * nx + ax[x][1], k[2, y, x]), (ay[y][1] * nx + x, k[3, y, x]),
+                     (ay[y][0] * nx + x, k[4, y, x])):
+            A[i, j] += v
+    return A
+
+
+def test_vdiff_impulse_reads_each_cells_own_coefficients(orc):
+    w = synth.make_vdiff(9, 7, seed=830)
+    x0, y0 = 4, 3
+    u = np.zeros((7, 9))
+    u[y0, x0] = 1.0
+    for dt in (np.float32, np.float64):
+        o = orc.run_vdiff2d(u, w.coef, 1, dtype=dt)
+        k = w.coef.astype(dt)
+        expect = np.zeros((7, 9), dt)
+        expect[y0, x0] = k[0, y0, x0]               # cc of the impulse cell
+        expect[y0, x0 + 1] = k[1, y0, x0 + 1]       # its west neighbour is the impulse
+        expect[y0, x0 - 1] = k[2, y0, x0 - 1]       # its east neighbour is the impulse
+        expect[y0 - 1, x0] = k[3, y0 - 1, x0]       # its south neighbour is the impulse
+        expect[y0 + 1, x0] = k[4, y0 + 1, x0]       # its north neighbour is the impulse
+        assert np.array_equal(o, expect), dt
+
+
+def test_vdiff_constant_planes_are_table2_diffusion(orc):
+    w = synth.make(0, 2, 37, 23, seed=831)
+    planes = np.broadcast_to(w.coef[:, None, None], (5, 23, 37)).copy()
+    for dt in (np.float32, np.float64):
+        assert np.array_equal(orc.run_vdiff2d(w.u0, planes, 17, dtype=dt),
+                              orc.run(0, w.u0, w.coef, 17, dtype=dt))
+
+
+def test_vdiff_dense_matrix_brute_force(orc):
+    for t, (nx, ny) in enumerate([(1, 1), (1, 6), (5, 1), (2, 2), (3, 5), (8, 8), (7, 4)]):
+        w = synth.make_vdiff(nx, ny, seed=840 + t)
+        steps = (5 * t) % 19
+        A = _dense_vdiff(nx, ny, w.coef)
+        u = w.u0.astype(np.float64).ravel()
+        for _ in range(steps):
+            u = A @ u
+        o = orc.run_vdiff2d(w.u0, w.coef, steps, dtype=np.float64).ravel()
+        assert np.allclose(o, u, rtol=1e-13, atol=0), (nx, ny, steps)
+
+
+def test_vdiff_constant_field_and_max_principle(orc):
+    # dyadic per-cell weights summing exactly to 1 keep a dyadic constant field exactly
+    ny, nx = 11, 13
+    rng = synth.uniform01(850, 4 * nx * ny).reshape(4, ny, nx)
+    q = np.floor(rng * 48) / 256.0                      # four weights in [0, 0.1875], dyadic
+    k = np.concatenate([1.0 - q.sum(0, keepdims=True), q])
+    u = np.full((ny, nx), 0.625)
+    for dt in (np.float32, np.float64):
+        assert np.all(orc.run_vdiff2d(u, k, 30, dtype=dt) == 0.625)
+    # positive weights summing to 1 per cell: the field's range never grows
+    # (the float32 weights sum to 1 within a few ulp, so the bound widens by that per step)
+    w = synth.make_vdiff(64, 40, seed=851)
+    o = orc.run_vdiff2d(w.u0, w.coef, 50, dtype=np.float64)
+    sums = w.coef.astype(np.float64).sum(0)
+    grow = float(sums.max()) ** 50
+    shrink = float(sums.min()) ** 50
+    lo, hi = float(w.u0.min()), float(w.u0.max())
+    assert o.min() >= lo * min(shrink, 1.0) - 1e-12 and o.max() <= hi * max(grow, 1.0) + 1e-12
