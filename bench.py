@@ -49,7 +49,11 @@ WORKLOADS = {
     # radius-2 star diffusion (9 points; Eqs. 1-2 with rad = 2), the 2D diffusion grid size
     "star2_2d_16384": lambda: synth.make_star(2, 2, 16384, 16384, steps=1000, seed=7,
                                               name="star2_2d_16384x16384_1000"),
+    # diffusion 2D with per-cell coefficients (Table 2 row 1, coefficients as arrays)
+    "vardiff2d_8192": lambda: synth.make_vdiff(8192, 8192, steps=1000, seed=8,
+                                               name="vardiff2d_8192x8192_1000"),
 }
+BYTES_VAR = 28   # per cell and pass: field in and out, five coefficient planes
 DEFAULT = "thermal2d_16384"
 
 
@@ -186,6 +190,8 @@ def profiled_traffic(workload: str, ndim: int):
 
 def _oracle_run(w, steps, dtype=np.float32):
     import oracle
+    if w.var:
+        return oracle.run_vdiff2d(w.u0, w.coef, steps, dtype=dtype)
     if w.rad > 1:
         return oracle.run_star(w.rad, w.u0, w.coef, steps, dtype=dtype)
     return oracle.run(w.kind, w.u0, w.coef, steps, w.power, dtype=dtype)
@@ -572,7 +578,10 @@ def main():
         return bench_adjoint(args)
     w = WORKLOADS[args.workload]()
     resized = bool(args.nx or args.ny or args.nz or args.time_steps)
-    if resized and w.rad > 1:
+    if resized and w.var:
+        w = synth.make_vdiff(args.nx or w.nx, args.ny or w.ny, steps=args.time_steps or w.steps,
+                             seed=w.seed, name=f"{w.name.split('_')[0]}_resized")
+    elif resized and w.rad > 1:
         w = synth.make_star(w.ndim, w.rad, args.nx or w.nx, args.ny or w.ny, args.nz or w.nz,
                             steps=args.time_steps or w.steps, seed=w.seed,
                             name=f"{w.name.split('_')[0]}_resized")
@@ -595,14 +604,18 @@ def main():
 
     stream = torch.cuda.current_stream(dev)
     u0 = torch.from_numpy(w.u0).to(dev)
-    pw = None if w.power is None else torch.from_numpy(w.power).to(dev)
+    # the per-cell input: the power map, or the five coefficient planes of ST_DIFFUSION_VAR
+    kind = st.ST_DIFFUSION_VAR if w.var else w.kind
+    h_pin = w.coef if w.var else w.power
+    pw = None if h_pin is None else torch.from_numpy(h_pin).to(dev)
+    coef = None if w.var else w.coef
     out = torch.empty_like(u0)
     tuned = None
     if args.tune > 0:
-        tuned = st.stencil_tune(w.kind, w.ndim, w.nx, w.ny, w.nz, u0, out, w.coef, w.steps, pw,
+        tuned = st.stencil_tune(kind, w.ndim, w.nx, w.ny, w.nz, u0, out, coef, w.steps, pw,
                                 top_k=args.tune, storage=args.storage, stream=stream.cuda_stream,
                                 rad=w.rad if w.rad > 1 else 0)
-    plan = st.Plan(w.kind, w.ndim, w.nx, w.ny, w.nz, force_T=args.T, force_bx=args.bx,
+    plan = st.Plan(kind, w.ndim, w.nx, w.ny, w.nz, force_T=args.T, force_bx=args.bx,
                    force_vec=args.vec, force_by=args.by, storage=args.storage,
                    stream=stream.cuda_stream, rad=w.rad if w.rad > 1 else 0)
     info = plan.info()
@@ -610,7 +623,7 @@ def main():
     passes = -(-w.steps // T)
 
     def step():
-        plan.run(u0, out, w.coef, w.steps, power=pw)
+        plan.run(u0, out, coef, w.steps, power=pw)
 
     for _ in range(args.warmup):
         step()
@@ -643,7 +656,7 @@ def main():
     e2e = None
     if not args.no_e2e:
         h_u = torch.from_numpy(w.u0).pin_memory()
-        h_p = None if w.power is None else torch.from_numpy(w.power).pin_memory()
+        h_p = None if h_pin is None else torch.from_numpy(h_pin).pin_memory()
         h_o = torch.empty_like(h_u).pin_memory()
         d_u = torch.empty_like(u0)
         d_p = None if pw is None else torch.empty_like(pw)
@@ -653,7 +666,7 @@ def main():
             d_u.copy_(h_u, non_blocking=True)
             if d_p is not None:
                 d_p.copy_(h_p, non_blocking=True)
-            st.stencil_run(plan.h, d_u, d_o, d_p, w.coef, w.nx, w.ny, w.nz, w.steps)
+            st.stencil_run(plan.h, d_u, d_o, d_p, coef, w.nx, w.ny, w.nz, w.steps)
             h_o.copy_(d_o, non_blocking=True)
 
         e2e_step()
@@ -669,7 +682,7 @@ def main():
         ems = rk.max_ms(a0.elapsed_time(a1))
         nb = w.u0.nbytes
         e2e = {"value": rk.job_rate(cells_step * args.steps, ems) / 1e9, "unit": "GCell/s",
-               "h2d_bytes_per_step": nb * (2 if w.power is not None else 1),
+               "h2d_bytes_per_step": nb + (0 if h_pin is None else h_pin.nbytes),
                "d2h_bytes_per_step": nb}
 
     # ---- roofline of the dominant kernel ---------------------------------------------------
@@ -678,7 +691,7 @@ def main():
     sms = props.multi_processor_count
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fl = _flops(w)
-    by = BYTES[w.kind]
+    by = BYTES_VAR if w.var else BYTES[w.kind]
     alu_peak = fp32_peak_tflops(sms, mhz)
     hbm_peak = float(peaks["hbm_gbs"])
     avg_launch_ms = kern_ms / max(timed_launches, 1)
@@ -713,7 +726,7 @@ def main():
 
     # ---- 16-bit storage: speed on the same workload, error vs the float64 oracle ------------
     lowp = None
-    if w.ndim == 2 and w.rad <= 1 and not resized and not args.no_lowp and not args.storage:
+    if w.ndim == 2 and w.rad <= 1 and not w.var and not resized and not args.no_lowp and not args.storage:
         lowp = {}
         for name, stor in (("bf16", st.ST_BF16), ("fp16", st.ST_F16)):
             qplan = st.Plan(w.kind, 2, w.nx, w.ny, storage=stor, stream=stream.cuda_stream)

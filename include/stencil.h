@@ -57,6 +57,14 @@ extern "C" {
 /* stencil kinds (Table 2) */
 #define ST_DIFFUSION 0
 #define ST_THERMAL   1
+/* Diffusion 2D with per-cell coefficients: Table 2 row 1 whose five coefficients are arrays
+ * (Sec. 5.1 lets a kernel variable be a scalar argument or an array), each cell updated with its own
+ * cc, cw, ce, cs, cn in the printed order.  The arrays are five dense planar grids
+ * [cc | cw | ce | cs | cn] of nx*ny floats each, passed to stencil_run in place of the power
+ * map (device pointer, 5*nx*ny floats, read only); stencil_run's host `coeffs` is unused and
+ * may be NULL.  2D, float32 storage, not strict (the stability bound would need the planes on
+ * the host). */
+#define ST_DIFFUSION_VAR 2
 
 /* storage types of the grids between passes */
 #define ST_F32  0
@@ -68,7 +76,7 @@ typedef struct stencil_plan_s *stencil_plan;
 
 /* Problem and tuning description for stencil_plan_create. */
 typedef struct {
-    int kind;        /* ST_DIFFUSION or ST_THERMAL */
+    int kind;        /* ST_DIFFUSION, ST_THERMAL or ST_DIFFUSION_VAR */
     int ndim;        /* 2 or 3 */
     int nx, ny, nz;  /* grid size in cells, each >= 1; nz is ignored (taken as 1) for 2D */
     int storage;     /* ST_F32 */
@@ -115,9 +123,11 @@ int stencil_plan_create(stencil_plan *out, const stencil_desc *desc);
  * grid_in  : device pointer, nx*ny*nz floats, read only (never modified).
  * grid_out : device pointer, nx*ny*nz floats; may equal grid_in (in place); any other
  *            overlap with grid_in or power is ST_ERR_INVALID_ARG.
- * power    : device pointer to the per-cell power map (same layout) for ST_THERMAL,
- *            NULL for ST_DIFFUSION.
- * coeffs   : host pointer to the coefficient array of the plan's stencil (layouts above).
+ * power    : device pointer to the per-cell power map (same layout) for ST_THERMAL, to the
+ *            five coefficient planes for ST_DIFFUSION_VAR (must not overlap grid_out), NULL
+ *            for ST_DIFFUSION.
+ * coeffs   : host pointer to the coefficient array of the plan's stencil (layouts above);
+ *            NULL is accepted for ST_DIFFUSION_VAR, which does not read it.
  * nx,ny,nz : must equal the plan's (ST_ERR_DIMS_MISMATCH); nz = 1 for 2D.
  * steps    : >= 0; 0 copies grid_in to grid_out.
  * Runs ceil(steps/T) passes on the plan's stream and returns without waiting. */

@@ -10,8 +10,8 @@
  *   - Sec. 5.1: out-of-bound neighbours fall back on the boundary cell itself.
  *   - Eqs. 1-2 with rad > 1 (the paper's named extension): star diffusion of radius R, the
  *     first-order diffusion order extended outwards one distance at a time.
- *   - Table 2 row 1 with every coefficient an array (Sec. 5.1 passes the kernel's variables
- *     as values or arrays): diffusion 2D whose cells carry their own five weights.
+ *   - Table 2 row 1 with every coefficient an array (Sec. 5.1 lets a kernel variable be a
+ *     scalar argument or an array): diffusion 2D whose cells carry their own five weights.
  * The spatial and temporal blocking of Sec. 3 reorganise this computation without changing
  * a single cell's arithmetic, so the blocked engine must reproduce these values exactly
  * when it evaluates the same operations in the same order.

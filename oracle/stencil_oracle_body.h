@@ -169,7 +169,7 @@ static void CAT(star_step, SFX)(const REAL *in, REAL *out, int ndim, int R, long
 }
 
 /* Diffusion 2D with per-cell coefficients: Table 2 row 1 with every coefficient an array
- * (Sec. 5.1 passes the kernel's variables as values or arrays), evaluated in the same order:
+ * (Sec. 5.1 lets a kernel variable be a scalar argument or an array), evaluated in the same order:
  * cc_i*c + cw_i*w + ce_i*e + cs_i*s + cn_i*n, the coefficients those of the cell being updated.
  * k holds five planar grids [cc | cw | ce | cs | cn], each nx*ny, row-major. */
 static void CAT(vdiff2d_step, SFX)(const REAL *in, REAL *out, long nx, long ny, const REAL *k)

@@ -27,6 +27,7 @@ ST_ERR_TOO_LARGE = -8
 
 ST_DIFFUSION = 0
 ST_THERMAL = 1
+ST_DIFFUSION_VAR = 2   # per-cell coefficients: five planes passed as `power`, coeffs unused
 ST_F32, ST_BF16, ST_F16, ST_F64 = 0, 1, 2, 3
 
 
@@ -195,6 +196,8 @@ def _addr(t):
 
 
 def _coef_array(coeffs):
+    if coeffs is None:   # ST_DIFFUSION_VAR plans take their coefficients from device planes
+        return None
     vals = [float(v) for v in (coeffs.tolist() if hasattr(coeffs, "tolist") else coeffs)]
     return (ctypes.c_float * len(vals))(*vals)
 

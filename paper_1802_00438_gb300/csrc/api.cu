@@ -90,6 +90,7 @@ long long cells_of(const stencil_desc &d) { return (long long)d.nx * d.ny * d.nz
 
 int ncoef(const stencil_desc &d)
 {
+    if (d.kind == ST_DIFFUSION_VAR) return 0;   // per-cell coefficient planes on the device
     if (d.rad > 1) return 1 + (d.ndim == 2 ? 4 : 6) * d.rad;
     if (d.ndim == 2) return 5;
     return d.kind == ST_DIFFUSION ? 7 : 9;
@@ -294,6 +295,13 @@ bool ranges_overlap(const void *a, const void *b, size_t n)
     return x < y + n && y < x + n;
 }
 
+// [a, a + na) and [b, b + nb) share a byte
+bool ranges_overlap2(const void *a, size_t na, const void *b, size_t nb)
+{
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + nb && y < x + na;
+}
+
 bool stable(const stencil_desc &d, const float *k)
 {
     const double eps = 1e-6;
@@ -362,6 +370,7 @@ int run_pass2(stencil_plan_s *p, const float *src, long long lds, float *dst, lo
     a.ld_in = lds;
     a.ld_out = ldd;
     a.ld_pw = p->d.nx;
+    a.pw_plane = (long long)p->d.nx * p->d.ny;   // per-cell coefficient planes, dense
     a.nx = p->d.nx;
     a.ny = p->d.ny;
     a.tsteps = tsteps;
@@ -542,7 +551,8 @@ static int plan_create(stencil_plan *out, const stencil_desc *desc)
     *out = nullptr;
     if (!desc) return ST_ERR_INVALID_ARG;
     stencil_desc d = *desc;
-    if (d.kind != ST_DIFFUSION && d.kind != ST_THERMAL) return ST_ERR_INVALID_ARG;
+    if (d.kind != ST_DIFFUSION && d.kind != ST_THERMAL && d.kind != ST_DIFFUSION_VAR)
+        return ST_ERR_INVALID_ARG;
     if (d.ndim != 2 && d.ndim != 3) return ST_ERR_INVALID_ARG;
     if (d.ndim == 2) d.nz = 1;
     if (d.nx < 1 || d.ny < 1 || d.nz < 1) return ST_ERR_INVALID_ARG;
@@ -553,6 +563,12 @@ static int plan_create(stencil_plan *out, const stencil_desc *desc)
     if (d.force_T < 0 || d.force_bx < 0 || d.force_by < 0 || d.force_vec < 0)
         return ST_ERR_INVALID_ARG;
     if (d.rad < 0) return ST_ERR_INVALID_ARG;
+    // per-cell coefficients: 2D float32 plans of the windowed kernel (V = 4, 128 or 512 cells
+    // wide); the stability check of strict plans needs host coefficients
+    if (d.kind == ST_DIFFUSION_VAR &&
+        (d.ndim != 2 || d.storage != ST_F32 || d.rad > 1 || d.strict || d.force_by ||
+         (d.force_vec && d.force_vec != 4) || (d.force_bx && d.force_bx != 128 && d.force_bx != 512)))
+        return ST_ERR_UNSUPPORTED;
     if (d.rad > 1 && (d.kind != ST_DIFFUSION || d.ndim != 2 || d.storage != ST_F32 || d.rad > 4 ||
                       (d.force_bx && d.force_bx != 128) || (d.force_by && d.force_by != 128) ||
                       (d.force_vec && d.force_vec != 4)))
@@ -601,7 +617,8 @@ static int plan_create(stencil_plan *out, const stencil_desc *desc)
         // per tile (bsize_x = 128 W).
         // measured on GB300 (16384^2, T = 8): Hotspot runs best with V = 4 (its V = 8 body
         // overflows the instruction cache), Diffusion with V = 8
-        p->V = d.force_vec ? d.force_vec : ((d.exact || d.kind == ST_THERMAL) ? 4 : 8);
+        const bool var = d.kind == ST_DIFFUSION_VAR;   // windowed kernel, exact or contracted
+        p->V = d.force_vec ? d.force_vec : ((d.exact || d.kind != ST_DIFFUSION) ? 4 : 8);
         if (d.force_bx) {
             if (d.force_bx % (32 * p->V)) rc = ST_ERR_UNSUPPORTED;
             p->W = d.force_bx / (32 * p->V);
@@ -610,7 +627,7 @@ static int plan_create(stencil_plan *out, const stencil_desc *desc)
             if (d.exact && d.nx >= 512) p->W = 4;
         }
         if (!d.exact && d.force_by == 1) p->W = 0;   // in-place partial-row variant
-        if (!d.exact && !p->stor && !d.force_T && !d.force_vec && !d.force_bx && !d.force_by) {
+        if (!d.exact && !var && !p->stor && !d.force_T && !d.force_vec && !d.force_bx && !d.force_by) {
             // contracted, nothing forced: the compiled (T, V, variant) the model rates best
             const Cand2D cands[] = {{4, 4, 1}, {8, 4, 1}, {12, 4, 1}, {4, 8, 1}, {6, 8, 1},
                                     {8, 8, 1}, {8, 8, 0}, {12, 4, 0}};
@@ -629,9 +646,12 @@ static int plan_create(stencil_plan *out, const stencil_desc *desc)
             }
             (void)cudaGetLastError();
         }
-        const int want = d.force_T ? d.force_T : 8;
+        // per-cell coefficients: every fused step keeps five more weight rows per tile column in
+        // shared memory, so deeper fusion costs resident warps; measured on 8192^2 (GB300):
+        // T = 4 with one-warp tiles 608 GCell/s, T = 8 545, four-warp tiles 532 / 451
+        const int want = d.force_T ? d.force_T : (var ? 4 : 8);
         p->T = kernel_T_for(p, want);
-        if (!d.exact && !p->stor && !d.force_T && !d.force_vec && !d.force_bx && !d.force_by) {
+        if (!d.exact && !var && !p->stor && !d.force_T && !d.force_vec && !d.force_bx && !d.force_by) {
             // and the T the model rates best within that family
             double best = -1.0;
             for (int t : kTcand) {
@@ -705,7 +725,7 @@ static int plan_create(stencil_plan *out, const stencil_desc *desc)
         e = cudaMalloc(&p->src, (size_t)d.nx * d.ny * sizeof(float));
         if (e != cudaSuccess) rc = map_cuda(e);
     }
-    if (rc == ST_OK && !d.exact && !p->stor && d.rad <= 1) {
+    if (rc == ST_OK && !d.exact && !p->stor && d.rad <= 1 && d.kind != ST_DIFFUSION_VAR) {
         if (d.ndim == 2) {
             int bps = 0;
             const Shape2D sh{d.kind, 0, p->T, p->V, p->W, d.kind == ST_THERMAL ? STOR_SRC : 0};
@@ -732,14 +752,21 @@ static int plan_create(stencil_plan *out, const stencil_desc *desc)
 int stencil_run(stencil_plan p, const void *grid_in, void *grid_out, const void *power,
                 const float *coeffs, int nx, int ny, int nz, int steps)
 {
-    if (!p || !grid_in || !grid_out || !coeffs || steps < 0) return ST_ERR_INVALID_ARG;
+    if (!p || !grid_in || !grid_out || steps < 0) return ST_ERR_INVALID_ARG;
     const stencil_desc &d = p->d;
+    // per-cell coefficients come as device planes in `power`; host coefficients are unused
+    static const float no_coeffs[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (!coeffs) {
+        if (d.kind != ST_DIFFUSION_VAR) return ST_ERR_INVALID_ARG;
+        coeffs = no_coeffs;
+    }
     if (d.ndim == 2 && nz != 1) return ST_ERR_DIMS_MISMATCH;
     if (nx != d.nx || ny != d.ny || nz != d.nz) return ST_ERR_DIMS_MISMATCH;
-    if ((d.kind == ST_THERMAL) != (power != nullptr)) return ST_ERR_INVALID_ARG;
+    if ((d.kind != ST_DIFFUSION) != (power != nullptr)) return ST_ERR_INVALID_ARG;
     const size_t bytes = (size_t)cells_of(d) * sizeof(float);
+    const size_t pw_bytes = d.kind == ST_DIFFUSION_VAR ? 5 * bytes : bytes;
     if (grid_in != grid_out && ranges_overlap(grid_in, grid_out, bytes)) return ST_ERR_INVALID_ARG;
-    if (power && ranges_overlap(power, grid_out, bytes)) return ST_ERR_INVALID_ARG;
+    if (power && ranges_overlap2(power, pw_bytes, grid_out, bytes)) return ST_ERR_INVALID_ARG;
     if (d.strict && !stable(d, coeffs)) return ST_ERR_UNSTABLE_COEFFS;
     if (p->sticky != ST_OK) return p->sticky;
 

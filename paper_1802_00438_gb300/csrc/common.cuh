@@ -6,7 +6,9 @@
 
 namespace stn {
 
-enum { KDIFF = 0, KTHERM = 1 };
+// stencil kinds: Table 2's diffusion and Hotspot, and diffusion whose five coefficients are
+// per-cell arrays (Table 2 row 1 with Sec. 5.1's array arguments)
+enum { KDIFF = 0, KTHERM = 1, KVDIFF = 2 };
 
 // ---------------------------------------------------------------------------------------
 // Cell updates (arXiv 1802.00438, Table 2).  EXACT = true evaluates the printed expression

@@ -11,8 +11,9 @@ namespace stn {
 struct Pass2D {
     const float *in;
     float *out;
-    const float *pw;       // power map (thermal) or nullptr
+    const float *pw;       // power map (thermal), coefficient planes (per-cell diffusion) or nullptr
     long long ld_in, ld_out, ld_pw;   // row pitches in floats
+    long long pw_plane;    // per-cell diffusion: floats from one coefficient plane to the next
     int nx, ny;
     int tsteps;            // steps fused in this pass, 1..T
     int ntx;               // tiles along x

@@ -5,9 +5,9 @@ namespace stn {
 
 static const Tb2dEntry *tb2d_find(const Shape2D &s)
 {
-    const Tb2dEntry *tabs[2] = {tb2d_table_diff, tb2d_table_therm};
-    const int ns[2] = {tb2d_table_diff_n, tb2d_table_therm_n};
-    if (s.kind < 0 || s.kind > 1) return nullptr;
+    const Tb2dEntry *tabs[3] = {tb2d_table_diff, tb2d_table_therm, tb2d_table_vdiff};
+    const int ns[3] = {tb2d_table_diff_n, tb2d_table_therm_n, tb2d_table_vdiff_n};
+    if (s.kind < 0 || s.kind > 2) return nullptr;
     const Tb2dEntry *t = tabs[s.kind];
     for (int i = 0; i < ns[s.kind]; i++)
         if (t[i].exact == s.exact && t[i].T == s.T && t[i].V == s.V && t[i].W == s.W &&

@@ -23,7 +23,8 @@
 //            and the neighbour warp reads it one row later (one barrier per row).  Lanes with
 //            nothing to publish store to a spare slot, so the store is branch-free.
 //   Power rows (Hotspot) stay in a ring of >= T+PF+1 rows so every stage reads the power of
-//            the row it is computing.
+//            the row it is computing; per-cell diffusion coefficients (kind KVDIFF: five
+//            planar arrays cc, cw, ce, cs, cn) travel the same way, one ring per plane.
 //   Three variants of the row body: PLAIN (interior warps), EDGE (a warp holding x = 0 or
 //            x = nx-1 clamps its neighbours) and SPECIAL (rows at the top or bottom of the grid,
 //            or a pass that forwards trailing stages); interior rows of interior warps carry
@@ -49,12 +50,13 @@ struct TB2 {
     static constexpr int CX = BX - 2 * H;
     static constexpr int PF = 3;                              // rows requested ahead
     static constexpr int NBF = pow2_at_least(PF + 3);         // field ring: r-1 .. r+1, PF ahead
-    static constexpr int NBP = (KIND == KTHERM) ? pow2_at_least(T + PF + 1) : 0;
+    static constexpr int NBP = (KIND != KDIFF) ? pow2_at_least(T + PF + 1) : 0;
+    static constexpr int NPL = (KIND == KVDIFF) ? 5 : 1;     // planes of per-cell input
     static constexpr int NS = T > 1 ? T - 1 : 1;              // register-window stages 1..T-1
     static constexpr int NX = (W > 1 && T > 1) ? (T - 1) : 0; // exchanged stage outputs
     static constexpr int XB = (W + 3) * 2;                    // floats per (parity, stage) block
     static constexpr size_t SMEM =
-        sizeof(float) * ((size_t)(NBF + NBP) * BX + (size_t)2 * (NX > 0 ? NX : 1) * XB);
+        sizeof(float) * ((size_t)(NBF + NPL * NBP) * BX + (size_t)2 * (NX > 0 ? NX : 1) * XB);
     static_assert(V % 4 == 0, "V must be a multiple of 4");
     static_assert(CX > 0, "tile narrower than its halos");
 };
@@ -64,9 +66,10 @@ enum { MODE_PLAIN = 0, MODE_EDGE = 1, MODE_SPECIAL = 2 };
 struct Ctx2 {
     const float *__restrict__ in;
     float *__restrict__ out;
-    const float *__restrict__ pw;
+    const float *__restrict__ pw;   // power map, or the first of the coefficient planes
     long long ld_in, ld_out, ld_pw;
-    float *ringF, *ringP, *xch;
+    long long pw_plane;   // floats from one coefficient plane to the next (KVDIFF)
+    float *ringF, *ringP, *xch;   // ringP: NPL rings of NBP rows each
     int nx, ny, tsteps;
     int x0, xt;           // tile origin, my first cell
     int y_start, last_row, s0, s1;
@@ -93,6 +96,21 @@ __device__ __forceinline__ float upd2(const Ctx2 &c, float m, float w, float e, 
         return hot2<EXACT>(m, w, e, s, n, p, c.k0, c.k1, c.k2, c.k3, c.k4);
 }
 
+// the cell update with per-cell inputs q (Hotspot: power in q[0]; KVDIFF: cc, cw, ce, cs, cn)
+template <int KIND, bool EXACT, int NPL>
+__device__ __forceinline__ float upd2q(const Ctx2 &c, float m, float w, float e, float s, float n,
+                                       const float (&q)[NPL])
+{
+    if (KIND == KVDIFF)
+        return diff5<EXACT>(m, w, e, s, n, q[0], q[NPL > 1 ? 1 : 0], q[NPL > 2 ? 2 : 0],
+                            q[NPL > 3 ? 3 : 0], q[NPL > 4 ? 4 : 0]);
+    return upd2<KIND, EXACT>(c, m, w, e, s, n, q[0]);
+}
+
+// my V cells of per-cell input row `slot` of every plane
+template <int V, int NPL, int NBP, int BX>
+__device__ __forceinline__ void ld_planes(const float *ring, int slot, int o, float (&q)[NPL][V]);
+
 template <int NT>
 __device__ __forceinline__ void tb2_sync()
 {
@@ -101,11 +119,11 @@ __device__ __forceinline__ void tb2_sync()
 }
 
 // Issue the async copy of tile row y (field, and power for Hotspot) into ring slots.
-template <int KIND, int BX, int NT>
+template <int KIND, int BX, int NT, int NPL = 1, int NBP = 0>
 __device__ __forceinline__ void tb2_load_row(const Ctx2 &c, int y, float *dstF, float *dstP)
 {
     const float *srcF = c.in + (long long)y * c.ld_in;
-    const float *srcP = (KIND == KTHERM) ? c.pw + (long long)y * c.ld_pw : nullptr;
+    const float *srcP = (KIND != KDIFF) ? c.pw + (long long)y * c.ld_pw : nullptr;
 #pragma unroll
     for (int qq = 0; qq < BX / 4 / NT; qq++) {
         const int q = c.tid + qq * NT;
@@ -121,16 +139,21 @@ __device__ __forceinline__ void tb2_load_row(const Ctx2 &c, int y, float *dstF, 
                 cp_async4(dstF + 4 * q + j, nb ? srcF + xx : srcF, nb);
             }
         }
-        if (KIND == KTHERM) {
-            if (c.vec_pw) {
-                const int nb = (x >= 0 && x < c.nx) ? min(16, 4 * (c.nx - x)) : 0;
-                cp_async16(dstP + 4 * q, nb ? srcP + x : srcP, nb);
-            } else {
+        if (KIND != KDIFF) {
 #pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const int xx = x + j;
-                    const int nb = (xx >= 0 && xx < c.nx) ? 4 : 0;
-                    cp_async4(dstP + 4 * q + j, nb ? srcP + xx : srcP, nb);
+            for (int pl = 0; pl < NPL; pl++) {
+                const float *sp = srcP + pl * c.pw_plane;
+                float *dp = dstP + pl * NBP * BX;
+                if (c.vec_pw) {
+                    const int nb = (x >= 0 && x < c.nx) ? min(16, 4 * (c.nx - x)) : 0;
+                    cp_async16(dp + 4 * q, nb ? sp + x : sp, nb);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        const int xx = x + j;
+                        const int nb = (xx >= 0 && xx < c.nx) ? 4 : 0;
+                        cp_async4(dp + 4 * q + j, nb ? sp + xx : sp, nb);
+                    }
                 }
             }
         }
@@ -145,6 +168,13 @@ __device__ __forceinline__ void ld_smem_row(const float *p, float (&v)[V])
         float4 t = *reinterpret_cast<const float4 *>(p + 4 * q);
         v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
     }
+}
+
+template <int V, int NPL, int NBP, int BX>
+__device__ __forceinline__ void ld_planes(const float *ring, int slot, int o, float (&q)[NPL][V])
+{
+#pragma unroll
+    for (int pl = 0; pl < NPL; pl++) ld_smem_row<V>(ring + (pl * NBP + slot) * BX + o, q[pl]);
 }
 
 // Neighbour values of my V cells of row `m`, given the cells just left and right of them.
@@ -218,12 +248,15 @@ __device__ __forceinline__ void tb2_iter(const Ctx2 &c, float (&B)[TB2<KIND, EXA
         const float w_in = fm[o > 0 ? o - 1 : 0];
         const float e_in = fm[o + V < C::BX ? o + V : C::BX - 1];
         neighbours<V, ED>(c, m, w_in, e_in, wv, ev);
-        float pv[V];
-        if (KIND == KTHERM) ld_smem_row<V>(c.ringP + ((i - 1) & (C::NBP - 1)) * C::BX + o, pv);
+        float pv[C::NPL][V];
+        if (KIND != KDIFF) ld_planes<V, C::NPL, C::NBP, C::BX>(c.ringP, (i - 1) & (C::NBP - 1), o, pv);
 #pragma unroll
-        for (int j = 0; j < V; j++)
-            out[j] = upd2<KIND, EXACT>(c, m[j], wv[j], ev[j], d[j], u[j],
-                                       KIND == KTHERM ? pv[j] : 0.f);
+        for (int j = 0; j < V; j++) {
+            float q[C::NPL];
+#pragma unroll
+            for (int pl = 0; pl < C::NPL; pl++) q[pl] = KIND != KDIFF ? pv[pl][j] : 0.f;
+            out[j] = upd2q<KIND, EXACT, C::NPL>(c, m[j], wv[j], ev[j], d[j], u[j], q);
+        }
     }
     if constexpr (T == 1) {
         const int R = R0 - 1;
@@ -247,7 +280,6 @@ __device__ __forceinline__ void tb2_stages(const Ctx2 &c,
     // exchange blocks: this row's outputs go to parity i&1, the rows read now came from (i-1)&1
     float *xw = c.xch + (i & 1) * (C::NX > 0 ? C::NX : 1) * C::XB + c.xw_off;
     const float *xr = c.xch + ((i - 1) & 1) * (C::NX > 0 ? C::NX : 1) * C::XB + c.xr_off;
-    const float *pbase = c.ringP + c.tid * V;
 
     // hand stage 0's row to stage 1
 #pragma unroll
@@ -280,12 +312,17 @@ __device__ __forceinline__ void tb2_stages(const Ctx2 &c,
             }
             float wv[V], ev[V];
             neighbours<V, ED>(c, Ws[PM], w_in, e_in, wv, ev);
-            float pv[V];
-            if (KIND == KTHERM) ld_smem_row<V>(pbase + ((i - 1 - s) & (C::NBP - 1)) * C::BX, pv);
+            float pv[C::NPL][V];
+            if (KIND != KDIFF)
+                ld_planes<V, C::NPL, C::NBP, C::BX>(c.ringP, (i - 1 - s) & (C::NBP - 1), c.tid * V, pv);
 #pragma unroll
-            for (int j = 0; j < V; j++)
-                out[j] = upd2<KIND, EXACT>(c, Ws[PM][j], wv[j], ev[j], Ws[PD][j], Ws[PU][j],
-                                           KIND == KTHERM ? pv[j] : 0.f);
+            for (int j = 0; j < V; j++) {
+                float q[C::NPL];
+#pragma unroll
+                for (int pl = 0; pl < C::NPL; pl++) q[pl] = KIND != KDIFF ? pv[pl][j] : 0.f;
+                out[j] = upd2q<KIND, EXACT, C::NPL>(c, Ws[PM][j], wv[j], ev[j], Ws[PD][j],
+                                                    Ws[PU][j], q);
+            }
             if (SP && R == -1) {   // top edge: the next window's row -1 is row 0
 #pragma unroll
                 for (int j = 0; j < V; j++) Ws[PM][j] = Ws[PD][j];
@@ -313,9 +350,10 @@ __global__ void __launch_bounds__(32 * W) k_tb2d(const Pass2D p)
     c.ld_in = p.ld_in;
     c.ld_out = p.ld_out;
     c.ld_pw = p.ld_pw;
+    c.pw_plane = p.pw_plane;
     c.ringF = smem;
     c.ringP = smem + C::NBF * C::BX;
-    c.xch = c.ringP + C::NBP * C::BX;
+    c.xch = c.ringP + C::NPL * C::NBP * C::BX;
     c.nx = p.nx;
     c.ny = p.ny;
     c.tsteps = p.tsteps;
@@ -378,7 +416,7 @@ __global__ void __launch_bounds__(32 * W) k_tb2d(const Pass2D p)
         for (int j = 0; j < C::PF; j++) {
             const int y = c.y_start + j;
             if (y <= c.last_row)
-                tb2_load_row<KIND, C::BX, C::NT>(c, y, c.ringF + (j & (C::NBF - 1)) * C::BX,
+                tb2_load_row<KIND, C::BX, C::NT, C::NPL, C::NBP>(c, y, c.ringF + (j & (C::NBF - 1)) * C::BX,
                                                  c.ringP + (j & (C::NBP > 0 ? C::NBP - 1 : 0)) * C::BX);
             cp_async_commit();
         }
@@ -397,7 +435,7 @@ __global__ void __launch_bounds__(32 * W) k_tb2d(const Pass2D p)
         {                                                                                      \
             const int y = c.y_start + i + C::PF;                                               \
             if (y <= c.last_row)                                                               \
-                tb2_load_row<KIND, C::BX, C::NT>(                                              \
+                tb2_load_row<KIND, C::BX, C::NT, C::NPL, C::NBP>(                              \
                     c, y, c.ringF + ((i + C::PF) & (C::NBF - 1)) * C::BX,                      \
                     c.ringP + ((i + C::PF) & (C::NBP > 0 ? C::NBP - 1 : 0)) * C::BX);          \
             cp_async_commit();                                                                 \

@@ -44,5 +44,7 @@ extern const Tb2dEntry tb2d_table_diff[];
 extern const int tb2d_table_diff_n;
 extern const Tb2dEntry tb2d_table_therm[];
 extern const int tb2d_table_therm_n;
+extern const Tb2dEntry tb2d_table_vdiff[];
+extern const int tb2d_table_vdiff_n;
 
 }  // namespace stn

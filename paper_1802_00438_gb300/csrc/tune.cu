@@ -46,7 +46,7 @@ std::vector<std::array<int, 4>> candidates(const stencil_desc &d)
     } else if (d.ndim == 2) {
         for (int V : {4, 8})
             for (int T : Ts) {
-                if (d.exact) {
+                if (d.exact || d.kind == ST_DIFFUSION_VAR) {   // the windowed kernel
                     if (V != 4) continue;
                     for (int bx : {128, 512}) c.push_back({T, bx, 0, 4});
                 } else {
