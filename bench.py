@@ -49,6 +49,9 @@ WORKLOADS = {
     # radius-2 star diffusion (9 points; Eqs. 1-2 with rad = 2), the 2D diffusion grid size
     "star2_2d_16384": lambda: synth.make_star(2, 2, 16384, 16384, steps=1000, seed=7,
                                               name="star2_2d_16384x16384_1000"),
+    # radius-2 star diffusion in 3D (13 points), the 3D diffusion grid size
+    "star2_3d_512": lambda: synth.make_star(3, 2, 512, 512, 512, steps=1000, seed=9,
+                                            name="star2_3d_512x512x512_1000"),
     # diffusion 2D with per-cell coefficients (Table 2 row 1, coefficients as arrays)
     "vardiff2d_8192": lambda: synth.make_vdiff(8192, 8192, steps=1000, seed=8,
                                                name="vardiff2d_8192x8192_1000"),
@@ -198,9 +201,10 @@ def _oracle_run(w, steps, dtype=np.float32):
 
 
 def _flops(w):
-    """Counted flops per cell update: Table 2's for the first-order stencils, 8R + 1 for the
-    radius-R star (one multiply and 4R multiply-adds counted as two flops each)."""
-    return 8 * w.rad + 1 if w.rad > 1 else FLOPS[(w.kind, w.ndim)]
+    """Counted flops per cell update: Table 2's for the first-order stencils, 8R + 1 (2D) or
+    12R + 1 (3D) for the radius-R star (one multiply and 2 ndim R multiply-adds counted as two
+    flops each)."""
+    return 4 * w.ndim * w.rad + 1 if w.rad > 1 else FLOPS[(w.kind, w.ndim)]
 
 
 def _oracle_sample_steps(w, budget_s: float):

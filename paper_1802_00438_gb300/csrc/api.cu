@@ -57,6 +57,7 @@ struct stencil_plan_s {
     int tuned = 0;        // configuration taken from the tuning cache
     float *src = nullptr;   // contracted float32 Hotspot 2D: the source map p + amb*Rz
     int ntx_star = 0, nty_star = 0;   // star diffusion (rad > 1): tiles along x and y
+    int nseg_star = 1, zseg_star = 0; // 3D star: z-segments per tile column, their length
     std::vector<PassCfg3D> cfg3;
     // timing
     bool timing = false;
@@ -429,8 +430,38 @@ int run_pass2q(stencil_plan_s *p, int src, int dst, const float *k, int tsteps)
     return map_cuda(e);
 }
 
+int run_pass_star3(stencil_plan_s *p, const float *src, float *dst, const float *k, int tsteps)
+{
+    PassStar3D a = {};
+    a.in = src;
+    a.out = dst;
+    a.nx = p->d.nx;
+    a.ny = p->d.ny;
+    a.nz = p->d.nz;
+    a.tsteps = tsteps;
+    a.ntx = p->ntx_star;
+    a.nty = p->nty_star;
+    a.nseg = p->nseg_star;
+    a.zseg = p->zseg_star;
+    for (int i = 0; i < ncoef(p->d) && i < 25; i++) a.k[i] = k[i];
+    a.vec_out = ((uintptr_t)dst % 16 == 0) && (p->d.nx % 4 == 0);
+    a.err = p->err;
+    CUtensorMap tm;
+    std::memset(&tm, 0, sizeof(tm));
+    a.use_tma = tma3d_encode(&tm, src, p->d.nx, p->d.ny, p->d.nz, 64, 64) ? 1 : 0;
+    if (p->timing && p->ev_used + 2 > 2 * 1024) {
+        const int rc = flush_timing(p);
+        if (rc != ST_OK) return rc;
+    }
+    cudaError_t e = record(p, true);
+    if (e == cudaSuccess) e = star3d_launch(p->d.rad, p->d.exact, p->T, a, tm, p->stream);
+    if (e == cudaSuccess) e = record(p, false);
+    return map_cuda(e);
+}
+
 int run_pass_star(stencil_plan_s *p, const float *src, float *dst, const float *k, int tsteps)
 {
+    if (p->d.ndim == 3) return run_pass_star3(p, src, dst, k, tsteps);
     PassStar2D a = {};
     a.in = src;
     a.out = dst;
@@ -569,10 +600,13 @@ static int plan_create(stencil_plan *out, const stencil_desc *desc)
         (d.ndim != 2 || d.storage != ST_F32 || d.rad > 1 || d.strict || d.force_by ||
          (d.force_vec && d.force_vec != 4) || (d.force_bx && d.force_bx != 128 && d.force_bx != 512)))
         return ST_ERR_UNSUPPORTED;
-    if (d.rad > 1 && (d.kind != ST_DIFFUSION || d.ndim != 2 || d.storage != ST_F32 || d.rad > 4 ||
-                      (d.force_bx && d.force_bx != 128) || (d.force_by && d.force_by != 128) ||
-                      (d.force_vec && d.force_vec != 4)))
-        return ST_ERR_UNSUPPORTED;
+    if (d.rad > 1) {
+        const int tile = d.ndim == 2 ? 128 : 64;   // star tiles: 128 x 128 in 2D, 64 x 64 in 3D
+        if (d.kind != ST_DIFFUSION || d.storage != ST_F32 || d.rad > 4 ||
+            (d.force_bx && d.force_bx != tile) || (d.force_by && d.force_by != tile) ||
+            (d.force_vec && d.force_vec != (d.ndim == 2 ? 4 : 16)))
+            return ST_ERR_UNSUPPORTED;
+    }
 
     stencil_plan_s *p = new (std::nothrow) stencil_plan_s();
     if (!p) return ST_ERR_OOM;
@@ -587,7 +621,45 @@ static int plan_create(stencil_plan *out, const stencil_desc *desc)
     }
 
     p->stor = d.storage == ST_BF16 ? 1 : (d.storage == ST_F16 ? 2 : 0);
-    if (d.rad > 1) {
+    if (d.rad > 1 && d.ndim == 3) {
+        // 3D star diffusion: 64 x 64 tiles streamed along z, T = 1 unless forced: measured on
+        // 512^3, R = 2 (GB300), T = 1 runs at 382 GCell/s and T = 2 at 271 -- the second ring
+        // of planes leaves one 8-warp block per SM and adds a barrier per plane
+        const int T = d.force_T ? d.force_T : 1;
+        int bps = 0;
+        if (!star3d_available(d.rad, d.exact, T)) rc = ST_ERR_UNSUPPORTED;
+        if (rc == ST_OK) {
+            e = star3d_prepare(d.rad, d.exact, T, &bps);
+            if (e != cudaSuccess) rc = map_cuda(e);
+            else if (bps < 1) rc = ST_ERR_UNSUPPORTED;
+        }
+        if (rc == ST_OK) {
+            p->T = T;
+            int cx = 0, cy = 0;
+            star3d_tile(d.rad, T, &cx, &cy);
+            p->ntx_star = (d.nx + cx - 1) / cx;
+            p->nty_star = (d.ny + cy - 1) / cy;
+            // z-segments: the count that keeps the most block slots busy, discounted by the
+            // planes a segment re-reads (R T at either end); segments at least 8 R T long
+            const long long cols = (long long)p->ntx_star * p->nty_star;
+            const long long slots = (long long)p->sms * bps;
+            const int max_seg = std::max(1, d.nz / (8 * d.rad * T));
+            double best = -1.0;
+            long long nseg = 1;
+            for (int n = 1; n <= max_seg; n++) {
+                const long long blocks = cols * n, waves = (blocks + slots - 1) / slots;
+                const double zs = (double)((d.nz + n - 1) / n);
+                const double eff = (double)blocks / (double)(waves * slots) * zs / (zs + 2.0 * d.rad * T);
+                if (eff > best + 1e-9) {
+                    best = eff;
+                    nseg = n;
+                }
+            }
+            p->zseg_star = (int)((d.nz + nseg - 1) / nseg);
+            p->nseg_star = (d.nz + p->zseg_star - 1) / p->zseg_star;
+            p->scratch_bytes = (size_t)cells_of(d) * sizeof(float);
+        }
+    } else if (d.rad > 1) {
         // star diffusion: 128 x 128 tiles, T from {1, 2, 4} (default: the largest whose halos
         // leave at least 70 % of the tile's cells in its compute block)
         int T = d.force_T;
@@ -868,7 +940,17 @@ int stencil_plan_get_info(stencil_plan p, stencil_plan_info *info)
     info->sms = p->sms;
     info->scratch_bytes = (long long)p->scratch_bytes;
     info->exact = p->d.exact;
-    if (p->d.rad > 1) {
+    if (p->d.rad > 1 && p->d.ndim == 3) {
+        int cx = 0, cy = 0;
+        star3d_tile(p->d.rad, p->T, &cx, &cy);
+        info->bx = 64;
+        info->by = 64;
+        info->halo = (64 - cx) / 2;
+        info->vec = 16;
+        info->warps = 8;
+        info->ctas = p->ntx_star * p->nty_star * p->nseg_star;
+        info->kernel_id = 6;
+    } else if (p->d.rad > 1) {
         info->bx = 128;
         info->by = 128;
         info->halo = star2d_halo_x(p->d.rad, p->T);

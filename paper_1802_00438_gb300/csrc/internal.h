@@ -101,6 +101,26 @@ cudaError_t star2d_prepare(int R, int exact, int T);
 cudaError_t star2d_launch(int R, int exact, int T, const PassStar2D &p, const CUtensorMap &tin,
                           cudaStream_t st);
 
+// One pass of the 3D star diffusion of radius R (star3d.cu): one block per (tile, z-segment).
+struct PassStar3D {
+    const float *in;
+    float *out;
+    int nx, ny, nz;            // dense grids: row pitch nx, plane pitch nx * ny
+    int tsteps;                // steps fused in this pass, 1..T
+    int ntx, nty;              // tiles along x and y
+    int nseg, zseg;            // z-segments per tile column and their length in planes
+    float k[25];               // cc, then cw, ce, cs, cn, cb, ca per distance 1..R
+    int use_tma;               // stage planes by tensor-map copies
+    int vec_out;               // output rows start on 16-byte boundaries
+    int *err;                  // device flag: a bounded wait gave up
+};
+
+bool star3d_available(int R, int exact, int T);
+void star3d_tile(int R, int T, int *cx, int *cy);   // compute block per tile
+cudaError_t star3d_prepare(int R, int exact, int T, int *blocks_per_sm);
+cudaError_t star3d_launch(int R, int exact, int T, const PassStar3D &p, const CUtensorMap &tin,
+                          cudaStream_t st);
+
 // One pass of the 3D sweep (tb3d.cu).
 struct Pass3D {
     const float *in;
