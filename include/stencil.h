@@ -82,7 +82,8 @@ typedef struct {
     int storage;     /* ST_F32 */
     int force_T;     /* fused steps per pass (par_time, Sec. 3.2); 0 = the plan chooses */
     int force_bx;    /* tile width in cells incl. halos (bsize_x, Sec. 3.1); 0 = choose */
-    int force_by;    /* 3D: tile height in cells incl. halos (bsize_y); 0 = choose */
+    int force_by;    /* 3D: tile height in cells incl. halos (bsize_y); 0 = choose.  2D
+                        contracted plans: 1 = the variant that updates partial rows in place */
     int force_vec;   /* 2D: cells per thread along x (par_vec, Sec. 3.1); 3D: cells per thread,
                         16 (2 x 8 rows, three-plane windows), 8 (2 x 4 rows) or 4 (2 x 2 rows;
                         8 and 4: partial sums along z, contracted only); 0 = choose */

@@ -364,7 +364,7 @@ int run_pass2(stencil_plan_s *p, const float *src, long long lds, float *dst, lo
     PassCfg2D *c = nullptr;
     int rc = prepare2(p, kernel_T_for(p, tsteps), &c);
     if (rc != ST_OK) return rc;
-    Pass2D a;
+    Pass2D a = {};
     a.in = src;
     a.out = dst;
     a.pw = pw;

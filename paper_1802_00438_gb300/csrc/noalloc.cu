@@ -93,7 +93,7 @@ int pass2(const DeviceSlot &dv, int kind, int exact, int V, int W, int T, const 
     if (e != cudaSuccess) return to_status(e);
     if (bps < 1) return ST_ERR_UNSUPPORTED;
     const int bx = tb2d_tile_width(sh), h = tb2d_halo(sh), cx = bx - 2 * h;
-    Pass2D a;
+    Pass2D a = {};
     a.in = src;
     a.out = dst;
     a.pw = pw;
