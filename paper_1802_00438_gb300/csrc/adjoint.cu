@@ -158,6 +158,8 @@ __global__ void __launch_bounds__(ANT) k_adj2d(const AdjPass a, const __grid_con
     const int x0 = tx * ACX - ATA, y0 = ty * ACY - ATA;
     const bool tma = a.use_tma != 0;
     const uint32_t b0 = sm32(&bars[0]);
+    // block-uniform: the whole tile is in the grid and no cell of it lies on the grid's edge
+    const bool interior = tma && x0 >= 1 && y0 >= 1 && x0 + AX <= a.nx - 1 && y0 + AY <= a.ny - 1;
 
     if (tma) {
         if (tid == 0) {
@@ -220,6 +222,37 @@ __global__ void __launch_bounds__(ANT) k_adj2d(const AdjPass a, const __grid_con
                 return;
             }
         }
+        if (interior) {
+            // the tile lies inside the grid, off its edges: no clamp, no diagonal correction,
+            // no mask but the compute block (the same operations, in the same order, as below)
+#pragma unroll
+            for (int q = 0; q < ACPT; q++) {
+                const int idx = tid + q * ANT, lx = idx % AX, ly = idx / AX;
+                const float l = cur[idx];
+                const float le = lx + 1 < AX ? cur[idx + 1] : 0.f;
+                const float lw = lx > 0 ? cur[idx - 1] : 0.f;
+                const float ln = ly > 0 ? cur[idx - AX] : 0.f;
+                const float ls = ly + 1 < AY ? cur[idx + AX] : 0.f;
+                float r = __fmul_rn(a.wc, l);
+                r = __fmaf_rn(a.ww, le, r);
+                r = __fmaf_rn(a.we, lw, r);
+                r = __fmaf_rn(a.ws, ln, r);
+                r = __fmaf_rn(a.wn, ls, r);
+                nxt[idx] = r;
+                if (lx >= ATA && lx < ATA + ACX && ly >= ATA && ly < ATA + ACY) {
+                    float g[NG];
+                    const float p = KIND == ST_THERMAL ? ptile[idx] : 0.f;
+                    dfdtheta<KIND>(a, ut[idx], ut[idx - 1], ut[idx + 1], ut[idx + AX],
+                                   ut[idx - AX], p, g);
+#pragma unroll
+                    for (int m = 0; m < NG; m++) {
+                        hi[m] = __fmaf_rn(l, g[m], hi[m]);
+                        ab[m] = __fmaf_rn(fabsf(l), fabsf(g[m]), ab[m]);
+                    }
+                    if (KIND == ST_THERMAL) pacc[q] = __fadd_rn(pacc[q], l);
+                }
+            }
+        } else {
 #pragma unroll
         for (int q = 0; q < ACPT; q++) {
             const int idx = tid + q * ANT, lx = idx % AX, ly = idx / AX;
@@ -267,6 +300,7 @@ __global__ void __launch_bounds__(ANT) k_adj2d(const AdjPass a, const __grid_con
                 }
                 if (KIND == ST_THERMAL) pacc[q] = __fadd_rn(pacc[q], l);
             }
+        }
         }
         __syncthreads();
         float *t = cur;
