@@ -40,6 +40,7 @@
 namespace {
 
 constexpr int AX = 128, AY = 64, ANT = 512, ACPT = AX * AY / ANT;   // tile, threads, cells/thread
+static_assert(AX == 4 * 32 && AY == 4 * (ANT / 32), "a lane owns 4 x 4 cells of the tile");
 constexpr int ATA = 4;                                                // fused adjoint steps
 constexpr int ACX = AX - 2 * ATA, ACY = AY - 2 * ATA;                // compute block
 constexpr int NG = 5;                                                 // coefficients
@@ -141,6 +142,98 @@ __device__ __forceinline__ void dfdtheta(const AdjPass &a, float c, float w, flo
     }
 }
 
+// Thread layout of a tile: lane L owns cells 4L .. 4L+3 of rows 4w .. 4w+3 of warp w; its
+// cells are visited row by row, left to right (cell c = 4 r + j), on every path, so every
+// path accumulates the same terms in the same order.
+__device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+
+// One transposed step on my 4 x 4 cells of a tile inside the grid and off its edges: the
+// rows by 16-byte loads, the x-neighbours across lanes by shuffles; per cell the operations
+// and their order are those of the general path.
+template <int KIND>
+__device__ __forceinline__ void adj_block_interior(const AdjPass &a, int lane, int ly0,
+                                                   const float *cur, float *nxt, const float *ut,
+                                                   const float *ptile, float (&hi)[NG],
+                                                   float (&ab)[NG], float (&pacc)[ACPT])
+{
+    const int lx0 = 4 * lane;
+    float L[6][4];   // lambda rows ly0-1 .. ly0+4 (zero beyond the tile)
+#pragma unroll
+    for (int rr = 0; rr < 6; rr++) {
+        const int row = ly0 - 1 + rr;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (row >= 0 && row < AY) v = lds4(cur + row * AX + lx0);
+        L[rr][0] = v.x; L[rr][1] = v.y; L[rr][2] = v.z; L[rr][3] = v.w;
+    }
+    float wl[4], er[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        wl[r] = __shfl_sync(0xffffffffu, L[r + 1][3], (lane + 31) & 31);
+        er[r] = __shfl_sync(0xffffffffu, L[r + 1][0], (lane + 1) & 31);
+        if (lane == 0) wl[r] = 0.f;
+        if (lane == 31) er[r] = 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        float o[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const float le = j < 3 ? L[r + 1][j + 1] : er[r];
+            const float lw = j > 0 ? L[r + 1][j - 1] : wl[r];
+            float v = __fmul_rn(a.wc, L[r + 1][j]);
+            v = __fmaf_rn(a.ww, le, v);
+            v = __fmaf_rn(a.we, lw, v);
+            v = __fmaf_rn(a.ws, L[r][j], v);
+            v = __fmaf_rn(a.wn, L[r + 2][j], v);
+            o[j] = v;
+        }
+        *reinterpret_cast<float4 *>(nxt + (ly0 + r) * AX + lx0) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+    // gradient terms of the compute block (its cells and their neighbours are in the tile);
+    // the condition is warp-uniform, so every lane takes part in the shuffles below
+    const bool rows_any = ly0 + 3 >= ATA && ly0 < ATA + ACY;
+    if (rows_any) {
+        float U[6][4];
+#pragma unroll
+        for (int rr = 0; rr < 6; rr++) {
+            const int row = min(max(ly0 - 1 + rr, 0), AY - 1);   // only own cells' rows are used
+            const float4 v = lds4(ut + row * AX + lx0);
+            U[rr][0] = v.x; U[rr][1] = v.y; U[rr][2] = v.z; U[rr][3] = v.w;
+        }
+        float uw[4], ue[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            uw[r] = __shfl_sync(0xffffffffu, U[r + 1][3], (lane + 31) & 31);
+            ue[r] = __shfl_sync(0xffffffffu, U[r + 1][0], (lane + 1) & 31);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const int ly = ly0 + r;
+            if (ly < ATA || ly >= ATA + ACY) continue;
+            float pr[4] = {0.f, 0.f, 0.f, 0.f};
+            if (KIND == ST_THERMAL) {
+                const float4 v = lds4(ptile + ly * AX + lx0);
+                pr[0] = v.x; pr[1] = v.y; pr[2] = v.z; pr[3] = v.w;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int lx = lx0 + j;
+                if (lx < ATA || lx >= ATA + ACX) continue;
+                float g[NG];
+                dfdtheta<KIND>(a, U[r + 1][j], j > 0 ? U[r + 1][j - 1] : uw[r],
+                               j < 3 ? U[r + 1][j + 1] : ue[r], U[r + 2][j], U[r][j], pr[j], g);
+                const float l = L[r + 1][j];
+#pragma unroll
+                for (int m = 0; m < NG; m++) {
+                    hi[m] = __fmaf_rn(l, g[m], hi[m]);
+                    ab[m] = __fmaf_rn(fabsf(l), fabsf(g[m]), ab[m]);
+                }
+                if (KIND == ST_THERMAL) pacc[4 * r + j] = __fadd_rn(pacc[4 * r + j], l);
+            }
+        }
+    }
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(ANT) k_adj2d(const AdjPass a, const __grid_constant__ CUtensorMap tl,
                                                const __grid_constant__ CUtensorMap tu,
@@ -196,6 +289,7 @@ __global__ void __launch_bounds__(ANT) k_adj2d(const AdjPass a, const __grid_con
         __syncthreads();
     }
 
+    const int lane = tid & 31, lx0 = 4 * lane, ly0 = 4 * (tid >> 5);   // my 4 x 4 cells
     float hi[NG], lo[NG], ab[NG], pacc[ACPT];
 #pragma unroll
     for (int m = 0; m < NG; m++) hi[m] = lo[m] = ab[m] = 0.f;
@@ -223,84 +317,56 @@ __global__ void __launch_bounds__(ANT) k_adj2d(const AdjPass a, const __grid_con
             }
         }
         if (interior) {
-            // the tile lies inside the grid, off its edges: no clamp, no diagonal correction,
-            // no mask but the compute block (the same operations, in the same order, as below)
+            adj_block_interior<KIND>(a, lane, ly0, cur, nxt, ut, ptile, hi, ab, pacc);
+        } else {
 #pragma unroll
-            for (int q = 0; q < ACPT; q++) {
-                const int idx = tid + q * ANT, lx = idx % AX, ly = idx / AX;
-                const float l = cur[idx];
+            for (int c = 0; c < ACPT; c++) {
+                const int lx = lx0 + (c & 3), ly = ly0 + (c >> 2), idx = ly * AX + lx;
+                const int gx = x0 + lx, gy = y0 + ly;
+                const bool in = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny;
+                const float l = cur[idx];   // lambda_{t+1}
                 const float le = lx + 1 < AX ? cur[idx + 1] : 0.f;
                 const float lw = lx > 0 ? cur[idx - 1] : 0.f;
                 const float ln = ly > 0 ? cur[idx - AX] : 0.f;
                 const float ls = ly + 1 < AY ? cur[idx + AX] : 0.f;
-                float r = __fmul_rn(a.wc, l);
+                float cs = a.wc;
+                if (gx == 0) cs = __fadd_rn(cs, a.ww);
+                if (gx == a.nx - 1) cs = __fadd_rn(cs, a.we);
+                if (gy == 0) cs = __fadd_rn(cs, a.wn);
+                if (gy == a.ny - 1) cs = __fadd_rn(cs, a.ws);
+                float r = __fmul_rn(cs, l);
                 r = __fmaf_rn(a.ww, le, r);
                 r = __fmaf_rn(a.we, lw, r);
                 r = __fmaf_rn(a.ws, ln, r);
                 r = __fmaf_rn(a.wn, ls, r);
-                nxt[idx] = r;
-                if (lx >= ATA && lx < ATA + ACX && ly >= ATA && ly < ATA + ACY) {
+                nxt[idx] = in ? r : 0.f;
+                const bool own = in && lx >= ATA && lx < ATA + ACX && ly >= ATA && ly < ATA + ACY;
+                if (own) {
                     float g[NG];
-                    const float p = KIND == ST_THERMAL ? ptile[idx] : 0.f;
-                    dfdtheta<KIND>(a, ut[idx], ut[idx - 1], ut[idx + 1], ut[idx + AX],
-                                   ut[idx - AX], p, g);
+                    if (tma) {
+                        // own cells are ATA >= 1 cells inside the tile; clamp at the domain edges
+                        const int dw = gx > 0 ? 1 : 0, de = gx < a.nx - 1 ? 1 : 0;
+                        const int dn = gy > 0 ? AX : 0, dsn = gy < a.ny - 1 ? AX : 0;
+                        const float p = KIND == ST_THERMAL ? ptile[idx] : 0.f;
+                        dfdtheta<KIND>(a, ut[idx], ut[idx - dw], ut[idx + de], ut[idx + dsn],
+                                       ut[idx - dn], p, g);
+                    } else {
+                        const long long o = (long long)gy * a.nx;
+                        const int xw = gx > 0 ? gx - 1 : 0, xe = gx < a.nx - 1 ? gx + 1 : a.nx - 1;
+                        const long long on = (long long)(gy > 0 ? gy - 1 : 0) * a.nx;
+                        const long long os = (long long)(gy < a.ny - 1 ? gy + 1 : a.ny - 1) * a.nx;
+                        const float p = KIND == ST_THERMAL ? __ldg(a.pw + o + gx) : 0.f;
+                        dfdtheta<KIND>(a, __ldg(u + o + gx), __ldg(u + o + xw), __ldg(u + o + xe),
+                                       __ldg(u + os + gx), __ldg(u + on + gx), p, g);
+                    }
 #pragma unroll
                     for (int m = 0; m < NG; m++) {
                         hi[m] = __fmaf_rn(l, g[m], hi[m]);
                         ab[m] = __fmaf_rn(fabsf(l), fabsf(g[m]), ab[m]);
                     }
-                    if (KIND == ST_THERMAL) pacc[q] = __fadd_rn(pacc[q], l);
+                    if (KIND == ST_THERMAL) pacc[c] = __fadd_rn(pacc[c], l);
                 }
             }
-        } else {
-#pragma unroll
-        for (int q = 0; q < ACPT; q++) {
-            const int idx = tid + q * ANT, lx = idx % AX, ly = idx / AX;
-            const int gx = x0 + lx, gy = y0 + ly;
-            const bool in = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny;
-            const float l = cur[idx];   // lambda_{t+1}
-            const float le = lx + 1 < AX ? cur[idx + 1] : 0.f;
-            const float lw = lx > 0 ? cur[idx - 1] : 0.f;
-            const float ln = ly > 0 ? cur[idx - AX] : 0.f;
-            const float ls = ly + 1 < AY ? cur[idx + AX] : 0.f;
-            float cs = a.wc;
-            if (gx == 0) cs = __fadd_rn(cs, a.ww);
-            if (gx == a.nx - 1) cs = __fadd_rn(cs, a.we);
-            if (gy == 0) cs = __fadd_rn(cs, a.wn);
-            if (gy == a.ny - 1) cs = __fadd_rn(cs, a.ws);
-            float r = __fmul_rn(cs, l);
-            r = __fmaf_rn(a.ww, le, r);
-            r = __fmaf_rn(a.we, lw, r);
-            r = __fmaf_rn(a.ws, ln, r);
-            r = __fmaf_rn(a.wn, ls, r);
-            nxt[idx] = in ? r : 0.f;
-            const bool own = in && lx >= ATA && lx < ATA + ACX && ly >= ATA && ly < ATA + ACY;
-            if (own) {
-                float g[NG];
-                if (tma) {
-                    // own cells are ATA >= 1 cells inside the tile; clamp at the domain edges
-                    const int dw = gx > 0 ? 1 : 0, de = gx < a.nx - 1 ? 1 : 0;
-                    const int dn = gy > 0 ? AX : 0, dsn = gy < a.ny - 1 ? AX : 0;
-                    const float p = KIND == ST_THERMAL ? ptile[idx] : 0.f;
-                    dfdtheta<KIND>(a, ut[idx], ut[idx - dw], ut[idx + de], ut[idx + dsn],
-                                   ut[idx - dn], p, g);
-                } else {
-                    const long long o = (long long)gy * a.nx;
-                    const int xw = gx > 0 ? gx - 1 : 0, xe = gx < a.nx - 1 ? gx + 1 : a.nx - 1;
-                    const long long on = (long long)(gy > 0 ? gy - 1 : 0) * a.nx;
-                    const long long os = (long long)(gy < a.ny - 1 ? gy + 1 : a.ny - 1) * a.nx;
-                    const float p = KIND == ST_THERMAL ? __ldg(a.pw + o + gx) : 0.f;
-                    dfdtheta<KIND>(a, __ldg(u + o + gx), __ldg(u + o + xw), __ldg(u + o + xe),
-                                   __ldg(u + os + gx), __ldg(u + on + gx), p, g);
-                }
-#pragma unroll
-                for (int m = 0; m < NG; m++) {
-                    hi[m] = __fmaf_rn(l, g[m], hi[m]);
-                    ab[m] = __fmaf_rn(fabsf(l), fabsf(g[m]), ab[m]);
-                }
-                if (KIND == ST_THERMAL) pacc[q] = __fadd_rn(pacc[q], l);
-            }
-        }
         }
         __syncthreads();
         float *t = cur;
@@ -309,20 +375,20 @@ __global__ void __launch_bounds__(ANT) k_adj2d(const AdjPass a, const __grid_con
     }
 
 #pragma unroll
-    for (int q = 0; q < ACPT; q++) {
-        const int idx = tid + q * ANT, lx = idx % AX, ly = idx / AX;
+    for (int c = 0; c < ACPT; c++) {
+        const int lx = lx0 + (c & 3), ly = ly0 + (c >> 2), idx = ly * AX + lx;
         const int gx = x0 + lx, gy = y0 + ly;
         const bool own = gx < a.nx && gy < a.ny && lx >= ATA && lx < ATA + ACX && ly >= ATA &&
                          ly < ATA + ACY;
         if (own) {
             const long long o = (long long)gy * a.nx + gx;
             a.lam_out[o] = cur[idx];
-            if (KIND == ST_THERMAL) a.gpw[o] = __fmaf_rn(a.k[0], pacc[q], a.gpw[o]);
+            if (KIND == ST_THERMAL) a.gpw[o] = __fmaf_rn(a.k[0], pacc[c], a.gpw[o]);
         }
     }
 
     // block reduction of the (hi, lo) pairs and the magnitudes, fixed order
-    const int lane = tid & 31, wid = tid >> 5;
+    const int wid = tid >> 5;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
