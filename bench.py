@@ -489,13 +489,14 @@ def bench_adjoint(args, ckpt=20):
     bwd = per - fms / args.steps
     value = rk.job_rate(n * w.steps * args.steps, ms) / 1e9
     # algorithmic HBM bytes of the backward: per transposed pass of s steps lambda in + out
-    # (8 B) and the s states (4 B each); per recomputed state one read and one write (8 B); the
-    # checkpoint copy into the state buffer (8 B) per segment; grad_u0 copy (8 B)
+    # (8 B) and the s states (4 B each); per segment the checkpoint copy into the state buffer
+    # (8 B) and one trajectory run that reads it and writes the L-1 recomputed states (4 B
+    # each); grad_u0 copy (8 B)
     nseg = -(-w.steps // ckpt)
     seg_len = [min(w.steps, (k + 1) * ckpt) - k * ckpt for k in range(nseg)]
     bytes_b = 0
     for L in seg_len:
-        bytes_b += n * (8 * (L - 1) + 8)
+        bytes_b += n * (4 * (L - 1) + 4 + 8)   # trajectory: read u_t0, write L-1 states; copy
         left = L
         while left > 0:
             s = min(4, left)
@@ -530,7 +531,7 @@ def bench_adjoint(args, ckpt=20):
            "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 4 * n + 20}
     fwd_T = st.Plan(w.kind, 2, w.nx, w.ny).info()["T"]
     launches = sum(-(-L // fwd_T) for L in seg_len)            # forward passes
-    launches += sum(L - 1 for L in seg_len)                      # recomputed states
+    launches += sum(-(-(L - 1) // 8) for L in seg_len)           # trajectory passes
     launches += sum(-(-L // 4) for L in seg_len) + 1             # transposed passes + final sum
     if rank == 0:
         print(json.dumps({"metric": "stencil GCell/s & GFLOP/s vs roofline", "value": value,

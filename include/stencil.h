@@ -135,6 +135,20 @@ int stencil_plan_create(stencil_plan *out, const stencil_desc *desc);
 int stencil_run(stencil_plan plan, const void *grid_in, void *grid_out, const void *power,
                 const float *coeffs, int nx, int ny, int nz, int steps);
 
+/* Advance grid_in by `steps` Jacobi steps and keep every intermediate state: state t+1 (t =
+ * 0 .. steps-1) lands at states + t * stride (in floats).  The passes are the plan's temporally
+ * blocked ones (Sec. 3.2) with T = 8 steps fused, each fused step's compute block also written
+ * out, so a trajectory costs ceil(steps / 8) launches instead of `steps`.  Used for the
+ * adjoint's recomputation of the forward states between checkpoints.
+ * plan     : a contracted (exact = 0), float32, 2D plan of ST_DIFFUSION or ST_THERMAL, rad <= 1
+ *            (else ST_ERR_UNSUPPORTED).
+ * grid_in  : device, nx*ny floats, read only; may not overlap the states written.
+ * states   : device, steps states of nx*ny floats each, stride >= nx*ny floats apart.
+ * power, coeffs : as for stencil_run.
+ * steps    : >= 1.  Asynchronous on the plan's stream. */
+int stencil_run_trajectory(stencil_plan plan, const void *grid_in, void *states, long long stride,
+                           const void *power, const float *coeffs, int steps);
+
 /* Wait for the plan's stream; returns the first asynchronous error seen (ST_ERR_CUDA,
  * ST_ERR_TIMEOUT) or ST_OK. */
 int stencil_plan_sync(stencil_plan plan);

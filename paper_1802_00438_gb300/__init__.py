@@ -146,6 +146,8 @@ SIGNATURES = {
     "stencil_adjoint_backward": ([_P, _P, _P, _P, _P, _P, _P], _I),
     "stencil_adjoint_sync": ([_P], _I),
     "stencil_adjoint_destroy": ([_P], _I),
+    "stencil_run_trajectory": ([_P, _P, _P, ctypes.c_longlong, _P, ctypes.POINTER(ctypes.c_float), _I],
+                               _I),
     "stencil_tune": ([ctypes.POINTER(stencil_desc), _P, _P, _P, ctypes.POINTER(ctypes.c_float), _I,
                       _I, ctypes.POINTER(stencil_tune_result)], _I),
     "stencil_plan_tuned": ([_P], _I),
@@ -228,6 +230,12 @@ def stencil_run(plan, grid_in, grid_out, power, coeffs, nx, ny, nz, steps):
     k = _coef_array(coeffs)
     _check(lib.stencil_run(plan, _addr(grid_in), _addr(grid_out), _addr(power), k, int(nx),
                            int(ny), int(nz), int(steps)), "stencil_run")
+
+
+def stencil_run_trajectory(plan, grid_in, states, stride, power, coeffs, steps):
+    """Every state of a `steps`-step run: state t+1 at states + t * stride floats."""
+    _check(lib.stencil_run_trajectory(plan, _addr(grid_in), _addr(states), int(stride), _addr(power),
+                                      _coef_array(coeffs), int(steps)), "stencil_run_trajectory")
 
 
 def stencil_plan_sync(plan):
@@ -403,6 +411,13 @@ class Plan:
     def run(self, grid_in, grid_out, coeffs, steps, power=None):
         stencil_run(self.h, grid_in, grid_out, power, coeffs, self.nx, self.ny, self.nz, steps)
         return grid_out
+
+    def trajectory(self, grid_in, states, coeffs, steps, power=None):
+        """Every state of a `steps`-step run into states, shaped (steps, ny, nx): states[t] is
+        the field after t+1 steps."""
+        stencil_run_trajectory(self.h, grid_in, states, self.nx * self.ny * self.nz, power, coeffs,
+                               steps)
+        return states
 
     def sync(self):
         stencil_plan_sync(self.h)

@@ -19,7 +19,8 @@
 // mbarrier completion, the next state's tile in flight while the current step computes);
 // otherwise the kernel reads them with plain loads.  The same pass accumulates the coefficient
 // and power gradients of its compute block from the forward states u_t, which are recomputed
-// from checkpoints every K steps into a K-state buffer (the forward plans of this library, T = 1 per state).  Coefficient gradients
+// from checkpoints every K steps into a K-state buffer (one trajectory run of this library per
+// segment: 8 fused steps per launch, every step written out).  Coefficient gradients
 // are float32 sums in a fixed order: each thread sums its own cells and steps of a pass (at most
 // 64 terms, fused multiply-adds), then blocks and one final kernel combine those partial sums
 // as (hi, lo) pairs with error-free transformations (TwoSum) in a fixed tree, so results are
@@ -494,7 +495,7 @@ int status(cudaError_t e)
 struct stencil_adjoint_s {
     int kind = 0, nx = 0, ny = 0, steps = 0, ckpt = 0, nseg = 0;
     cudaStream_t stream = nullptr;
-    stencil_plan fwd = nullptr, step = nullptr;
+    stencil_plan fwd = nullptr;   // forward runs and the trajectories between checkpoints
     float *ck = nullptr;      // nseg checkpoints: u at 0, K, 2K, ...
     float *seg = nullptr;     // K recomputed states of one segment
     float *lam[2] = {nullptr, nullptr};
@@ -541,10 +542,6 @@ int stencil_adjoint_create(stencil_adjoint *out, int kind, int nx, int ny, int s
     d.storage = ST_F32;
     d.stream = stream;
     rc = stencil_plan_create(&a->fwd, &d);
-    if (rc == ST_OK) {
-        d.force_T = 1;
-        rc = stencil_plan_create(&a->step, &d);
-    }
     const size_t n = (size_t)nx * ny * sizeof(float);
     cudaError_t e = cudaSuccess;
     if (rc == ST_OK && a->nseg > 0) {
@@ -667,9 +664,9 @@ int stencil_adjoint_backward(stencil_adjoint a, const float *grad_out, const flo
         const int t0 = sg * a->ckpt, t1 = std::min(a->steps, t0 + a->ckpt), len = t1 - t0;
         // recompute u_{t0} .. u_{t1-1} into the segment buffer
         e = cudaMemcpyAsync(a->seg, a->ck + sg * cells, n, cudaMemcpyDeviceToDevice, a->stream);
-        for (int k = 1; k < len && e == cudaSuccess; k++) {
-            const int rc = stencil_run(a->step, a->seg + (k - 1) * cells, a->seg + k * cells,
-                                       power, a->coef, a->nx, a->ny, 1, 1);
+        if (len > 1 && e == cudaSuccess) {   // u_{t0+1} .. u_{t1-1}: one trajectory run
+            const int rc = stencil_run_trajectory(a->fwd, a->seg, a->seg + cells, cells, power,
+                                                  a->coef, len - 1);
             if (rc != ST_OK) return rc;
         }
         int t_hi = t1;
@@ -725,7 +722,6 @@ int stencil_adjoint_destroy(stencil_adjoint a)
     if (a->stream) cudaStreamSynchronize(a->stream);
     else cudaDeviceSynchronize();
     if (a->fwd) stencil_plan_destroy(a->fwd);
-    if (a->step) stencil_plan_destroy(a->step);
     if (a->ck) cudaFree(a->ck);
     if (a->seg) cudaFree(a->seg);
     for (float *l : a->lam)

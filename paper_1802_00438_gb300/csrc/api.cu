@@ -55,6 +55,7 @@ struct stencil_plan_s {
     int *err = nullptr;   // device flag set by a kernel whose bounded wait gave up
     double model = 0.0;   // calibrated model's prediction for this plan (1000 steps), GCell/s
     int tuned = 0;        // configuration taken from the tuning cache
+    PassCfg2D traj;       // trajectory passes (stencil_run_trajectory)
     float *src = nullptr;   // contracted float32 Hotspot 2D: the source map p + amb*Rz
     int ntx_star = 0, nty_star = 0;   // star diffusion (rad > 1): tiles along x and y
     int nseg_star = 1, zseg_star = 0; // 3D star: z-segments per tile column, their length
@@ -262,6 +263,34 @@ int prepare2(stencil_plan_s *p, int Tk, PassCfg2D **out)
     return ST_OK;
 }
 
+// Trajectory passes run the in-place T = 8, V = 8 contracted kernel that also writes every
+// fused step; same launch geometry rules as the plan's own passes.
+constexpr int kTrajT = 8;
+
+int prepare_traj(stencil_plan_s *p, PassCfg2D **out)
+{
+    PassCfg2D &c = p->traj;
+    if (!c.ready) {
+        c.shape = Shape2D{p->d.kind, 0, kTrajT, 8, 0,
+                          (p->d.kind == ST_THERMAL ? (int)STOR_SRC : 0) | (int)STOR_ALL};
+        if (!tb2d_available(c.shape)) return ST_ERR_UNSUPPORTED;
+        int bps = 0;
+        cudaError_t e = tb2d_prepare(c.shape, &bps);
+        if (e != cudaSuccess) return map_cuda(e);
+        if (bps < 1) return ST_ERR_UNSUPPORTED;
+        const int cx = tb2d_tile_width(c.shape) - 2 * tb2d_halo(c.shape);
+        c.ntx = (p->d.nx + cx - 1) / cx;
+        c.total = (long long)c.ntx * p->d.ny;
+        const long long ctas = std::min<long long>((long long)p->sms * bps,
+                                                   std::max<long long>(1, c.total / 4));
+        c.rows_per_cta = (c.total + ctas - 1) / ctas;
+        c.ctas = (int)((c.total + c.rows_per_cta - 1) / c.rows_per_cta);
+        c.ready = true;
+    }
+    *out = &c;
+    return ST_OK;
+}
+
 int prepare3(stencil_plan_s *p, int Tk, PassCfg3D **out)
 {
     if ((int)p->cfg3.size() <= Tk) p->cfg3.resize(Tk + 1);
@@ -358,13 +387,17 @@ int flush_timing(stencil_plan_s *p)
     return ST_OK;
 }
 
+// traj (trajectory passes): its configuration, and where the pass's intermediate steps go
 int run_pass2(stencil_plan_s *p, const float *src, long long lds, float *dst, long long ldd,
-              const float *pw, const float *k, int tsteps)
+              const float *pw, const float *k, int tsteps, PassCfg2D *traj = nullptr,
+              float *states = nullptr, long long stride = 0)
 {
-    PassCfg2D *c = nullptr;
-    int rc = prepare2(p, kernel_T_for(p, tsteps), &c);
+    PassCfg2D *c = traj;
+    int rc = traj ? ST_OK : prepare2(p, kernel_T_for(p, tsteps), &c);
     if (rc != ST_OK) return rc;
     Pass2D a = {};
+    a.states = states;
+    a.state_stride = stride;
     a.in = src;
     a.out = dst;
     a.pw = pw;
@@ -384,7 +417,8 @@ int run_pass2(stencil_plan_s *p, const float *src, long long lds, float *dst, lo
     a.kf[6] = -2.0f * k[2];   // Hotspot: -2 Ry (exact)
     if (stor_src_bits(c->shape.stor)) hot_coeffs_src(k, a.kf);
     a.vec_in = ((uintptr_t)src % 16 == 0) && (lds % 4 == 0);
-    a.vec_out = ((uintptr_t)dst % 16 == 0) && (ldd % 4 == 0);
+    a.vec_out = ((uintptr_t)dst % 16 == 0) && (ldd % 4 == 0) &&
+                (!states || ((uintptr_t)states % 16 == 0 && stride % 4 == 0));
     a.vec_pw = pw ? (((uintptr_t)pw % 16 == 0) && (p->d.nx % 4 == 0)) : 0;
     if (p->timing && p->ev_used + 2 > 2 * 1024) {
         rc = flush_timing(p);
@@ -910,6 +944,49 @@ int stencil_run(stencil_plan p, const void *grid_in, void *grid_out, const void 
         else
             e = cudaMemcpyAsync(out, p->scratch, bytes, cudaMemcpyDeviceToDevice, p->stream);
         if (e != cudaSuccess) return map_cuda(e);
+    }
+    return ST_OK;
+}
+
+int stencil_run_trajectory(stencil_plan p, const void *grid_in, void *states, long long stride,
+                           const void *power, const float *coeffs, int steps)
+{
+    if (!p || !grid_in || !states || !coeffs || steps < 1) return ST_ERR_INVALID_ARG;
+    const stencil_desc &d = p->d;
+    if (d.ndim != 2 || d.exact || p->stor || d.rad > 1 || d.kind == ST_DIFFUSION_VAR)
+        return ST_ERR_UNSUPPORTED;
+    const long long n = (long long)d.nx * d.ny;
+    if (stride < n) return ST_ERR_INVALID_ARG;
+    if ((d.kind == ST_THERMAL) != (power != nullptr)) return ST_ERR_INVALID_ARG;
+    const size_t bytes = (size_t)n * sizeof(float);
+    const size_t span = ((size_t)(steps - 1) * stride + n) * sizeof(float);
+    if (ranges_overlap2(grid_in, bytes, states, span)) return ST_ERR_INVALID_ARG;
+    if (power && ranges_overlap2(power, bytes, states, span)) return ST_ERR_INVALID_ARG;
+    if (d.strict && !stable(d, coeffs)) return ST_ERR_UNSTABLE_COEFFS;
+    if (p->sticky != ST_OK) return p->sticky;
+    PassCfg2D *c = nullptr;
+    int rc = prepare_traj(p, &c);
+    if (rc != ST_OK) return rc;
+    const float *pw = static_cast<const float *>(power);
+    if (p->src) {
+        // contracted Hotspot kernels stage p + amb*Rz (Table 2's ambient term folded in)
+        const cudaError_t e = hot_source(pw, d.nx, p->src, d.nx, d.ny, coeffs[4], coeffs[3], p->stream);
+        if (e != cudaSuccess) return map_cuda(e);
+        pw = p->src;
+    }
+    float *st = static_cast<float *>(states);
+    const int passes = (steps + kTrajT - 1) / kTrajT;
+    for (int i = 0; i < passes; i++) {
+        const int ts = std::min(kTrajT, steps - i * kTrajT);
+        const float *src = i == 0 ? static_cast<const float *>(grid_in)
+                                  : st + ((long long)i * kTrajT - 1) * stride;
+        float *dst = st + ((long long)i * kTrajT + ts - 1) * stride;
+        rc = run_pass2(p, src, d.nx, dst, d.nx, pw, coeffs, ts, c,
+                       st + (long long)i * kTrajT * stride, stride);
+        if (rc != ST_OK) {
+            p->sticky = rc;
+            return rc;
+        }
     }
     return ST_OK;
 }

@@ -34,12 +34,16 @@ struct Pass2D {
     float2 *mout;
     const float2 *mpw;
     long long ld_q;                // row pitch of the 16-bit grids, cells (multiple of 8)
+    // trajectory passes (STOR_ALL): step t < tsteps-1 of the pass goes to states + t*state_stride
+    float *states;
+    long long state_stride;
 };
 
 // stor: storage format (0 float32, 1 bf16, 2 fp16) plus 4 when the kernel stages the Hotspot
 // source map p + amb*Rz instead of the power map (every contracted Hotspot plan and batch)
 struct Shape2D { int kind, exact, T, V, W; int stor = 0; };
-enum { STOR_SRC = 4 };
+enum { STOR_SRC = 4,     // Hotspot: the power rows carry amb*Rz (source map)
+       STOR_ALL = 8 };    // every fused step's rows are also written (trajectory passes)
 
 // One pass over many 2D grids (contracted kernels): grids[g] describes grid g's pass (its
 // tile columns ntx, sizes, buffers, coefficients, tsteps); prefix[g] = sum of ntx*ny of the

@@ -2,7 +2,8 @@
 // Exact (Table 2 order, rotating register windows): T in {1,2,4,8}, V = 4, W in {1,4}.
 // Contracted (partial-sum stages, one warp per block): V = 8 for T in {1,2,4,6,8}, V = 4 for
 // T in {1,2,4,8,12}; larger T or V do not fit the register file.  In-place variants (no
-// two-row unroll) for (T, V) = (8, 8) and (12, 4).  16-bit block-coded storage (bf16, fp16)
+// two-row unroll) for (T, V) = (8, 8) and (12, 4), and (8, 8) for trajectory passes that write
+// every fused step.  16-bit block-coded storage (bf16, fp16)
 // for (T, V) in {(4, 4), (8, 4), (8, 8)}.
 #include "tb2d_table.cuh"
 
@@ -16,7 +17,7 @@ const Tb2dEntry tb2d_table_diff[] = {
     STN_TB2F_ENTRY(0, 8, 8), STN_TB2F_ENTRY(0, 6, 8),
     STN_TB2F_ENTRY(0, 1, 4), STN_TB2F_ENTRY(0, 2, 4), STN_TB2F_ENTRY(0, 4, 4),
     STN_TB2F_ENTRY(0, 8, 4), STN_TB2F_ENTRY(0, 12, 4),
-    STN_TB2F1_ENTRY(0, 8, 8), STN_TB2F1_ENTRY(0, 12, 4),
+    STN_TB2F1_ENTRY(0, 8, 8), STN_TB2F1_ENTRY(0, 12, 4), STN_TB2FA_ENTRY(0, 8, 8),
     STN_TB2FQ_ENTRY(0, 4, 4, 1), STN_TB2FQ_ENTRY(0, 8, 4, 1), STN_TB2FQ_ENTRY(0, 8, 8, 1),
     STN_TB2FQ_ENTRY(0, 4, 4, 2), STN_TB2FQ_ENTRY(0, 8, 4, 2), STN_TB2FQ_ENTRY(0, 8, 8, 2),
 };

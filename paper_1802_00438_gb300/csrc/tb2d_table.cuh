@@ -34,6 +34,11 @@ struct Tb2dEntry {
 #define STN_TB2F0_ENTRY(K, T_, V_)                                                           \
     { K, 0, T_, V_, 1, reinterpret_cast<const void *>(&k_tb2f<K, T_, V_, true, 0>),        \
       TB2F<K, T_, V_>::SMEM, 0 }
+// trajectory passes (every fused step's rows written too): in-place partial rows
+#define STN_TB2FA_ENTRY(K, T_, V_)                                                           \
+    { K, 0, T_, V_, 0,                                                                       \
+      reinterpret_cast<const void *>(&k_tb2f<K, T_, V_, false, STN_TB2F_SRC(K) | STOR_ALL>), \
+      TB2F<K, T_, V_, STN_TB2F_SRC(K) | STOR_ALL>::SMEM, STN_TB2F_SRC(K) | STOR_ALL }
 // 16-bit block-coded storage (S = 1 bf16, 2 fp16), two-row unroll
 #define STN_TB2FQ_ENTRY(K, T_, V_, S)                                                        \
     { K, 0, T_, V_, 1,                                                                       \

@@ -45,6 +45,7 @@ enum { STOR_F32 = 0, STOR_BF16 = 1, STOR_F16 = 2 };
 // decode a power row.
 __host__ __device__ constexpr int stor_fmt(int s) { return s & 3; }
 __host__ __device__ constexpr bool stor_src(int s) { return (s & STOR_SRC) != 0; }
+__host__ __device__ constexpr bool stor_all(int s) { return (s & STOR_ALL) != 0; }
 
 template <int KIND, int T, int V, int STOR = STOR_F32>
 struct TB2F {
@@ -197,6 +198,8 @@ struct CtxF {
     int ntx, tx;           // tile columns; my tile column
     int msel;              // which of the three blocks of a loaded row my cells belong to
     float src_add;         // amb * Rz (STOR_SRC, rounded once)
+    float *st_states;      // trajectory passes (STOR_ALL): where step t's rows go
+    long long st_stride;
 };
 
 // my V cells of the ring row at byte address row
@@ -332,6 +335,26 @@ struct RowF {
     int colr;
 };
 
+// Trajectory passes: the row `row` of step t+1 of the pass (stage t's output) into state t,
+// for the steps before the pass's last (whose rows go to the pass output) and the rows of
+// this segment, compute-block cells only.
+template <int V>
+__device__ __forceinline__ void tbf_store_state(const CtxF &c, int t, int row, const float (&v)[V])
+{
+    if (t >= c.tsteps - 1 || row < c.s0 || row >= c.s1) return;
+    float *g = c.st_states + (long long)t * c.st_stride + (long long)row * c.ld_out + c.xt;
+    if (c.st_full) {
+#pragma unroll
+        for (int q = 0; q < V / 4; q++)
+            *reinterpret_cast<float4 *>(g + 4 * q) =
+                make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else if (c.st_any) {
+#pragma unroll
+        for (int j = 0; j < V; j++)
+            if (j >= c.st_lo && j < c.st_hi) g[j] = v[j];
+    }
+}
+
 // One row iteration.  PH selects which of A/B holds P (PH = 0: A) for every stage.
 template <int KIND, int T, int V, int MODE, int PH, bool SWAP, int STOR>
 __device__ __forceinline__ void tbf_iter(const CtxF &c, const CoefF &k,
@@ -382,6 +405,7 @@ __device__ __forceinline__ void tbf_iter(const CtxF &c, const CoefF &k,
     // R0 (ring-relative i), row i-t sits t slots below it
 #pragma unroll
     for (int s = 1; s < T; s++) {
+        if (stor_all(STOR)) tbf_store_state<V>(c, s - 1, R0 - s, out);
 #pragma unroll
         for (int j = 0; j < V; j++) d[j] = out[j];
         const float w_in = __shfl_sync(0xffffffffu, d[V - 1], (c.lane + 31) & 31);
@@ -639,6 +663,8 @@ __device__ __forceinline__ void tbf_range(const Pass2D &p, long long f, const lo
     k.a5 = p.kf[5];   // Hotspot: sdc * Ry
     k.a6 = p.kf[6];   // Hotspot: -2 Ry (source-map kernels: -(2Rx' + 2Ry'))
     c.src_add = __fmul_rn(k.a4, k.a3);   // Hotspot: amb * Rz
+    c.st_states = p.states;
+    c.st_stride = p.state_stride;
 
     while (f < fend) {
         const int tx = (int)(f / p.ny);
