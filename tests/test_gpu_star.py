@@ -79,5 +79,5 @@ def test_star_in_place_and_errors(eng, orc, R):
         eng.Plan(0, 2, 64, 64, rad=5)
     with pytest.raises(eng.StencilError):      # star Hotspot is not defined
         eng.Plan(1, 2, 64, 64, rad=2)
-    with pytest.raises(eng.StencilError):      # 3D star not built
-        eng.Plan(0, 3, 32, 32, 32, rad=2)
+    with pytest.raises(eng.StencilError):      # 2D star tiles are 128 wide
+        eng.Plan(0, 2, 64, 64, rad=2, force_bx=64)
