@@ -801,8 +801,12 @@ static int plan_create(stencil_plan *out, const stencil_desc *desc)
         // tile width 64 (2 cells per lane) or 128 (4 cells per lane), tile height, cells per
         // thread; 64 x 64 with 16 cells per thread is the three-plane-window kernel (exact or
         // contracted), every other shape the partial-sum kernel (contracted)
+        // nothing forced, contracted: 64 x 32 tiles in 8-warp blocks, two per SM (measured on
+        // GB300 against 64 x 64 tiles in 16-warp blocks: 512^3 diffusion 950 vs 918 GCell/s,
+        // 512^2 x 256 Hotspot 784 vs 776)
+        const bool free_tile = !d.exact && !d.force_bx && !d.force_by && !d.force_vec;
         const int bx = d.force_bx ? d.force_bx : 64;
-        const int by = d.force_by ? d.force_by : (bx == 128 ? 32 : 64);
+        const int by = d.force_by ? d.force_by : (bx == 128 || free_tile ? 32 : 64);
         const int cells = d.force_vec ? d.force_vec : (d.exact ? 16 : 8);
         if (bx != 64 && bx != 128) rc = ST_ERR_UNSUPPORTED;
         p->VX3 = bx / 32;
@@ -814,9 +818,9 @@ static int plan_create(stencil_plan *out, const stencil_desc *desc)
             p->alg3 = (p->VX3 == 2 && p->VY == 8 && p->NW == 8) ? 0 : 1;
             if (p->alg3 && d.exact) rc = ST_ERR_UNSUPPORTED;
         }
-        // contracted default: T = 3 (512^3 diffusion and 512^2 x 256 Hotspot measure best at
-        // T = 3 with 4 rows x 2 cells per thread; the x halo is rounded up to 4 anyway)
-        const int want = d.force_T ? d.force_T : (p->alg3 ? 3 : 4);
+        // contracted default: T = 4 for diffusion, 3 for Hotspot (best measured with the
+        // default tiles: 512^3 diffusion T = 2, 3, 4: 838, 912, 950; Hotspot 540, 784, 764)
+        const int want = d.force_T ? d.force_T : (p->alg3 ? (d.kind == ST_DIFFUSION ? 4 : 3) : 4);
         p->T = kernel_T_for(p, want);
         if (p->T == 0 || (d.force_T && p->T != d.force_T)) rc = ST_ERR_UNSUPPORTED;
         PassCfg3D *c = nullptr;

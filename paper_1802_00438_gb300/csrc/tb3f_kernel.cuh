@@ -52,13 +52,16 @@ struct TB3F {
         return sizeof(float) * ((size_t)((pf + 3) + (KIND == KTHERM ? (T > 1 ? T : 2) + pf : 0)) *
                                     PLANE + XCH) + 8 * (pf + 3);
     }
-    // the deepest prefetch (2..5 planes) that fits
-    static constexpr int PF = smem_for(5) <= 227 * 1024 ? 5 : smem_for(4) <= 227 * 1024 ? 4
-                            : smem_for(3) <= 227 * 1024 ? 3 : 2;
+    // blocks of up to 8 warps run two per SM, larger ones one
+    static constexpr int MINB = NT <= 256 ? 2 : 1;
+    // the deepest prefetch (2..5 planes) whose shared memory fits MINB blocks per SM (1 KiB of
+    // each block's share is reserved by the hardware)
+    static constexpr size_t BUDGET = MINB == 2 ? 113 * 1024 : 227 * 1024;
+    static constexpr int PF = smem_for(5) <= BUDGET ? 5 : smem_for(4) <= BUDGET ? 4
+                            : smem_for(3) <= BUDGET ? 3 : 2;
     static constexpr int NBF = PF + 3;
     static constexpr int NBP = KIND == KTHERM ? (T > 1 ? T : 2) + PF : 0;
     static constexpr size_t SMEM = smem_for(PF);
-    static constexpr int MINB = NT <= 256 ? 2 : 1;
     static_assert(CX > 0 && CY > 0, "tile smaller than its halos");
     static_assert(VX == 2 || VX == 4, "cells per lane");
     static_assert(VX * VY <= 32, "store mask");

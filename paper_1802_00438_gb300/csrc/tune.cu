@@ -55,7 +55,7 @@ std::vector<std::array<int, 4>> candidates(const stencil_desc &d)
                 }
             }
     } else {
-        const int shapes[][3] = {{64, 64, 16}, {64, 64, 8}, {64, 64, 4}, {128, 32, 8}};
+        const int shapes[][3] = {{64, 64, 16}, {64, 64, 8}, {64, 64, 4}, {128, 32, 8}, {64, 32, 8}};
         for (const auto &s : shapes)
             for (int T : Ts) c.push_back({T, s[0], s[1], s[2]});
     }

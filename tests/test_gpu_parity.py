@@ -103,22 +103,25 @@ def test_contracted_2d_in_place_rows(eng, orc, kind):
                 assert max_rel(g, o) <= TOL, (nx, ny, steps, "in place")
 
 
-SHAPES_3D = [(64, 16, T) for T in (1, 2, 3, 4)] + [(64, 8, T) for T in (1, 2, 3, 4)] + \
-    [(64, 4, T) for T in (2, 3, 4)] + [(128, 8, T) for T in (2, 3, 4)]
+SHAPES_3D = [(64, 16, T, 0) for T in (1, 2, 3, 4)] + [(64, 8, T, 0) for T in (1, 2, 3, 4)] + \
+    [(64, 4, T, 0) for T in (2, 3, 4)] + [(128, 8, T, 0) for T in (2, 3, 4)] + \
+    [(64, 8, T, 32) for T in (2, 3, 4)]
 
 
 @pytest.mark.parametrize("kind", [0, 1])
-@pytest.mark.parametrize("bx,vec,T", SHAPES_3D)
-def test_contracted_3d(eng, orc, kind, bx, vec, T):
+@pytest.mark.parametrize("bx,vec,T,by", SHAPES_3D)
+def test_contracted_3d(eng, orc, kind, bx, vec, T, by):
     # 64 x 64 tiles: vec 16 = three-plane windows; 8 and 4 = partial sums along z (2 cells x
-    # 4 or 2 rows); 128 x 32 tiles: 4 cells x 2 rows, partial sums
+    # 4 or 2 rows); 128 x 32 tiles: 4 cells x 2 rows, partial sums; 64 x 32 tiles (by = 32):
+    # 2 cells x 4 rows in 8 warps, two blocks per SM
     # rows of a multiple of 4 cells (132, 200) are staged by tensor-map copies, others by cp.async
     for t, (nx, ny, nz) in enumerate(SIZES_3D[:2] + SIZES_3D[3:] + [(203, 150, 37), (132, 70, 21),
                                                                     (200, 33, 17)]):
         w = synth.make(kind, 3, nx, ny, nz, seed=4000 + 43 * t + kind)
         for steps in (1, T + 2, 3 * T + 1):
-            g, info = gpu_run(eng, w, steps, T=T, vec=vec, bx=bx)
+            g, info = gpu_run(eng, w, steps, T=T, vec=vec, bx=bx, by=by)
             assert info["vec"] == vec and info["T"] == T and info["bx"] == bx
+            assert by == 0 or info["by"] == by
             o = orc.run(kind, w.u0, w.coef, steps, w.power)
             assert max_rel(g, o) <= TOL, (nx, ny, nz, steps, max_rel(g, o))
 
