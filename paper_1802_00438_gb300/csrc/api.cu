@@ -1037,7 +1037,7 @@ int stencil_plan_get_info(stencil_plan p, stencil_plan_info *info)
         info->halo = star2d_halo_x(p->d.rad, p->T);
         info->vec = 4;
         info->warps = 16;
-        info->ctas = p->ntx_star * p->nty_star;
+        info->ctas = std::min(p->ntx_star * p->nty_star, p->sms);   // persistent, one per SM
         info->kernel_id = 5;
     } else if (p->d.ndim == 2) {
         PassCfg2D *c = nullptr;

@@ -1,5 +1,7 @@
 // Compiled instances of the 2D star diffusion (radius R in {2, 3, 4}, fused steps T in
 // {1, 2, 4}, exact and contracted) and their dispatch.
+#include <algorithm>
+
 #include "star2d.cuh"
 
 namespace stn {
@@ -58,7 +60,14 @@ cudaError_t star2d_launch(int R, int exact, int T, const PassStar2D &p, const CU
     const StarEntry *e = find(R, exact, T);
     if (!e) return cudaErrorInvalidValue;
     void *args[] = {const_cast<PassStar2D *>(&p), const_cast<CUtensorMap *>(&tin)};
-    return cudaLaunchKernel(e->fn, dim3((unsigned)((long long)p.ntx * p.nty)), dim3(32 * SNW), args,
+    // persistent blocks, one per SM (three tile buffers fill its shared memory)
+    int dev = 0, sms = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess) return err;
+    const long long tiles = (long long)p.ntx * p.nty;
+    const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(tiles, sms));
+    return cudaLaunchKernel(e->fn, dim3(grid), dim3(32 * SNW), args,
                             e->smem, st);
 }
 
