@@ -733,6 +733,12 @@ static int plan_create(stencil_plan *out, const stencil_desc *desc)
             if (d.exact && d.nx >= 512) p->W = 4;
         }
         if (!d.exact && d.force_by == 1) p->W = 0;   // in-place partial-row variant
+        if (p->stor && !d.force_T && !d.force_vec && !d.force_bx && !d.force_by) {
+            // 16-bit storage, nothing forced: T = 8, 8 cells per lane, rows in place (measured
+            // on 16384^2: Hotspot 1544 GCell/s against 1480 for V = 4 two-row; diffusion 2721)
+            p->V = 8;
+            p->W = 0;
+        }
         if (!d.exact && !var && !p->stor && !d.force_T && !d.force_vec && !d.force_bx && !d.force_by) {
             // contracted, nothing forced: the compiled (T, V, variant) the model rates best
             const Cand2D cands[] = {{4, 4, 1}, {8, 4, 1}, {12, 4, 1}, {4, 8, 1}, {6, 8, 1},

@@ -4,7 +4,7 @@
 // T in {1,2,4,8,12}; larger T or V do not fit the register file.  In-place variants (no
 // two-row unroll) for (T, V) = (8, 8) and (12, 4), and (8, 8) for trajectory passes that write
 // every fused step.  16-bit block-coded storage (bf16, fp16)
-// for (T, V) in {(4, 4), (8, 4), (8, 8)}.
+// for (T, V) in {(1, 4), (2, 4), (4, 4), (8, 4), (8, 8)}, and (8, 8) with in-place rows.
 #include "tb2d_table.cuh"
 
 namespace stn {
@@ -20,6 +20,9 @@ const Tb2dEntry tb2d_table_diff[] = {
     STN_TB2F1_ENTRY(0, 8, 8), STN_TB2F1_ENTRY(0, 12, 4), STN_TB2FA_ENTRY(0, 8, 8),
     STN_TB2FQ_ENTRY(0, 4, 4, 1), STN_TB2FQ_ENTRY(0, 8, 4, 1), STN_TB2FQ_ENTRY(0, 8, 8, 1),
     STN_TB2FQ_ENTRY(0, 4, 4, 2), STN_TB2FQ_ENTRY(0, 8, 4, 2), STN_TB2FQ_ENTRY(0, 8, 8, 2),
+    STN_TB2FQ1_ENTRY(0, 8, 8, 1), STN_TB2FQ1_ENTRY(0, 8, 8, 2),
+    STN_TB2FQ_ENTRY(0, 1, 4, 1), STN_TB2FQ_ENTRY(0, 2, 4, 1), STN_TB2FQ_ENTRY(0, 1, 4, 2),
+    STN_TB2FQ_ENTRY(0, 2, 4, 2),
 };
 const int tb2d_table_diff_n = sizeof(tb2d_table_diff) / sizeof(tb2d_table_diff[0]);
 

@@ -45,6 +45,12 @@ struct Tb2dEntry {
       reinterpret_cast<const void *>(&k_tb2f<K, T_, V_, true, (S) | STN_TB2F_SRC(K)>),     \
       TB2F<K, T_, V_, (S) | STN_TB2F_SRC(K)>::SMEM, (S) | STN_TB2F_SRC(K) }
 
+// 16-bit block-coded storage, partial rows updated in place (W = 0 marker)
+#define STN_TB2FQ1_ENTRY(K, T_, V_, S)                                                       \
+    { K, 0, T_, V_, 0,                                                                       \
+      reinterpret_cast<const void *>(&k_tb2f<K, T_, V_, false, (S) | STN_TB2F_SRC(K)>),    \
+      TB2F<K, T_, V_, (S) | STN_TB2F_SRC(K)>::SMEM, (S) | STN_TB2F_SRC(K) }
+
 extern const Tb2dEntry tb2d_table_diff[];
 extern const int tb2d_table_diff_n;
 extern const Tb2dEntry tb2d_table_therm[];

@@ -3,9 +3,10 @@
 // Contracted (partial-sum stages, one warp per block): V = 8 for T in {1,2,4,6,8}, V = 4 for
 // T in {1,2,4,8,12}; larger T or V do not fit the register file.  In-place variants (no
 // two-row unroll) for (T, V) = (8, 8) and (12, 4), and (8, 8) for trajectory passes that write
-// every fused step.  16-bit block-coded storage (bf16, fp16)
-// for (T, V) in {(4, 4), (8, 4), (8, 8)}.  All of these read the power map with amb*Rz folded
-// in; the V = 4 two-row family also comes with the plain power map (allocation-free entry).
+// every fused step.  16-bit block-coded storage (bf16, fp16) for (T, V) in {(1, 4), (2, 4),
+// (4, 4), (8, 4), (8, 8)}, and (8, 8) with in-place rows.  All of these read the power map
+// with amb*Rz folded in; the V = 4 two-row family also comes with the plain power map
+// (allocation-free entry).
 #include "tb2d_table.cuh"
 
 namespace stn {
@@ -23,6 +24,9 @@ const Tb2dEntry tb2d_table_therm[] = {
     STN_TB2F0_ENTRY(1, 8, 4), STN_TB2F0_ENTRY(1, 12, 4),
     STN_TB2FQ_ENTRY(1, 4, 4, 1), STN_TB2FQ_ENTRY(1, 8, 4, 1), STN_TB2FQ_ENTRY(1, 8, 8, 1),
     STN_TB2FQ_ENTRY(1, 4, 4, 2), STN_TB2FQ_ENTRY(1, 8, 4, 2), STN_TB2FQ_ENTRY(1, 8, 8, 2),
+    STN_TB2FQ1_ENTRY(1, 8, 8, 1), STN_TB2FQ1_ENTRY(1, 8, 8, 2),
+    STN_TB2FQ_ENTRY(1, 1, 4, 1), STN_TB2FQ_ENTRY(1, 2, 4, 1), STN_TB2FQ_ENTRY(1, 1, 4, 2),
+    STN_TB2FQ_ENTRY(1, 2, 4, 2),
 };
 const int tb2d_table_therm_n = sizeof(tb2d_table_therm) / sizeof(tb2d_table_therm[0]);
 

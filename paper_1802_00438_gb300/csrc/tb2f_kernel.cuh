@@ -67,6 +67,9 @@ struct TB2F {
     static constexpr size_t SMEM = (size_t)(NBF + NBPX) * ROWB +
                                    (size_t)NBR * RAWB * (KIND == KTHERM ? 2 : 1);
     static_assert(V % 4 == 0 && V <= 8, "V must be 4 or 8");
+    // 16-bit storage: a lane decodes its V cells with one block code, so block boundaries
+    // (every CX cells from the tile's first compute cell, H cells in) must fall between lanes
+    static_assert(stor_fmt(STOR) == STOR_F32 || H % V == 0, "16-bit blocks split a lane's cells");
     static_assert(CX > 0, "tile narrower than its halos");
 };
 

@@ -51,7 +51,7 @@ std::vector<std::array<int, 4>> candidates(const stencil_desc &d)
                     for (int bx : {128, 512}) c.push_back({T, bx, 0, 4});
                 } else {
                     c.push_back({T, 0, 0, V});
-                    if (d.storage == ST_F32) c.push_back({T, 0, 1, V});   // in-place rows
+                    c.push_back({T, 0, 1, V});   // in-place rows
                 }
             }
     } else {
