@@ -53,16 +53,19 @@ struct TB2F {
     static constexpr int H = (T + 3) / 4 * 4;
     static constexpr int CX = BX - 2 * H;
     static constexpr int PF = 4;                                    // rows requested ahead
-    static constexpr int NBF = PF + 3;                              // field rows i-2 .. i+PF
+    // 16-bit storage: the rows in flight wait in the staging rings, so the float rings hold
+    // only the rows in use (decoded on arrival); float32 rows land in the float rings directly
+    static constexpr bool Q16 = stor_fmt(STOR) != STOR_F32;
+    static constexpr int NBF = Q16 ? 3 : PF + 3;                    // field rows i-2 .. i(+PF)
     static constexpr int PW = T > 1 ? T : 2;                        // power rows read per row:
                                                                     // i-PW+1 .. i
-    static constexpr int NBP = (KIND == KTHERM) ? (PW + PF + 1) : 0; // power ring rows
+    static constexpr int NBP = (KIND == KTHERM) ? (Q16 ? PW : PW + PF + 1) : 0;   // power ring
     static constexpr int NBPX = (KIND == KTHERM) ? (NBP + PW - 1) : 0;  // incl. mirror
     static constexpr int NS = T > 1 ? T - 1 : 1;                    // partial-sum stages
     static constexpr int ROWB = BX * 4;                             // bytes per ring row
     // 16-bit storage: rows arrive raw (32-byte header of block codes + 2 bytes per cell) in a
     // staging ring of PF+1 rows per input and are decoded into the float rings once
-    static constexpr int NBR = (stor_fmt(STOR) != STOR_F32) ? PF + 1 : 0;
+    static constexpr int NBR = Q16 ? PF + 1 : 0;
     static constexpr int RAWB = 32 + 2 * BX;
     static constexpr size_t SMEM = (size_t)(NBF + NBPX) * ROWB +
                                    (size_t)NBR * RAWB * (KIND == KTHERM ? 2 : 1);
@@ -579,15 +582,15 @@ __device__ __forceinline__ void tbf_step(const CtxF &c, const CoefF &k,
         }
     }
     __syncwarp();
-    int lf = r.rf + C::PF;
-    lf -= (lf >= C::NBF) ? C::NBF : 0;
-    int lp = 0;
-    if (KIND == KTHERM) {
-        lp = r.rp + C::PF;
-        lp -= (lp >= C::NBP) ? C::NBP : 0;
-    }
-    int lr = 0;
-    if (stor_fmt(STOR) != STOR_F32) {
+    int lf = 0, lp = 0, lr = 0;   // slots of row i+PF: float rings, or the staging ring
+    if (!C::Q16) {
+        lf = r.rf + C::PF;
+        lf -= (lf >= C::NBF) ? C::NBF : 0;
+        if (KIND == KTHERM) {
+            lp = r.rp + C::PF;
+            lp -= (lp >= C::NBP) ? C::NBP : 0;
+        }
+    } else {
         lr = r.rr + C::PF;
         lr -= (lr >= C::NBR) ? C::NBR : 0;
     }
@@ -728,7 +731,7 @@ __device__ __forceinline__ void tbf_range(const Pass2D &p, long long f, const lo
 #pragma unroll 1
         for (int j = 0; j < C::PF; j++) {
             if (c.y_start + j <= c.last_row) {
-                tbf_queue<KIND, T, V, STOR>(c, r, j, (KIND == KTHERM) ? j : 0, j);
+                tbf_queue<KIND, T, V, STOR>(c, r, C::Q16 ? 0 : j, (KIND == KTHERM && !C::Q16) ? j : 0, j);
                 if (stor_fmt(STOR) == STOR_F32) {
                     r.gF += c.ld_in;
                     if (KIND == KTHERM) r.gP += c.ld_pw;
