@@ -532,7 +532,7 @@ def bench_adjoint(args, ckpt=20):
     fwd_T = st.Plan(w.kind, 2, w.nx, w.ny).info()["T"]
     launches = sum(-(-L // fwd_T) for L in seg_len)            # forward passes
     launches += sum(-(-(L - 1) // 8) for L in seg_len)           # trajectory passes
-    launches += sum(-(-L // 4) for L in seg_len) + 1             # transposed passes + final sum
+    launches += sum(-(-L // 4) for L in seg_len) + 2             # transposed passes + 2-level sum
     if rank == 0:
         print(json.dumps({"metric": "stencil GCell/s & GFLOP/s vs roofline", "value": value,
                           "unit": "GCell/s", "n_gpus": world, "steps": args.steps,

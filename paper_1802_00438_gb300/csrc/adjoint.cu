@@ -12,17 +12,17 @@
 // that the forward step folded into cell j (x = 0: ww, x = nx-1: we, y = 0: wn, y = ny-1: ws).
 //
 // GPU design.  The reverse sweep is temporally blocked like the forward sweep (Sec. 3.2): a
-// pass loads a 128 x 64 tile of lambda_{t+TA} with a halo of TA cells into shared memory and
+// pass loads a 128 x 32 tile of lambda_{t+TA} with a halo of TA cells into shared memory and
 // applies TA transposed steps there (ping-pong buffers, redundant halo work, only the compute
 // block written).  With rows on 16-byte boundaries the lambda tile, the power tile and the
 // state tile u_t of every fused step arrive by tensor-map bulk copies (one elected thread,
-// mbarrier completion, the next state's tile in flight while the current step computes);
+// mbarrier completion, every step's state tile requested when the tile starts);
 // otherwise the kernel reads them with plain loads.  The same pass accumulates the coefficient
 // and power gradients of its compute block from the forward states u_t, which are recomputed
 // from checkpoints every K steps into a K-state buffer (one trajectory run of this library per
 // segment: 8 fused steps per launch, every step written out).  Coefficient gradients
 // are float32 sums in a fixed order: each thread sums its own cells and steps of a pass (at most
-// 64 terms, fused multiply-adds), then blocks and one final kernel combine those partial sums
+// 64 terms, fused multiply-adds), then blocks and two final launches combine those partial sums
 // as (hi, lo) pairs with error-free transformations (TwoSum) in a fixed tree, so results are
 // deterministic and the rounding of the combination is negligible beside the per-thread sums.  Alongside each gradient the
 // same reduction yields sum |term|, the scale its rounding error is relative to.
@@ -40,12 +40,21 @@
 
 namespace {
 
-constexpr int AX = 128, AY = 64, ANT = 512, ACPT = AX * AY / ANT;   // tile, threads, cells/thread
+// 128 x 32 tiles in 256-thread blocks, two blocks per SM: one block's copies land while the
+// other computes (128 x 64 tiles in one 512-thread block per SM left HBM idle between tiles)
+constexpr int AX = 128, AY = 32, ANT = 256, ACPT = AX * AY / ANT;   // tile, threads, cells/thread
 static_assert(AX == 4 * 32 && AY == 4 * (ANT / 32), "a lane owns 4 x 4 cells of the tile");
 constexpr int ATA = 4;                                                // fused adjoint steps
 constexpr int ACX = AX - 2 * ATA, ACY = AY - 2 * ATA;                // compute block
 constexpr int NG = 5;                                                 // coefficients
 constexpr int NPART = 3 * NG;                                         // (hi, lo, |.|) x 5
+
+// dynamic shared memory of a pass: two lambda tiles, one state tile per fused step, and the
+// power tile for Hotspot (7 x 16 KiB: two blocks and their static arrays fit in one SM)
+constexpr int adj_smem(int kind)
+{
+    return (2 + ATA + (kind == ST_THERMAL ? 1 : 0)) * AX * AY * (int)sizeof(float);
+}
 
 struct AdjPass {
     const float *lam_in;     // lambda_{t_hi}
@@ -236,17 +245,17 @@ __device__ __forceinline__ void adj_block_interior(const AdjPass &a, int lane, i
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(ANT) k_adj2d(const AdjPass a, const __grid_constant__ CUtensorMap tl,
+__global__ void __launch_bounds__(ANT, 2) k_adj2d(const AdjPass a, const __grid_constant__ CUtensorMap tl,
                                                const __grid_constant__ CUtensorMap tu,
                                                const __grid_constant__ CUtensorMap tp)
 {
     extern __shared__ __align__(128) float sm[];
     constexpr uint32_t TILE_B = 4u * AX * AY;
     float *buf0 = sm, *buf1 = sm + AX * AY;
-    float *ubuf = sm + 2 * AX * AY;          // two state tiles
-    float *ptile = sm + 4 * AX * AY;         // power tile (Hotspot)
+    float *ubuf = sm + 2 * AX * AY;             // one state tile per fused step
+    float *ptile = sm + (2 + ATA) * AX * AY;    // power tile (Hotspot)
     __shared__ float red[ANT / 32][NPART];
-    __shared__ __align__(8) uint64_t bars[4];   // lambda, state tile 0, state tile 1, power
+    __shared__ __align__(8) uint64_t bars[2 + ATA];   // lambda, power, state tiles 0 .. ATA-1
     const int tid = threadIdx.x;
     const int tx = blockIdx.x % a.ntx, ty = blockIdx.x / a.ntx;
     const int x0 = tx * ACX - ATA, y0 = ty * ACY - ATA;
@@ -255,27 +264,37 @@ __global__ void __launch_bounds__(ANT) k_adj2d(const AdjPass a, const __grid_con
     // block-uniform: the whole tile is in the grid and no cell of it lies on the grid's edge
     const bool interior = tma && x0 >= 1 && y0 >= 1 && x0 + AX <= a.nx - 1 && y0 + AY <= a.ny - 1;
 
+    // every copy of the tile is requested at once (lambda, power and the state tile of each
+    // fused step, each on its own barrier, used once): the steps then wait only for their own
+    // state tile, and one block keeps the whole tile's bytes in flight
+    const auto drain = [&](int j0) {   // after a failed wait: let the copies in flight land
+        for (int j = j0; j < a.nsteps; j++) (void)bar_wait(b0 + 8u * (2 + j), 0);
+    };
     if (tma) {
         if (tid == 0) {
-            for (int b = 0; b < 4; b++) bar_init(b0 + 8u * b);
+            for (int b = 0; b < 2 + ATA; b++) bar_init(b0 + 8u * b);
             asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             bar_expect(b0, TILE_B);
             tile_copy(sm32(buf0), &tl, x0, y0, 0, b0);
-            bar_expect(b0 + 8u, TILE_B);
-            tile_copy(sm32(ubuf), &tu, x0, y0, a.k_hi, b0 + 8u);
             if (KIND == ST_THERMAL) {
-                bar_expect(b0 + 24u, TILE_B);
-                tile_copy(sm32(ptile), &tp, x0, y0, 0, b0 + 24u);
+                bar_expect(b0 + 8u, TILE_B);
+                tile_copy(sm32(ptile), &tp, x0, y0, 0, b0 + 8u);
+            }
+            for (int j = 0; j < a.nsteps; j++) {
+                bar_expect(b0 + 8u * (2 + j), TILE_B);
+                tile_copy(sm32(ubuf + j * AX * AY), &tu, x0, y0, a.k_hi - j, b0 + 8u * (2 + j));
             }
         }
         __syncthreads();   // barriers initialised before anyone polls them
         bool ok = bar_wait(b0, 0);
-        if (KIND == ST_THERMAL) ok = bar_wait(b0 + 24u, 0) && ok;
+        if (KIND == ST_THERMAL) ok = bar_wait(b0 + 8u, 0) && ok;
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 atomicExch(a.err, 1);
-                (void)bar_wait(b0 + 8u, 0);   // the first state tile may still be in flight
+                (void)bar_wait(b0, 0);
+                if (KIND == ST_THERMAL) (void)bar_wait(b0 + 8u, 0);
+                drain(0);
             }
             return;
         }
@@ -300,20 +319,14 @@ __global__ void __launch_bounds__(ANT) k_adj2d(const AdjPass a, const __grid_con
     float *cur = buf0, *nxt = buf1;
     for (int j = 0; j < a.nsteps; j++) {
         const float *u = a.states + (long long)(a.k_hi - j) * a.n;   // u_t, t = t_hi - 1 - j
-        const float *ut = ubuf + (j & 1) * AX * AY;                  // its tile (staged path)
+        const float *ut = ubuf + j * AX * AY;                        // its tile (staged path)
         if (tma) {
-            if (tid == 0 && j + 1 < a.nsteps) {
-                // the other state tile was last read in step j-1, before the barrier below it
-                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                const uint32_t bn = b0 + 8u * (1 + ((j + 1) & 1));
-                bar_expect(bn, TILE_B);
-                tile_copy(sm32(ubuf + ((j + 1) & 1) * AX * AY), &tu, x0, y0, a.k_hi - j - 1, bn);
-            }
-            const bool ok = bar_wait(b0 + 8u * (1 + (j & 1)), (j >> 1) & 1);
+            const bool ok = bar_wait(b0 + 8u * (2 + j), 0);
             if (__syncthreads_or(!ok)) {
-                if (tid == 0) atomicExch(a.err, 1);
-                if (tid == 0 && j + 1 < a.nsteps)
-                    (void)bar_wait(b0 + 8u * (1 + ((j + 1) & 1)), ((j + 1) >> 1) & 1);
+                if (tid == 0) {
+                    atomicExch(a.err, 1);
+                    drain(j);
+                }
                 return;
             }
         }
@@ -436,16 +449,23 @@ __global__ void __launch_bounds__(ANT) k_adj2d(const AdjPass a, const __grid_con
     }
 }
 
-// Combine `count` partial triples per coefficient in a fixed order: thread t takes entries
-// t, t + 256, ... sequentially, then a fixed shuffle / shared-memory tree.
+// Combine partial triples per coefficient in a fixed order, in two launches: block b of the
+// first takes the `chunk` entries from b * chunk on and writes one triple to out[b]; the second
+// (one block, out == nullptr) combines those and writes the gradients.  Within a block thread
+// t takes entries t, t + 256, ... sequentially, then a fixed shuffle / shared-memory tree.  The
+// partition depends only on the entry count, so the result is deterministic.
+constexpr int ADJ_SUM_BLOCKS = 256;   // blocks of the first launch, at most
+
 __global__ void __launch_bounds__(256) k_adj_final(const float *partials, long long count,
-                                                   float *grad, float *grad_abs)
+                                                   long long chunk, float *out, float *grad,
+                                                   float *grad_abs)
 {
     __shared__ float red[8][NPART];
     float hi[NG], lo[NG], ab[NG];
 #pragma unroll
     for (int m = 0; m < NG; m++) hi[m] = lo[m] = ab[m] = 0.f;
-    for (long long i = threadIdx.x; i < count; i += blockDim.x)
+    const long long i0 = (long long)blockIdx.x * chunk, i1 = min(count, i0 + chunk);
+    for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x)
 #pragma unroll
         for (int m = 0; m < NG; m++) {
             add_pair(hi[m], lo[m], partials[i * NPART + 3 * m], partials[i * NPART + 3 * m + 1]);
@@ -477,8 +497,14 @@ __global__ void __launch_bounds__(256) k_adj_final(const float *partials, long l
                 add_pair(h, l, red[w][3 * m], red[w][3 * m + 1]);
                 s = __fadd_rn(s, red[w][3 * m + 2]);
             }
-            grad[m] = __fadd_rn(h, l);
-            if (grad_abs) grad_abs[m] = s;
+            if (out) {
+                out[(long long)blockIdx.x * NPART + 3 * m] = h;
+                out[(long long)blockIdx.x * NPART + 3 * m + 1] = l;
+                out[(long long)blockIdx.x * NPART + 3 * m + 2] = s;
+            } else {
+                grad[m] = __fadd_rn(h, l);
+                if (grad_abs) grad_abs[m] = s;
+            }
         }
     }
 }
@@ -550,16 +576,18 @@ int stencil_adjoint_create(stencil_adjoint *out, int kind, int nx, int ny, int s
         if (e == cudaSuccess) e = cudaMalloc(&a->lam[0], n);
         if (e == cudaSuccess) e = cudaMalloc(&a->lam[1], n);
         if (e == cudaSuccess)
-            e = cudaMalloc(&a->partials, sizeof(float) * NPART * (size_t)(a->blocks * a->passes));
+            e = cudaMalloc(&a->partials, sizeof(float) * NPART *
+                                             (size_t)(a->blocks * a->passes + ADJ_SUM_BLOCKS));
         if (e == cudaSuccess) e = cudaMalloc(&a->err, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(a->err, 0, sizeof(int));
         if (e == cudaSuccess) {
-            const int smem = 5 * AX * AY * (int)sizeof(float);
             e = cudaFuncSetAttribute(k_adj2d<ST_DIFFUSION>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     adj_smem(ST_DIFFUSION));
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(k_adj2d<ST_THERMAL>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         adj_smem(ST_THERMAL));
         }
         if (e != cudaSuccess) rc = status(e);
     }
@@ -656,7 +684,7 @@ int stencil_adjoint_backward(stencil_adjoint a, const float *grad_out, const flo
     if (tma && power) tma = stn::tma3d_encode(&mp.in, power, a->nx, a->ny, 1, AX, AY);
     p.use_tma = tma ? 1 : 0;
     p.err = a->err;
-    const int smem = (a->kind == ST_THERMAL ? 5 : 4) * AX * AY * (int)sizeof(float);
+    const int smem = adj_smem(a->kind);
     const float *lin = grad_out;
     int which = 0;
     long long pass = 0;
@@ -694,9 +722,18 @@ int stencil_adjoint_backward(stencil_adjoint a, const float *grad_out, const flo
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(grad_u0, lin, n, cudaMemcpyDeviceToDevice, a->stream);
     if (e == cudaSuccess) {
-        k_adj_final<<<1, 256, 0, a->stream>>>(a->partials, pass * a->blocks, grad_coeffs,
-                                              grad_coeffs_abs);
+        const long long count = pass * a->blocks;
+        const long long chunk = std::max<long long>(1, (count + ADJ_SUM_BLOCKS - 1) / ADJ_SUM_BLOCKS);
+        const long long nb = (count + chunk - 1) / chunk;   // <= ADJ_SUM_BLOCKS
+        float *stage = a->partials + (size_t)a->blocks * a->passes * NPART;
+        k_adj_final<<<(unsigned)std::max<long long>(nb, 1), 256, 0, a->stream>>>(
+            a->partials, count, chunk, stage, nullptr, nullptr);
         e = cudaGetLastError();
+        if (e == cudaSuccess) {
+            k_adj_final<<<1, 256, 0, a->stream>>>(stage, nb, std::max<long long>(nb, 1), nullptr,
+                                                  grad_coeffs, grad_coeffs_abs);
+            e = cudaGetLastError();
+        }
     }
     return status(e);
 }
