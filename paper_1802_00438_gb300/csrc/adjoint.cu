@@ -160,7 +160,7 @@ __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cas
 // One transposed step on my 4 x 4 cells of a tile inside the grid and off its edges: the
 // rows by 16-byte loads, the x-neighbours across lanes by shuffles; per cell the operations
 // and their order are those of the general path.
-template <int KIND>
+template <int KIND, bool ABS>
 __device__ __forceinline__ void adj_block_interior(const AdjPass &a, int lane, int ly0,
                                                    const float *cur, float *nxt, const float *ut,
                                                    const float *ptile, float (&hi)[NG],
@@ -236,7 +236,7 @@ __device__ __forceinline__ void adj_block_interior(const AdjPass &a, int lane, i
 #pragma unroll
                 for (int m = 0; m < NG; m++) {
                     hi[m] = __fmaf_rn(l, g[m], hi[m]);
-                    ab[m] = __fmaf_rn(fabsf(l), fabsf(g[m]), ab[m]);
+                    if (ABS) ab[m] = __fmaf_rn(fabsf(l), fabsf(g[m]), ab[m]);
                 }
                 if (KIND == ST_THERMAL) pacc[4 * r + j] = __fadd_rn(pacc[4 * r + j], l);
             }
@@ -244,7 +244,9 @@ __device__ __forceinline__ void adj_block_interior(const AdjPass &a, int lane, i
     }
 }
 
-template <int KIND>
+// ABS: also accumulate sum |term| per coefficient (only when the caller asks for it; the
+// gradients themselves are the same sums in the same order either way)
+template <int KIND, bool ABS>
 __global__ void __launch_bounds__(ANT, 2) k_adj2d(const AdjPass a, const __grid_constant__ CUtensorMap tl,
                                                const __grid_constant__ CUtensorMap tu,
                                                const __grid_constant__ CUtensorMap tp)
@@ -331,7 +333,7 @@ __global__ void __launch_bounds__(ANT, 2) k_adj2d(const AdjPass a, const __grid_
             }
         }
         if (interior) {
-            adj_block_interior<KIND>(a, lane, ly0, cur, nxt, ut, ptile, hi, ab, pacc);
+            adj_block_interior<KIND, ABS>(a, lane, ly0, cur, nxt, ut, ptile, hi, ab, pacc);
         } else {
 #pragma unroll
             for (int c = 0; c < ACPT; c++) {
@@ -376,7 +378,7 @@ __global__ void __launch_bounds__(ANT, 2) k_adj2d(const AdjPass a, const __grid_
 #pragma unroll
                     for (int m = 0; m < NG; m++) {
                         hi[m] = __fmaf_rn(l, g[m], hi[m]);
-                        ab[m] = __fmaf_rn(fabsf(l), fabsf(g[m]), ab[m]);
+                        if (ABS) ab[m] = __fmaf_rn(fabsf(l), fabsf(g[m]), ab[m]);
                     }
                     if (KIND == ST_THERMAL) pacc[c] = __fadd_rn(pacc[c], l);
                 }
@@ -580,15 +582,22 @@ int stencil_adjoint_create(stencil_adjoint *out, int kind, int nx, int ny, int s
                                              (size_t)(a->blocks * a->passes + ADJ_SUM_BLOCKS));
         if (e == cudaSuccess) e = cudaMalloc(&a->err, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(a->err, 0, sizeof(int));
-        if (e == cudaSuccess) {
-            e = cudaFuncSetAttribute(k_adj2d<ST_DIFFUSION>,
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_adj2d<ST_DIFFUSION, false>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      adj_smem(ST_DIFFUSION));
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(k_adj2d<ST_THERMAL>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         adj_smem(ST_THERMAL));
-        }
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_adj2d<ST_DIFFUSION, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     adj_smem(ST_DIFFUSION));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_adj2d<ST_THERMAL, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     adj_smem(ST_THERMAL));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_adj2d<ST_THERMAL, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     adj_smem(ST_THERMAL));
         if (e != cudaSuccess) rc = status(e);
     }
     if (rc != ST_OK) {
@@ -707,12 +716,19 @@ int stencil_adjoint_backward(stencil_adjoint a, const float *grad_out, const flo
             p.nsteps = ns;
             p.partials = a->partials + (size_t)pass * a->blocks * NPART;
             const CUtensorMap &tl = lin == grad_out ? mo.in : (lin == a->lam[0] ? m0.in : m1.in);
-            if (a->kind == ST_DIFFUSION)
-                k_adj2d<ST_DIFFUSION><<<(unsigned)a->blocks, ANT, smem, a->stream>>>(p, tl, ms.in,
-                                                                                    mp.in);
-            else
-                k_adj2d<ST_THERMAL><<<(unsigned)a->blocks, ANT, smem, a->stream>>>(p, tl, ms.in,
-                                                                                  mp.in);
+            const bool abs_sums = grad_coeffs_abs != nullptr;
+            const dim3 grid((unsigned)a->blocks);
+            if (a->kind == ST_DIFFUSION) {
+                if (abs_sums)
+                    k_adj2d<ST_DIFFUSION, true><<<grid, ANT, smem, a->stream>>>(p, tl, ms.in, mp.in);
+                else
+                    k_adj2d<ST_DIFFUSION, false><<<grid, ANT, smem, a->stream>>>(p, tl, ms.in, mp.in);
+            } else {
+                if (abs_sums)
+                    k_adj2d<ST_THERMAL, true><<<grid, ANT, smem, a->stream>>>(p, tl, ms.in, mp.in);
+                else
+                    k_adj2d<ST_THERMAL, false><<<grid, ANT, smem, a->stream>>>(p, tl, ms.in, mp.in);
+            }
             e = cudaGetLastError();
             lin = a->lam[which];
             which ^= 1;

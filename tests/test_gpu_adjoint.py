@@ -137,6 +137,30 @@ def test_adjoint_staged_and_plain_paths_agree_bitwise(eng, orc, kind):
 
 
 @pytest.mark.parametrize("kind", [0, 1])
+def test_adjoint_abs_sums_leave_gradients_unchanged(eng, orc, kind):
+    """The transposed pass accumulates sum |term| only when the caller asks for it; the
+    gradients are the same sums in the same order either way: equal bits."""
+    import torch
+    nx, ny, steps = 530, 270, 11
+    w = synth.make(kind, 2, nx, ny, steps=steps, seed=7300 + kind)
+    wt = synth.loss_weights(7301, w.shape)
+    u0 = torch.from_numpy(np.ascontiguousarray(w.u0)).cuda()
+    pw = None if w.power is None else torch.from_numpy(np.ascontiguousarray(w.power)).cuda()
+    g = torch.from_numpy(np.ascontiguousarray(wt)).cuda()
+    res = []
+    for with_abs in (True, False):
+        adj = eng.Adjoint(w.kind, nx, ny, steps, 4)
+        adj.forward(u0, w.coef, pw)
+        gu, gk, gp, ga = adj.backward(g, pw, with_abs=with_abs)
+        torch.cuda.synchronize()
+        adj.close()
+        assert (ga is not None) == with_abs
+        res.append([t.cpu().numpy() for t in (gu, gk) + ((gp,) if gp is not None else ())])
+    for a, b in zip(*res):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
 def test_adjoint_no_cancellation_is_tight(eng, orc, kind):
     """With w >= 0 every diffusion term is non-negative (lambda >= 0, u >= 0): the coefficient
     gradients must then match to the growth bound relative to their own size."""
