@@ -157,14 +157,17 @@ __device__ __forceinline__ void dfdtheta(const AdjPass &a, float c, float w, flo
 // path accumulates the same terms in the same order.
 __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 
-// One transposed step on my 4 x 4 cells of a tile inside the grid and off its edges: the
-// rows by 16-byte loads, the x-neighbours across lanes by shuffles; per cell the operations
-// and their order are those of the general path.
-template <int KIND, bool ABS>
-__device__ __forceinline__ void adj_block_interior(const AdjPass &a, int lane, int ly0,
-                                                   const float *cur, float *nxt, const float *ut,
-                                                   const float *ptile, float (&hi)[NG],
-                                                   float (&ab)[NG], float (&pacc)[ACPT])
+// One transposed step on my 4 x 4 cells of a staged tile: the rows by 16-byte loads, the
+// x-neighbours across lanes by shuffles; per cell the operations and their order are those of
+// the general path.  EDGE = false: the tile lies inside the grid and off its edges (no clamp,
+// no mask).  EDGE = true: any staged tile; cells off the grid are masked and the clamped
+// neighbours of cells on the grid's edges are applied per cell (out-of-grid cells of the
+// staged tiles arrive as zeros, as the general path reads them).
+template <int KIND, bool ABS, bool EDGE>
+__device__ __forceinline__ void adj_block(const AdjPass &a, int lane, int ly0, int x0, int y0,
+                                          const float *cur, float *nxt, const float *ut,
+                                          const float *ptile, float (&hi)[NG], float (&ab)[NG],
+                                          float (&pacc)[ACPT])
 {
     const int lx0 = 4 * lane;
     float L[6][4];   // lambda rows ly0-1 .. ly0+4 (zero beyond the tile)
@@ -186,15 +189,25 @@ __device__ __forceinline__ void adj_block_interior(const AdjPass &a, int lane, i
 #pragma unroll
     for (int r = 0; r < 4; r++) {
         float o[4];
+        const int gy = y0 + ly0 + r;
 #pragma unroll
         for (int j = 0; j < 4; j++) {
+            const int gx = x0 + lx0 + j;
             const float le = j < 3 ? L[r + 1][j + 1] : er[r];
             const float lw = j > 0 ? L[r + 1][j - 1] : wl[r];
-            float v = __fmul_rn(a.wc, L[r + 1][j]);
+            float cs = a.wc;
+            if (EDGE) {   // the weights of clamped neighbours fold into the diagonal
+                if (gx == 0) cs = __fadd_rn(cs, a.ww);
+                if (gx == a.nx - 1) cs = __fadd_rn(cs, a.we);
+                if (gy == 0) cs = __fadd_rn(cs, a.wn);
+                if (gy == a.ny - 1) cs = __fadd_rn(cs, a.ws);
+            }
+            float v = __fmul_rn(cs, L[r + 1][j]);
             v = __fmaf_rn(a.ww, le, v);
             v = __fmaf_rn(a.we, lw, v);
             v = __fmaf_rn(a.ws, L[r][j], v);
             v = __fmaf_rn(a.wn, L[r + 2][j], v);
+            if (EDGE && !(gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny)) v = 0.f;
             o[j] = v;
         }
         *reinterpret_cast<float4 *>(nxt + (ly0 + r) * AX + lx0) = make_float4(o[0], o[1], o[2], o[3]);
@@ -218,8 +231,9 @@ __device__ __forceinline__ void adj_block_interior(const AdjPass &a, int lane, i
         }
 #pragma unroll
         for (int r = 0; r < 4; r++) {
-            const int ly = ly0 + r;
+            const int ly = ly0 + r, gy = y0 + ly;
             if (ly < ATA || ly >= ATA + ACY) continue;
+            if (EDGE && gy >= a.ny) continue;
             float pr[4] = {0.f, 0.f, 0.f, 0.f};
             if (KIND == ST_THERMAL) {
                 const float4 v = lds4(ptile + ly * AX + lx0);
@@ -227,11 +241,21 @@ __device__ __forceinline__ void adj_block_interior(const AdjPass &a, int lane, i
             }
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                const int lx = lx0 + j;
+                const int lx = lx0 + j, gx = x0 + lx;
                 if (lx < ATA || lx >= ATA + ACX) continue;
+                if (EDGE && gx >= a.nx) continue;
+                const float uc = U[r + 1][j];
+                float uwj = j > 0 ? U[r + 1][j - 1] : uw[r];
+                float uej = j < 3 ? U[r + 1][j + 1] : ue[r];
+                float usj = U[r + 2][j], unj = U[r][j];
+                if (EDGE) {   // clamp at the domain edges (own cells are never off the grid's start)
+                    if (gx == 0) uwj = uc;
+                    if (gx == a.nx - 1) uej = uc;
+                    if (gy == 0) unj = uc;
+                    if (gy == a.ny - 1) usj = uc;
+                }
                 float g[NG];
-                dfdtheta<KIND>(a, U[r + 1][j], j > 0 ? U[r + 1][j - 1] : uw[r],
-                               j < 3 ? U[r + 1][j + 1] : ue[r], U[r + 2][j], U[r][j], pr[j], g);
+                dfdtheta<KIND>(a, uc, uwj, uej, usj, unj, pr[j], g);
                 const float l = L[r + 1][j];
 #pragma unroll
                 for (int m = 0; m < NG; m++) {
@@ -333,7 +357,9 @@ __global__ void __launch_bounds__(ANT, 2) k_adj2d(const AdjPass a, const __grid_
             }
         }
         if (interior) {
-            adj_block_interior<KIND, ABS>(a, lane, ly0, cur, nxt, ut, ptile, hi, ab, pacc);
+            adj_block<KIND, ABS, false>(a, lane, ly0, x0, y0, cur, nxt, ut, ptile, hi, ab, pacc);
+        } else if (tma) {
+            adj_block<KIND, ABS, true>(a, lane, ly0, x0, y0, cur, nxt, ut, ptile, hi, ab, pacc);
         } else {
 #pragma unroll
             for (int c = 0; c < ACPT; c++) {
