@@ -278,7 +278,9 @@ int stencil_adjoint_forward(stencil_adjoint a, const float *u0, const float *pow
  *   grad_u0         : dL/du_0, nx*ny floats (may not overlap grad_out)
  *   grad_coeffs     : 5 floats, dL/dcoeffs in the coefficient layout of the kind
  *   grad_coeffs_abs : 5 floats or NULL: sum over (t, i) of |lambda_{t+1}[i] dF_i/dcoeff_m|,
- *                     the scale the rounding error of grad_coeffs[m] is relative to
+ *                     the scale the rounding error of grad_coeffs[m] is relative to; with NULL
+ *                     the sweep does not accumulate it (fewer operations per cell, the other
+ *                     results bit-identical)
  *   grad_power      : dL/dpower, nx*ny floats (ST_THERMAL; NULL for ST_DIFFUSION)
  * Coefficient gradients are float32 sums in a fixed order (per thread at most 64 terms, then
  * error-free pairwise combination): deterministic for a given size.  Errors: ST_ERR_INVALID_ARG (no forward run yet, missing or
