@@ -51,7 +51,7 @@ extern "C" {
 #define ST_ERR_CUDA             -4   /* a CUDA runtime call or a launch failed */
 #define ST_ERR_OOM              -5   /* device allocation failed */
 #define ST_ERR_TIMEOUT          -6   /* a bounded device-side wait gave up */
-#define ST_ERR_UNSUPPORTED      -7   /* valid request this build does not provide */
+#define ST_ERR_UNSUPPORTED      -7   /* valid request with no compiled kernel */
 #define ST_ERR_TOO_LARGE        -8   /* grid exceeds the fixed buffer of stencil_run_noalloc */
 
 /* stencil kinds (Table 2) */
@@ -117,7 +117,7 @@ typedef struct {
  * ping-pong scratch buffer (Sec. 2.1's second buffer) and keeps it until destroy.
  * out: receives the plan (NULL on failure).
  * Errors: ST_ERR_INVALID_ARG (bad desc), ST_ERR_UNSUPPORTED (e.g. a storage type or forced
- * parameter set this build does not provide), ST_ERR_OOM, ST_ERR_CUDA. */
+ * parameter set with no compiled kernel), ST_ERR_OOM, ST_ERR_CUDA. */
 int stencil_plan_create(stencil_plan *out, const stencil_desc *desc);
 
 /* Advance grid_in by `steps` Jacobi steps (Sec. 2.1) into grid_out.
@@ -176,11 +176,11 @@ typedef struct {
     int force_T, force_bx, force_by, force_vec;   /* the fastest configuration, as desc forces */
     double gcells;        /* its measured rate, 10^9 cell updates/s */
     double model_gcells;  /* the model's rate for it (0 where the family has no calibration) */
-    int candidates;       /* configurations this build provides for the problem */
+    int candidates;       /* compiled configurations for the problem */
     int timed;            /* how many of them were run and timed */
 } stencil_tune_result;
 
-/* Rank every configuration the build provides for *desc by the model, run the top_k of them
+/* Rank every compiled configuration for *desc by the model, run the top_k of them
  * (top_k = 0: all) once untimed and once timed (CUDA events on desc->stream) on the caller's
  * grids, and cache the fastest.
  * desc     : as for stencil_plan_create, with every force_* field 0 (else ST_ERR_INVALID_ARG).
@@ -200,7 +200,7 @@ int stencil_plan_tuned(stencil_plan plan);
 /* The cache: clear it; count its entries; write it to a text file (one entry per line:
  * kind ndim nx ny nz storage exact rad T bx by vec gcells); merge a file written that way into
  * it (a malformed line rejects the whole file with ST_ERR_INVALID_ARG and changes nothing).
- * An entry whose configuration this build cannot make is ignored by stencil_plan_create.
+ * An entry whose configuration has no compiled kernel is ignored by stencil_plan_create.
  * Host-only calls; safe to call from several threads. */
 int stencil_tune_cache_clear(void);
 int stencil_tune_cache_size(void);

@@ -1,6 +1,6 @@
 // Measured refinement of the model's parameter choice (arXiv 1802.00438, Sec. 5.3 and 5.4.2):
 // the performance model (Eqs. 3-9, restated for this GPU and calibrated in api.cu) ranks every
-// configuration the build provides; only the few it rates best are run and timed on the
+// compiled configuration; only the few it rates best are run and timed on the
 // caller's data, and the fastest is kept.  The choice is cached per problem key (kind, ndim,
 // nx, ny, nz, storage, exact, rad) for the life of the process, and stencil_plan_create with
 // nothing forced takes it from there.  The cache can be written to and read from a text file.
@@ -36,7 +36,7 @@ Key key_of(const stencil_desc &d)
 }
 
 // Every configuration a plan can be forced to, as (force_T, force_bx, force_by, force_vec);
-// those this build does not compile are refused by stencil_plan_create and skipped.
+// those not compiled into the library are refused by stencil_plan_create and skipped.
 std::vector<std::array<int, 4>> candidates(const stencil_desc &d)
 {
     std::vector<std::array<int, 4>> c;
