@@ -167,7 +167,7 @@ int stencil_plan_kernel_time(stencil_plan plan, double *ms, long long *launches,
 int stencil_plan_destroy(stencil_plan plan);
 
 /* ---- measured parameter choice (Sec. 5.3 and 5.4.2) --------------------------------------
- * The plan's own choice comes from the model alone (Eqs. 3-9 restated for this GPU).  The
+ * The plan's own choice comes from the model alone (Eqs. 3-9 restated for the GB300).  The
  * paper narrows the configurations with its model and then builds and measures the few it
  * rates best; stencil_tune does the same on the caller's data and remembers the winner for the
  * problem key (kind, ndim, nx, ny, nz, storage, exact, rad) in a process-wide cache, which

@@ -1,5 +1,5 @@
 // Measured refinement of the model's parameter choice (arXiv 1802.00438, Sec. 5.3 and 5.4.2):
-// the performance model (Eqs. 3-9, restated for this GPU and calibrated in api.cu) ranks every
+// the performance model (Eqs. 3-9, restated for the GB300 and calibrated in api.cu) ranks every
 // compiled configuration; only the few it rates best are run and timed on the
 // caller's data, and the fastest is kept.  The choice is cached per problem key (kind, ndim,
 // nx, ny, nz, storage, exact, rad) for the life of the process, and stencil_plan_create with
