@@ -319,7 +319,9 @@ template <int KIND, bool EXACT, int T, int VY, int NW>
 __global__ void __launch_bounds__(32 * NW) k_tb3d(const Pass3D p)
 {
     using C = TB3<KIND, EXACT, T, VY, NW>;
-    extern __shared__ __align__(16) float smem[];
+    // 128-byte aligned as in the 3D contracted kernel: both 3D kernels share translation
+    // units, where the declarations of the dynamic shared array must agree
+    extern __shared__ __align__(128) float smem[];
     Ctx3 c;
     c.in = p.in;
     c.out = p.out;
