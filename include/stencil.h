@@ -79,7 +79,9 @@ typedef struct {
     int kind;        /* ST_DIFFUSION, ST_THERMAL or ST_DIFFUSION_VAR */
     int ndim;        /* 2 or 3 */
     int nx, ny, nz;  /* grid size in cells, each >= 1; nz is ignored (taken as 1) for 2D */
-    int storage;     /* ST_F32 */
+    int storage;     /* grid storage between passes: ST_F32, or ST_BF16 / ST_F16 (2D contracted
+                        plans of ST_DIFFUSION / ST_THERMAL, rad <= 1: 16-bit codes with a
+                        float32 offset and scale per block; arithmetic stays float32) */
     int force_T;     /* fused steps per pass (par_time, Sec. 3.2); 0 = the plan chooses */
     int force_bx;    /* tile width in cells incl. halos (bsize_x, Sec. 3.1); 0 = choose */
     int force_by;    /* 3D: tile height in cells incl. halos (bsize_y); 0 = choose.  2D
@@ -393,8 +395,11 @@ int stencil_model_gpu(const stencil_gpu_model_in *in, stencil_gpu_model_out *out
  * 4,194,304 cells return ST_ERR_TOO_LARGE.  It calls no cudaMalloc, cudaFree or allocating
  * routine.  All calls on a device share that buffer: calls whose work overlaps on the GPU
  * (different streams, unordered host threads) race on it.  The first call on each device looks
- * up the buffer's device address (cudaGetSymbolAddress) and caches it; make that first call
- * before any stream capture.  Returns ST_OK or an ST_ERR_* code; launches are asynchronous. */
+ * up the buffer's device address (cudaGetSymbolAddress) and caches it with the context it was
+ * found in; make that first call before any stream capture.  After cudaDeviceReset (or any
+ * re-creation of the device's primary context) the next call looks the address up again, so
+ * it too should come before any capture.  Returns ST_OK or an ST_ERR_* code; launches are
+ * asynchronous. */
 int stencil_run_noalloc(int kind, const void *grid_in, void *grid_out, const void *power,
                         const float *coeffs, int nx, int ny, int steps, int exact, int T,
                         void *stream);

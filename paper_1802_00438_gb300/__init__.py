@@ -343,11 +343,31 @@ def stencil_model_gpu(**kw) -> dict:
     return r.as_dict()
 
 
+def _check_extent(t, need: int, name: str):
+    """Refuse a tensor that holds fewer than `need` elements or lives on another device than
+    the current one (the device whose buffers and SM count the library uses for the call):
+    either would make the kernels read or write outside the tensor.  Integer addresses are the
+    caller's responsibility.  Runs before anything is launched."""
+    if t is None or isinstance(t, int):
+        return
+    if t.numel() < need:
+        raise ValueError(f"{name} holds {t.numel()} elements, the grid needs {need}")
+    import torch
+    if t.get_device() != torch.cuda.current_device():
+        raise ValueError(f"{name} is on device {t.get_device()}, the current device is "
+                         f"{torch.cuda.current_device()}")
+
+
 def stencil_run_noalloc(kind, grid_in, grid_out, power, coeffs, nx, ny, steps, exact=False, T=0,
                         stream=None):
     """2D run without a plan and without any device allocation (see include/stencil.h): for
     callers that must not allocate device memory where they advance a grid.  Uses a fixed
-    16 MiB buffer the library reserves per device; larger grids raise ST_ERR_TOO_LARGE."""
+    16 MiB buffer the library reserves per device; larger grids raise ST_ERR_TOO_LARGE.
+    Tensors smaller than nx*ny elements, or on a device other than the current one, raise
+    ValueError before any work is queued."""
+    n = int(nx) * int(ny)
+    for name, t in (("grid_in", grid_in), ("grid_out", grid_out), ("power", power)):
+        _check_extent(t, n, name)
     k = _coef_array(coeffs)
     _check(lib.stencil_run_noalloc(int(kind), _addr(grid_in), _addr(grid_out), _addr(power), k,
                                    int(nx), int(ny), int(steps), 1 if exact else 0, int(T),
@@ -409,6 +429,10 @@ class Plan:
         self.h = stencil_plan_create(kind, ndim, nx, ny, self.nz, **kw)
 
     def run(self, grid_in, grid_out, coeffs, steps, power=None):
+        n = self.nx * self.ny * self.nz
+        _check_extent(grid_in, n, "grid_in")
+        _check_extent(grid_out, n, "grid_out")
+        _check_extent(power, 5 * n if self.kind == ST_DIFFUSION_VAR else n, "power")
         stencil_run(self.h, grid_in, grid_out, power, coeffs, self.nx, self.ny, self.nz, steps)
         return grid_out
 

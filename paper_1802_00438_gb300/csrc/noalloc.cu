@@ -17,7 +17,12 @@
 // Host code cannot use the array's name as a device address: on the host it names a shadow
 // variable.  The first call on each device therefore looks the device address up once with
 // cudaGetSymbolAddress (with that device current) and caches it; make that first call before
-// any stream capture.  No call allocates: no cudaMalloc, cudaFree or allocating library routine.
+// any stream capture.  The cache entry remembers the CUDA context it was looked up in: after a
+// cudaDeviceReset (or any release and re-creation of the device's primary context) the module
+// is loaded again and the array may move, so the next call looks the address up again; that
+// call, too, should come before any stream capture.  No call allocates: no cudaMalloc,
+// cudaFree or allocating library routine.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,6 +44,7 @@ static __device__ __align__(256) float g_static_scratch[kStaticScratchCells];
 struct DeviceSlot {
     float *scratch = nullptr;   // device address of g_static_scratch on this device
     int sms = 0;
+    unsigned long long ctx_id = 0;   // the context the address was looked up in
 };
 
 DeviceSlot g_dev[kMaxDevices];
@@ -50,7 +56,37 @@ int to_status(cudaError_t e)
     return ST_ERR_CUDA;
 }
 
-// once per device, with that device current: the scratch array's device address, the SM count
+// Unique ID of the calling thread's current context (0 when there is none yet or the driver
+// cannot tell), through the driver entry points the runtime hands out (no link to libcuda).
+unsigned long long current_ctx_id()
+{
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool resolved = false;
+    if (!resolved) {   // called under g_mu
+        void *f = nullptr, *g = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q1) ==
+                cudaSuccess && q1 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &g, 12000, cudaEnableDefault, &q2) ==
+                cudaSuccess && q2 == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<GetCurrent>(f);
+            get_id = reinterpret_cast<GetId>(g);
+        }
+        resolved = true;
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// once per device and context, with that device current: the scratch array's device address,
+// the SM count
 int device_slot(DeviceSlot **out)
 {
     int dev = 0;
@@ -59,15 +95,17 @@ int device_slot(DeviceSlot **out)
     if (dev < 0 || dev >= kMaxDevices) return ST_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_mu);
     DeviceSlot &s = g_dev[dev];
-    if (!s.scratch) {
+    const unsigned long long ctx = current_ctx_id();
+    if (!s.scratch || (ctx && ctx != s.ctx_id)) {
         void *addr = nullptr;
-        e = cudaGetSymbolAddress(&addr, g_static_scratch);
+        e = cudaGetSymbolAddress(&addr, g_static_scratch);   // makes the context current
         if (e != cudaSuccess) return to_status(e);
         int sms = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return to_status(e);
         s.sms = sms;
         s.scratch = static_cast<float *>(addr);
+        s.ctx_id = current_ctx_id();
     }
     *out = &s;
     return ST_OK;

@@ -68,3 +68,41 @@ def test_no_oracle_in_product():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 txt = open(os.path.join(dp, f)).read()
                 assert "oracle" not in txt.lower().replace("oracle's", ""), os.path.join(dp, f)
+
+
+class _FakeGrid:
+    """Stands in for a CUDA tensor in the binding's size and device checks: those checks run
+    before the binding takes an address or calls the library, so nothing is launched."""
+
+    def __init__(self, n, device):
+        self.n, self.device_index = n, device
+
+    def numel(self):
+        return self.n
+
+    def get_device(self):
+        return self.device_index
+
+
+def test_binding_refuses_short_or_foreign_tensors(lib_path, monkeypatch):
+    import torch
+
+    import paper_1802_00438_gb300 as st
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+    ok = _FakeGrid(64 * 32, 0)
+    short = _FakeGrid(64 * 32 - 1, 0)
+    other = _FakeGrid(64 * 32, 1)
+    for args in ((short, ok, None), (ok, short, None), (other, ok, None), (ok, other, None)):
+        with pytest.raises(ValueError):
+            st.stencil_run_noalloc(0, *args, [0.2] * 5, 64, 32, 3)
+    with pytest.raises(ValueError):                       # short power map
+        st.stencil_run_noalloc(1, ok, _FakeGrid(64 * 32, 0), short, [0.5, 0.1, 0.1, 1e-4, 80.0],
+                               64, 32, 3)
+    with pytest.raises(ValueError):                       # power map on another device
+        st.stencil_run_noalloc(1, ok, _FakeGrid(64 * 32, 0), other, [0.5, 0.1, 0.1, 1e-4, 80.0],
+                               64, 32, 3)
+    # the plan wrapper applies the same checks (a plan object needs no device to be checked)
+    plan = st.Plan.__new__(st.Plan)
+    plan.kind, plan.ndim, plan.nx, plan.ny, plan.nz, plan.h = 2, 2, 64, 32, 1, None
+    with pytest.raises(ValueError):                       # five coefficient planes expected
+        plan.run(ok, _FakeGrid(64 * 32, 0), None, 1, power=_FakeGrid(4 * 64 * 32, 0))
