@@ -224,27 +224,51 @@ typedef struct {
     float coeffs[5];       /* Table 2 coefficients (layouts above) */
 } stencil_batch_grid;
 
-/* Prepare `count` grids for repeated batched runs: each grid gets (T, cells per thread) from
- * the GPU restatement of the paper's model (Eqs. 3-9) and its own ping-pong scratch (Sec. 2.1);
- * grids that share a kernel form a group, and each launch slot of a group is one persistent
- * launch over a work queue spanning all its grids that run a pass in that slot (Eq. 8:
- * ceil(steps/T) passes per grid, the last fusing the remainder, Sec. 3.2; each grid's chain of
- * passes starts at the slot that levels the group's work).  All launches are captured into one
- * CUDA graph, one branch per group, on `stream` (NULL: an owned stream that synchronises with
- * the legacy default stream).  Buffers
- * and coefficients are fixed at creation.  Errors: ST_ERR_INVALID_ARG, ST_ERR_UNSUPPORTED,
- * ST_ERR_OOM, ST_ERR_CUDA. */
+/* Prepare `count` grids for repeated batched runs.  Every grid advances by its own step count
+ * in ceil(steps/T) temporally-blocked passes (Eq. 8; the last pass fuses the remainder,
+ * Sec. 3.2) with its own ping-pong scratch (Sec. 2.1); one (T, cells per thread) for the whole
+ * batch comes from the GPU restatement of the paper's model (Eqs. 3-9), the compiled choice with
+ * the least predicted total time.  The passes of all grids are cut into items of one tile column
+ * (Sec. 3.1's overlapped tile) by 128 rows and queued pass by pass; ONE persistent kernel launch,
+ * one warp per block and as many blocks as the device holds at once, pops the items in order,
+ * and an item waits for the neighbouring tiles of its grid's previous pass (the halo it reads and
+ * the cells of the ping-pong buffer it overwrites) before it starts.  Each such wait is bounded
+ * (1 s by default, stencil_batch_set_wait): when one gives up, every block of the launch leaves
+ * and stencil_batch_sync reports ST_ERR_TIMEOUT.  The launch, a reset of the queue's counters
+ * before it and a copy of its status word after it are captured into one CUDA graph on `stream`
+ * (NULL: an owned stream that synchronises with the legacy default stream).  Buffers and
+ * coefficients are fixed at creation; the power maps' contents are read at every replay.
+ * Errors: ST_ERR_INVALID_ARG, ST_ERR_UNSUPPORTED, ST_ERR_OOM, ST_ERR_CUDA. */
 int stencil_batch_create(stencil_batch *out, const stencil_batch_grid *grids, int count,
                          void *stream);
+
+/* stencil_batch_create with the queue's parameters chosen by the caller (0 = the library's
+ * choice): rows_per_item, the rows of one tile column an item covers (>= T); force_T and
+ * force_vec, the fused steps per pass and cells per thread of the launch's kernel (ST_ERR_
+ * UNSUPPORTED when no compiled kernel matches). */
+int stencil_batch_create_ex(stencil_batch *out, const stencil_batch_grid *grids, int count,
+                            void *stream, int rows_per_item, int force_T, int force_vec);
 
 /* Replay the batch's graph (asynchronous): every grid advances by its step count into its
  * grid_out. */
 int stencil_batch_run(stencil_batch b);
 
+/* Wait for the batch's stream.  Returns ST_ERR_TIMEOUT when a bounded wait of the last replay
+ * gave up (its grids' results are then invalid; the batch and the CUDA context stay usable and
+ * the next replay starts afresh), ST_ERR_CUDA on a CUDA error, else ST_OK. */
+int stencil_batch_sync(stencil_batch b);
+
+/* Set how long (wait_ns > 0 nanoseconds) an item of later replays may wait for the tiles it
+ * depends on before the launch gives up.  hold_pass >= 0 is a test hook that makes the items of
+ * that pass never report themselves finished, so the items of the next pass wait until the
+ * limit runs out (a dependency that is never satisfied, without any fault); -1 turns it off.
+ * Synchronises the batch's stream.  Errors: ST_ERR_INVALID_ARG, ST_ERR_CUDA. */
+int stencil_batch_set_wait(stencil_batch b, long long wait_ns, int hold_pass);
+
 /* Grid g's chosen fused steps T, cells per thread and pass count. */
 int stencil_batch_get_grid(stencil_batch b, int g, int *T, int *vec, int *passes);
 
-/* Kernel launches in the batch's graph (or ST_ERR_INVALID_ARG). */
+/* Kernel launches in the batch's graph: 1 (0 when no grid has work), or ST_ERR_INVALID_ARG. */
 int stencil_batch_launch_count(stencil_batch b);
 
 /* Wait for the batch's stream, free its graph and scratch.  NULL is accepted. */
@@ -403,6 +427,15 @@ int stencil_model_gpu(const stencil_gpu_model_in *in, stencil_gpu_model_out *out
 int stencil_run_noalloc(int kind, const void *grid_in, void *grid_out, const void *power,
                         const float *coeffs, int nx, int ny, int steps, int exact, int T,
                         void *stream);
+
+/* Measured FP32 arithmetic peak of the current device, for the arithmetic side of the roofline
+ * R(T) = min(P_FP32 / flops per cell, HBM bandwidth x T / bytes per cell) that the paper's model
+ * (Sec. 4, Eq. 6: compute-bound cell rate) sets against memory throughput.  Runs a kernel of
+ * independent float32 fused multiply-add chains on every SM (a warm-up launch, then the best of
+ * three timed launches, CUDA events on `stream`, NULL = legacy default stream) and writes the
+ * rate in 10^12 flops/s (a multiply-add counted as 2) to *tflops.  Synchronous; allocates
+ * nothing.  Errors: ST_ERR_INVALID_ARG (NULL tflops), ST_ERR_CUDA. */
+int stencil_fp32_peak(double *tflops, void *stream);
 
 /* Static description of a status code. */
 const char *stencil_strerror(int code);

@@ -129,7 +129,11 @@ SIGNATURES = {
                                   ctypes.POINTER(ctypes.c_longlong), _I], _I),
     "stencil_plan_destroy": ([_P], _I),
     "stencil_batch_create": ([ctypes.POINTER(_P), ctypes.POINTER(stencil_batch_grid), _I, _P], _I),
+    "stencil_batch_create_ex": ([ctypes.POINTER(_P), ctypes.POINTER(stencil_batch_grid), _I, _P, _I,
+                                 _I, _I], _I),
     "stencil_batch_run": ([_P], _I),
+    "stencil_batch_sync": ([_P], _I),
+    "stencil_batch_set_wait": ([_P, ctypes.c_longlong, _I], _I),
     "stencil_batch_get_grid": ([_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "stencil_batch_launch_count": ([_P], _I),
     "stencil_batch_destroy": ([_P], _I),
@@ -155,6 +159,7 @@ SIGNATURES = {
     "stencil_tune_cache_size": ([], _I),
     "stencil_tune_cache_save": ([ctypes.c_char_p], _I),
     "stencil_tune_cache_load": ([ctypes.c_char_p], _I),
+    "stencil_fp32_peak": ([ctypes.POINTER(ctypes.c_double), _P], _I),
 }
 
 
@@ -326,6 +331,14 @@ def stencil_reduce(a, b=None, stream=None) -> dict:
     return dict(zip(REDUCE_FIELDS, vals))
 
 
+def stencil_fp32_peak(stream=None) -> float:
+    """Measured float32 fused-multiply-add rate of the current device, TFLOP/s."""
+    v = ctypes.c_double()
+    _check(lib.stencil_fp32_peak(ctypes.byref(v), current_stream() if stream is None else stream),
+           "stencil_fp32_peak")
+    return v.value
+
+
 def stencil_model_fpga(**kw) -> dict:
     """The paper's performance model (Eqs. 3-9); keyword arguments are the fields of
     stencil_fpga_model_in."""
@@ -379,7 +392,7 @@ class Batch:
     """Owning wrapper of stencil_batch: grids is a list of dicts with keys kind, nx, ny, steps,
     grid_in, grid_out, power (CUDA tensors or None) and coeffs."""
 
-    def __init__(self, grids, stream=None):
+    def __init__(self, grids, stream=None, rows_per_item=0, force_T=0, force_vec=0):
         arr = (stencil_batch_grid * len(grids))()
         for i, g in enumerate(grids):
             arr[i].kind = g["kind"]
@@ -393,11 +406,23 @@ class Batch:
                 arr[i].coeffs[j] = float(c)
         self.keep = grids
         self.h = ctypes.c_void_p()
-        _check(lib.stencil_batch_create(ctypes.byref(self.h), arr, len(grids), stream),
-               "stencil_batch_create")
+        _check(lib.stencil_batch_create_ex(ctypes.byref(self.h), arr, len(grids), stream,
+                                           int(rows_per_item), int(force_T), int(force_vec)),
+               "stencil_batch_create_ex")
 
     def run(self):
         _check(lib.stencil_batch_run(self.h), "stencil_batch_run")
+
+    def sync(self):
+        """Wait for the last replay; raises StencilError(ST_ERR_TIMEOUT) if a bounded wait of
+        the persistent launch gave up."""
+        _check(lib.stencil_batch_sync(self.h), "stencil_batch_sync")
+
+    def set_wait(self, wait_ns: int, hold_pass: int = -1):
+        """Wait limit of the launch's dependency waits; hold_pass >= 0 is the test hook that
+        keeps that pass from ever reporting finished (see include/stencil.h)."""
+        _check(lib.stencil_batch_set_wait(self.h, int(wait_ns), int(hold_pass)),
+               "stencil_batch_set_wait")
 
     def grid_info(self, g):
         t, v, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

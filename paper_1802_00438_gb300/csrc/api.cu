@@ -205,8 +205,10 @@ double model_gcells_3d(const stencil_desc &d, int sms, int T, int VX, int VY, in
 }  // namespace
 
 namespace stn {
-// the batch's per-grid choice uses the same calibrated model
-double batch_model_gcells(int kind, int nx, int ny, int steps, int sms, int T, int V, int bps)
+// the batch's (T, V) choice uses the same calibrated model; seg_rows: rows per queue item (each
+// item streams 2T rows more than it stores)
+double batch_model_gcells(int kind, int nx, int ny, int steps, int sms, int T, int V, int bps,
+                          int seg_rows)
 {
     stencil_desc d = {};
     d.kind = kind;
@@ -214,11 +216,7 @@ double batch_model_gcells(int kind, int nx, int ny, int steps, int sms, int T, i
     d.nx = nx;
     d.ny = ny;
     d.nz = 1;
-    // a batch launch splits all its grids' units over SMs x resident blocks, and a block's
-    // range crosses grids, so its segments are short: 24 rows reproduces the measured order on
-    // the 64-grid workload (T = 4 everywhere 1318, the standalone choice 1260, T = 8 everywhere
-    // 1219 GCell/s)
-    return model_gcells_2d(d, sms, Cand2D{T, V, 1}, bps, steps, 24);
+    return model_gcells_2d(d, sms, Cand2D{T, V, 1}, bps, steps, std::min(seg_rows, ny));
 }
 }  // namespace stn
 
@@ -903,8 +901,10 @@ int stencil_run(stencil_plan p, const void *grid_in, void *grid_out, const void 
         // 16-bit storage: code the field (and the power map), run every pass on the coded
         // grids, decode into the output
         e = lp_encode(p->stor, in, d.nx, p->q[0], p->ld_q, p->qm[0], d.nx, d.ny, p->cx, p->stream);
+        // the power map is coded as the Hotspot source map sdc*(p + amb*Rz) the kernels read
         if (e == cudaSuccess && pw)
-            e = lp_encode(p->stor, pw, d.nx, p->qp, p->ld_q, p->qpm, d.nx, d.ny, p->cx, p->stream);
+            e = lp_encode(p->stor, pw, d.nx, p->qp, p->ld_q, p->qpm, d.nx, d.ny, p->cx, p->stream,
+                          coeffs[4] * coeffs[3], coeffs[0]);
         if (e != cudaSuccess) return map_cuda(e);
         int cur = 0;
         for (int i = 0; i < passes; i++) {
@@ -925,8 +925,9 @@ int stencil_run(stencil_plan p, const void *grid_in, void *grid_out, const void 
     const bool shift = (in == out) && (passes % 2 == 1);
     const long long ldo = d.nx, ldsc = d.ndim == 2 ? p->ld_scratch : d.nx;
     if (p->src) {
-        // contracted Hotspot 2D kernels stage p + amb*Rz (Table 2's ambient term folded in)
-        e = hot_source(pw, d.nx, p->src, d.nx, d.ny, coeffs[4], coeffs[3], p->stream);
+        // contracted Hotspot 2D kernels stage sdc*(p + amb*Rz) (Table 2's source and ambient
+        // terms folded into one map)
+        e = hot_source(pw, d.nx, p->src, d.nx, d.ny, coeffs[4], coeffs[3], coeffs[0], p->stream);
         if (e != cudaSuccess) return map_cuda(e);
         pw = p->src;
     }
@@ -980,8 +981,10 @@ int stencil_run_trajectory(stencil_plan p, const void *grid_in, void *states, lo
     if (rc != ST_OK) return rc;
     const float *pw = static_cast<const float *>(power);
     if (p->src) {
-        // contracted Hotspot kernels stage p + amb*Rz (Table 2's ambient term folded in)
-        const cudaError_t e = hot_source(pw, d.nx, p->src, d.nx, d.ny, coeffs[4], coeffs[3], p->stream);
+        // contracted Hotspot kernels stage sdc*(p + amb*Rz) (Table 2's source and ambient terms
+        // folded into one map)
+        const cudaError_t e = hot_source(pw, d.nx, p->src, d.nx, d.ny, coeffs[4], coeffs[3],
+                                         coeffs[0], p->stream);
         if (e != cudaSuccess) return map_cuda(e);
         pw = p->src;
     }

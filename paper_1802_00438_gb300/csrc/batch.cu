@@ -1,25 +1,21 @@
-// Many 2D grids of uneven sizes and step counts advanced by one CUDA-graph launch.
+// Many 2D grids of uneven sizes and step counts advanced by ONE persistent kernel launch fed by a
+// tile work queue, captured in a CUDA graph.
 //
-// Each grid gets its own (T, cells per thread) from the GPU restatement of the paper's model
-// (Eqs. 3-9, model.cu) and its own ping-pong scratch, and runs ceil(steps/T) temporally-blocked
-// passes like stencil_run (Sec. 3.2; the last pass fuses the remainder).  Grids that share a
-// kernel instance (stencil kind, T, V) form a group; pass p of a group is one persistent launch
-// over a work queue of all its grids' (tile column, row) units that run a pass in that launch,
-// split evenly over the blocks, so small and large grids are served in the same launch without
-// idle blocks; each grid's chain of passes starts at the launch slot that levels the work of
-// the group's launches (a grid with few passes fills in where long-running grids leave room).
-// All launches (and the final copies of grids run in place with an odd pass count) are
-// captured once into a CUDA graph with one branch per group; stencil_batch_run replays it.
-// The order of passes of one grid is the order of launches on its branch: no device-side
-// waiting.
+// Every grid runs ceil(steps/T) temporally-blocked passes like stencil_run (Eq. 8, Sec. 3.2: the
+// last pass fuses the remainder) with its own ping-pong scratch; one (T, cells per thread) for
+// the whole batch comes from the GPU restatement of the paper's model (Eqs. 3-9), the choice that
+// minimises the predicted total time.  The passes are cut into items (one tile column x L rows),
+// queued pass by pass on a levelled timeline with the Hotspot source-map rows first and the
+// copies of grids with no steps last; the blocks of one launch (one warp each, as many as are
+// resident) pop them and wait, bounded, for the neighbouring tiles of the previous pass
+// (tb2q.cu).  The graph is: reset of the queue head, status and per-tile counters; the launch; a
+// copy of the status word to host memory that stencil_batch_sync reads.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
-#include <map>
 #include <new>
-#include <tuple>
 #include <vector>
 
 #include "../../include/stencil.h"
@@ -28,25 +24,34 @@
 using namespace stn;
 
 namespace stn {
-double batch_model_gcells(int kind, int nx, int ny, int steps, int sms, int T, int V, int bps);
+double batch_model_gcells(int kind, int nx, int ny, int steps, int sms, int T, int V, int bps,
+                          int seg_rows);
 }
 
 struct stencil_batch_s {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int sms = 0;
+    int qT = 0, qV = 0;
     std::vector<stencil_batch_grid> grid;
-    std::vector<int> T, V, passes;
-    std::vector<float *> scratch;
-    std::vector<float *> src;         // Hotspot grids: the source map p + amb*Rz
+    std::vector<int> passes;
+    std::vector<float *> scratch;     // two per grid: the passes between the first and the last
+    std::vector<float *> src;         // Hotspot grids: the source map sdc*(p + amb*Rz)
     std::vector<long long> ld_scratch;
-    void *dev = nullptr;              // descriptors and prefix arrays of every (group, pass)
+    void *dev = nullptr;              // items, grids, pass descriptors, counters, control
+    QueueCtl *ctl = nullptr;          // inside dev
+    int *h_status = nullptr;          // pinned: the status word after the last replay
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int launches = 0;
+    long long items = 0;
 };
 
 namespace {
+
+constexpr int kRows = 128;                        // rows per queue item (L), by default
+constexpr long long kWaitNs = 1000LL * 1000 * 1000;   // 1 s: a wait of a healthy batch is far shorter
+const int kCand[][2] = {{8, 8}, {8, 4}};          // (T, V) of the compiled queue kernels
 
 int status(cudaError_t e)
 {
@@ -54,16 +59,7 @@ int status(cudaError_t e)
     return e == cudaErrorMemoryAllocation ? ST_ERR_OOM : ST_ERR_CUDA;
 }
 
-const int kCand[][2] = {{4, 4}, {8, 4}, {4, 8}, {8, 8}};   // (T, V) compiled for batches
-
-struct LaunchRec {
-    int group;                     // branch of the graph the launch is captured on
-    Shape2D shape;
-    BatchPass2D bp;
-    size_t desc_off, prefix_off;   // byte offsets into the device table
-    std::vector<Pass2D> desc;
-    std::vector<long long> prefix;
-};
+size_t align256(size_t n) { return (n + 255) / 256 * 256; }
 
 }  // namespace
 
@@ -72,9 +68,17 @@ extern "C" {
 int stencil_batch_create(stencil_batch *out, const stencil_batch_grid *grids, int count,
                          void *stream)
 {
+    return stencil_batch_create_ex(out, grids, count, stream, 0, 0, 0);
+}
+
+int stencil_batch_create_ex(stencil_batch *out, const stencil_batch_grid *grids, int count,
+                            void *stream, int rows_per_item, int force_T, int force_vec)
+{
     if (!out) return ST_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!grids || count < 1) return ST_ERR_INVALID_ARG;
+    if (!grids || count < 1 || rows_per_item < 0 || force_T < 0 || force_vec < 0)
+        return ST_ERR_INVALID_ARG;
+    const int L = rows_per_item ? rows_per_item : kRows;
     for (int g = 0; g < count; g++) {
         const stencil_batch_grid &q = grids[g];
         if ((q.kind != ST_DIFFUSION && q.kind != ST_THERMAL) || q.nx < 1 || q.ny < 1 ||
@@ -106,83 +110,145 @@ int stencil_batch_create(stencil_batch *out, const stencil_batch_grid *grids, in
     int dev = 0, rc = ST_OK;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&B->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaMallocHost(&B->h_status, sizeof(int));
     if (e != cudaSuccess) {
-        delete B;
+        stencil_batch_destroy(B);
         return status(e);
     }
-    // per-grid parameters from the model
-    B->T.resize(count);
-    B->V.resize(count);
-    B->passes.resize(count);
-    B->scratch.assign(count, nullptr);
-    B->src.assign(count, nullptr);
-    B->ld_scratch.resize(count);
-    // One (T, V) per kind: the grids that share a kernel run together in each launch slot, so
-    // a split of one kind over several kernels multiplies the launches and leaves each of them
-    // small.  The choice minimises the kind's predicted total time, sum over its grids of
-    // cells x steps / modelled rate.
-    int kind_T[2] = {0, 0}, kind_V[2] = {0, 0};
-    for (int kind = 0; kind < 2; kind++) {
+    *B->h_status = 0;
+
+    // one (T, V) for the launch: the compiled candidate with the least predicted total time
+    int bps = 0;
+    {
         double best = -1.0;
         for (const auto &tv : kCand) {
-            const Shape2D sh{kind, 0, tv[0], tv[1], 1};
-            int bps = 0;
-            if (tb2d_batch_prepare(sh, &bps) != cudaSuccess || bps < 1) continue;
+            int b = 0;
+            if ((force_T && tv[0] != force_T) || (force_vec && tv[1] != force_vec)) continue;
+            if (tv[0] > L) continue;   // an item's halo rows must come from its neighbours
+            if (tb2q_prepare(tv[0], tv[1], &b) != cudaSuccess || b < 1) continue;
             double t = 0.0;
-            for (int g = 0; g < count; g++) {
-                const stencil_batch_grid &q = B->grid[g];
-                if (q.kind != kind || q.steps <= 0) continue;
-                const double m = batch_model_gcells(q.kind, q.nx, q.ny, q.steps, B->sms, tv[0], tv[1], bps);
+            for (const stencil_batch_grid &q : B->grid) {
+                if (q.steps <= 0) continue;
+                const double m = batch_model_gcells(q.kind, q.nx, q.ny, q.steps, B->sms, tv[0],
+                                                    tv[1], b, L);
                 t += (double)q.nx * q.ny * q.steps / std::max(m, 1e-9);
             }
             if (best < 0 || t < best) {
                 best = t;
-                kind_T[kind] = tv[0];
-                kind_V[kind] = tv[1];
+                B->qT = tv[0];
+                B->qV = tv[1];
+                bps = b;
             }
         }
         (void)cudaGetLastError();
         if (best < 0) rc = ST_ERR_UNSUPPORTED;
     }
+    const int T = B->qT, V = B->qV;
+    const int halo = (T + 3) / 4 * 4, cx = 32 * V - 2 * halo;
+
+    // Buffers: pass 0 reads grid_in, the last pass writes grid_out, every pass between them
+    // reads and writes two grid-sized scratch buffers with rows padded to 32 cells.  So the
+    // launch never reads data it wrote itself except from the padded scratch, through
+    // 16-byte copies that bypass L1 (a row of the caller's grids may be unaligned and would be
+    // read through L1, which other SMs' writes do not update), and a grid run in place needs no
+    // final copy.
+    B->passes.assign(count, 0);
+    B->scratch.assign(2 * count, nullptr);
+    B->src.assign(count, nullptr);
+    B->ld_scratch.assign(count, 0);
     for (int g = 0; g < count && rc == ST_OK; g++) {
         const stencil_batch_grid &q = B->grid[g];
-        B->T[g] = kind_T[q.kind];
-        B->V[g] = kind_V[q.kind];
-        B->passes[g] = q.steps > 0 ? (q.steps + B->T[g] - 1) / B->T[g] : 0;
+        B->passes[g] = q.steps > 0 ? (q.steps + T - 1) / T : 0;
         B->ld_scratch[g] = ((long long)q.nx + 31) / 32 * 32;
-        if (rc == ST_OK && B->passes[g] > 0) {
-            e = cudaMalloc(&B->scratch[g], (size_t)B->ld_scratch[g] * q.ny * sizeof(float));
-            if (e == cudaSuccess && q.kind == ST_THERMAL)
-                e = cudaMalloc(&B->src[g], (size_t)q.nx * q.ny * sizeof(float));
-            if (e != cudaSuccess) rc = status(e);
+        const size_t sb = (size_t)B->ld_scratch[g] * q.ny * sizeof(float);
+        if (B->passes[g] > 1) e = cudaMalloc(&B->scratch[2 * g], sb);
+        if (e == cudaSuccess && B->passes[g] > 2) e = cudaMalloc(&B->scratch[2 * g + 1], sb);
+        if (e == cudaSuccess && B->passes[g] > 0 && q.kind == ST_THERMAL)
+            e = cudaMalloc(&B->src[g], (size_t)q.nx * q.ny * sizeof(float));
+        if (e != cudaSuccess) rc = status(e);
+    }
+
+    // grids, pass descriptors and the queue
+    std::vector<QGrid> qg(count);
+    std::vector<Pass2D> desc;
+    std::vector<QItem> items;
+    int ndone = 0, nsrcf = 0, maxp = 0;
+    for (int g = 0; g < count && rc == ST_OK; g++) {
+        const stencil_batch_grid &q = B->grid[g];
+        const int P = B->passes[g];
+        QGrid &G = qg[g];
+        G.kind = q.kind;
+        G.ntx = (q.nx + cx - 1) / cx;
+        G.nseg = (q.ny + L - 1) / L;
+        G.P = P;
+        G.nx = q.nx;
+        G.ny = q.ny;
+        G.done_off = ndone;
+        ndone += G.ntx * G.nseg;
+        G.srcf_off = nsrcf;
+        if (q.kind == ST_THERMAL && P > 0) nsrcf += G.ntx * G.nseg;
+        G.pass_base = (int)desc.size();
+        G.power = static_cast<const float *>(q.power);
+        G.src = B->src[g];
+        G.amb = q.coeffs[4];
+        G.rz = q.coeffs[3];
+        G.sdc = q.coeffs[0];
+        G.copy_from = nullptr;
+        G.ld_copy = q.nx;
+        G.copy_to = static_cast<float *>(q.grid_out);
+        maxp = std::max(maxp, P);
+        const int last = P > 0 ? q.steps - T * (P - 1) : 0;
+        for (int p = 0; p < P; p++) {
+            Pass2D a = {};
+            a.in = p == 0 ? static_cast<const float *>(q.grid_in) : B->scratch[2 * g + (p - 1) % 2];
+            a.ld_in = p == 0 ? q.nx : B->ld_scratch[g];
+            a.out = p == P - 1 ? static_cast<float *>(q.grid_out) : B->scratch[2 * g + p % 2];
+            a.ld_out = p == P - 1 ? q.nx : B->ld_scratch[g];
+            a.pw = B->src[g];   // Hotspot: sdc*(p + amb*Rz), rebuilt at every replay
+            a.ld_pw = q.nx;
+            a.nx = q.nx;
+            a.ny = q.ny;
+            a.tsteps = (p == P - 1) ? last : T;
+            a.ntx = G.ntx;
+            a.total_rows = (long long)a.ntx * q.ny;
+            for (int i = 0; i < 5; i++) a.k[i] = a.kf[i] = q.coeffs[i];
+            a.kf[5] = q.coeffs[0] * q.coeffs[2];
+            a.kf[6] = -2.0f * q.coeffs[2];
+            if (q.kind == ST_THERMAL) hot_coeffs_src(q.coeffs, a.kf);   // source-map kernels
+            a.vec_in = ((uintptr_t)a.in % 16 == 0) && (a.ld_in % 4 == 0);
+            a.vec_out = ((uintptr_t)a.out % 16 == 0) && (a.ld_out % 4 == 0);
+            a.vec_pw = a.pw ? (((uintptr_t)a.pw % 16 == 0) && (q.nx % 4 == 0)) : 0;
+            desc.push_back(a);
+        }
+        if (P == 0 && q.grid_in != q.grid_out) {
+            G.copy_from = static_cast<const float *>(q.grid_in);   // no steps: a plain copy
+            G.ld_copy = q.nx;
         }
     }
-    // launches: group (kind, T, V) x pass index
-    std::vector<LaunchRec> recs;
-    std::map<std::tuple<int, int, int>, std::vector<int>> groups;
-    for (int g = 0; g < count; g++)
-        if (B->passes[g] > 0) groups[std::make_tuple(B->grid[g].kind, B->T[g], B->V[g])].push_back(g);
-    // Level the work of a group's launches: grid g's P_g passes occupy launch slots
-    // [start_g, start_g + P_g) of the group's timeline of max P slots; largest grids first, each
-    // at the start that keeps the heaviest slot it touches lightest.
+    // Queue order.  Each grid's pass chain is placed on a common timeline of `maxp` slots so
+    // that the work per slot is level: the grids with the most work first, each at the start
+    // slot that keeps the heaviest slot it touches lightest (a grid of few passes fills in
+    // beside the long chains, which start at once: they set the launch's critical path).
+    // Items go in slot order (source-map rows first, copies last); within a slot by grid, row
+    // segment, tile column.  Every item depends only on items before it: its grid's previous
+    // pass sits in an earlier slot.
     std::vector<int> start(count, 0);
-    int maxp = 0;
-    for (int g = 0; g < count; g++) maxp = std::max(maxp, B->passes[g]);
-    for (auto &kv : groups) {
-        int S = 0;
-        for (int g : kv.second) S = std::max(S, B->passes[g]);
-        std::vector<double> load(S, 0.0);
-        std::vector<int> order = kv.second;
+    {
+        std::vector<double> load(std::max(maxp, 1), 0.0);
+        std::vector<int> order;
+        for (int g = 0; g < count; g++)
+            if (qg[g].P > 0) order.push_back(g);
         std::sort(order.begin(), order.end(), [&](int a, int b) {
-            return (double)B->grid[a].nx * B->grid[a].ny * B->passes[a] >
-                   (double)B->grid[b].nx * B->grid[b].ny * B->passes[b];
+            const double wa = (double)qg[a].nx * qg[a].ny * qg[a].P;
+            const double wb = (double)qg[b].nx * qg[b].ny * qg[b].P;
+            return wa != wb ? wa > wb : a < b;
         });
         for (int g : order) {
-            const int P = B->passes[g];
-            const double wgt = (double)B->grid[g].nx * B->grid[g].ny;
+            const int P = qg[g].P;
+            const double wgt = (double)qg[g].nx * qg[g].ny;
             int best_s = 0;
             double best_m = 1e300, best_sum = 1e300;
-            for (int s0 = 0; s0 + P <= S; s0++) {
+            for (int s0 = 0; s0 + P <= maxp; s0++) {
                 double m = 0.0, sum = 0.0;
                 for (int k = s0; k < s0 + P; k++) {
                     m = std::max(m, load[k]);
@@ -198,151 +264,78 @@ int stencil_batch_create(stencil_batch *out, const stencil_batch_grid *grids, in
             for (int k = best_s; k < best_s + P; k++) load[k] += wgt;
         }
     }
-    size_t table = 0;
-    std::vector<int> group_of(count, -1);
-    {
-        int gi = 0;
-        for (auto &kv : groups) {
-            for (int g : kv.second) group_of[g] = gi;
-            gi++;
+    for (int g = 0; g < count && rc == ST_OK; g++)
+        if (B->grid[g].kind == ST_THERMAL && qg[g].P > 0)
+            for (int s = 0; s < qg[g].nseg; s++)
+                for (int tx = 0; tx < qg[g].ntx; tx++) items.push_back(QItem{g, -1, tx, s});
+    for (int slot = 0; slot < maxp && rc == ST_OK; slot++)
+        for (int g = 0; g < count; g++) {
+            const int p = slot - start[g];
+            if (p < 0 || p >= qg[g].P) continue;
+            for (int s = 0; s < qg[g].nseg; s++)
+                for (int tx = 0; tx < qg[g].ntx; tx++) items.push_back(QItem{g, p, tx, s});
         }
-    }
-    for (int slot = 0; slot < maxp && rc == ST_OK; slot++) {
-        int gi = -1;
-        for (auto &kv : groups) {
-            gi++;
-            const int kind = std::get<0>(kv.first), T = std::get<1>(kv.first), V = std::get<2>(kv.first);
-            LaunchRec r;
-            r.group = gi;
-            r.shape = Shape2D{kind, 0, T, V, 1};
-            const int bx = 32 * V, h = (T + 3) / 4 * 4, cx = bx - 2 * h;
-            r.prefix.push_back(0);
-            for (int g : kv.second) {
-                const stencil_batch_grid &q = B->grid[g];
-                const int P = B->passes[g];
-                const int p = slot - start[g];   // this grid's pass in this slot
-                if (p < 0 || p >= P) continue;
-                const int last = q.steps - T * (P - 1);
-                const bool shift = (q.grid_in == q.grid_out) && (P % 2 == 1);
-                auto to_out = [&](int i) { return shift ? ((P - i) % 2 == 0) : ((P - 1 - i) % 2 == 0); };
-                Pass2D a = {};
-                const bool src_in = (p == 0);
-                const bool src_out = !src_in && to_out(p - 1);
-                a.in = src_in ? static_cast<const float *>(q.grid_in)
-                              : (src_out ? static_cast<const float *>(q.grid_out) : B->scratch[g]);
-                a.ld_in = (src_in || src_out) ? q.nx : B->ld_scratch[g];
-                a.out = to_out(p) ? static_cast<float *>(q.grid_out) : B->scratch[g];
-                a.ld_out = to_out(p) ? q.nx : B->ld_scratch[g];
-                a.pw = B->src[g];   // Hotspot: p + amb*Rz, rebuilt at every replay
-                a.ld_pw = q.nx;
-                a.nx = q.nx;
-                a.ny = q.ny;
-                a.tsteps = (p == P - 1) ? last : T;
-                a.ntx = (q.nx + cx - 1) / cx;
-                a.total_rows = (long long)a.ntx * q.ny;
-                for (int i = 0; i < 5; i++) a.k[i] = a.kf[i] = q.coeffs[i];
-                a.kf[5] = q.coeffs[0] * q.coeffs[2];
-                a.kf[6] = -2.0f * q.coeffs[2];
-                if (q.kind == ST_THERMAL) hot_coeffs_src(q.coeffs, a.kf);   // source-map kernels
-                a.vec_in = ((uintptr_t)a.in % 16 == 0) && (a.ld_in % 4 == 0);
-                a.vec_out = ((uintptr_t)a.out % 16 == 0) && (a.ld_out % 4 == 0);
-                a.vec_pw = a.pw ? (((uintptr_t)a.pw % 16 == 0) && (q.nx % 4 == 0)) : 0;
-                r.desc.push_back(a);
-                r.prefix.push_back(r.prefix.back() + a.total_rows);
-            }
-            if (r.desc.empty()) continue;
-            int bps = 0;
-            e = tb2d_batch_prepare(r.shape, &bps);
-            if (e != cudaSuccess || bps < 1) {
-                rc = e != cudaSuccess ? status(e) : ST_ERR_UNSUPPORTED;
-                break;
-            }
-            r.bp.ngrids = (int)r.desc.size();
-            r.bp.total_units = r.prefix.back();
-            const long long min_rows = 4;   // short segments keep small grids parallel
-            const long long ctas = std::min<long long>((long long)B->sms * bps,
-                                                       std::max<long long>(1, r.bp.total_units / min_rows));
-            r.bp.units_per_cta = (r.bp.total_units + ctas - 1) / ctas;
-            r.bp.ctas = (int)((r.bp.total_units + r.bp.units_per_cta - 1) / r.bp.units_per_cta);
-            r.desc_off = table;
-            table += (r.desc.size() * sizeof(Pass2D) + 255) / 256 * 256;
-            r.prefix_off = table;
-            table += (r.prefix.size() * sizeof(long long) + 255) / 256 * 256;
-            recs.push_back(std::move(r));
-        }
-    }
-    if (rc == ST_OK && table) {
+    for (int g = 0; g < count && rc == ST_OK; g++)
+        if (qg[g].copy_from)
+            for (int s = 0; s < qg[g].nseg; s++) items.push_back(QItem{g, qg[g].P, 0, s});
+    B->items = (long long)items.size();
+
+    // device table: [items | grids | descriptors | control | counters (reset per replay)]
+    const size_t o_items = 0;
+    const size_t o_grids = o_items + align256(items.size() * sizeof(QItem));
+    const size_t o_desc = o_grids + align256(qg.size() * sizeof(QGrid));
+    const size_t o_ctl = o_desc + align256(std::max<size_t>(1, desc.size()) * sizeof(Pass2D));
+    const size_t o_cnt = o_ctl + align256(sizeof(QueueCtl));
+    const size_t cnt_bytes = (size_t)(2 + ndone + nsrcf) * sizeof(int);   // head, status, counters
+    const size_t table = o_cnt + align256(cnt_bytes);
+    if (rc == ST_OK) {
         e = cudaMalloc(&B->dev, table);
         if (e != cudaSuccess) rc = status(e);
     }
-    if (rc == ST_OK && table) {
-        std::vector<unsigned char> host(table, 0);
-        for (LaunchRec &r : recs) {
-            std::memcpy(host.data() + r.desc_off, r.desc.data(), r.desc.size() * sizeof(Pass2D));
-            std::memcpy(host.data() + r.prefix_off, r.prefix.data(), r.prefix.size() * sizeof(long long));
-            r.bp.grids = reinterpret_cast<const Pass2D *>(static_cast<char *>(B->dev) + r.desc_off);
-            r.bp.prefix = reinterpret_cast<const long long *>(static_cast<char *>(B->dev) + r.prefix_off);
-        }
-        e = cudaMemcpy(B->dev, host.data(), table, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) rc = status(e);
-    }
-    // Capture every launch (and the in-place copies) into one graph.  Each group is a branch
-    // of its own (captured on its own stream, forked from and joined back into B->stream), so
-    // the groups' launches overlap on the GPU and one group's launch tails fill with another's
-    // work; within a branch, launch order is pass order.
+    char *d = static_cast<char *>(B->dev);
+    QueueBatch2D qb = {};
     if (rc == ST_OK) {
-        const int ng = (int)groups.size();
-        std::vector<cudaStream_t> gs(ng, nullptr);
-        std::vector<cudaEvent_t> join(ng, nullptr);
-        cudaEvent_t fork = nullptr;
-        e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
-        for (int i = 0; i < ng && e == cudaSuccess; i++) {
-            e = cudaStreamCreateWithFlags(&gs[i], cudaStreamNonBlocking);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
-        }
-        if (e == cudaSuccess) e = cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal);
+        std::vector<unsigned char> host(o_cnt, 0);
+        if (!items.empty()) std::memcpy(host.data() + o_items, items.data(), items.size() * sizeof(QItem));
+        std::memcpy(host.data() + o_grids, qg.data(), qg.size() * sizeof(QGrid));
+        if (!desc.empty()) std::memcpy(host.data() + o_desc, desc.data(), desc.size() * sizeof(Pass2D));
+        QueueCtl ctl = {kWaitNs, -1, 0};
+        std::memcpy(host.data() + o_ctl, &ctl, sizeof(ctl));
+        e = cudaMemcpy(B->dev, host.data(), o_cnt, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) rc = status(e);
+        B->ctl = reinterpret_cast<QueueCtl *>(d + o_ctl);
+        int *cnt = reinterpret_cast<int *>(d + o_cnt);
+        qb.items = reinterpret_cast<const QItem *>(d + o_items);
+        qb.total = (int)items.size();
+        qb.L = L;
+        qb.grids = reinterpret_cast<const QGrid *>(d + o_grids);
+        qb.passes = reinterpret_cast<const Pass2D *>(d + o_desc);
+        qb.head = reinterpret_cast<unsigned *>(cnt);
+        qb.status = cnt + 1;
+        qb.done = cnt + 2;
+        qb.srcf = cnt + 2 + ndone;
+        qb.ctl = B->ctl;
+        // as many one-warp blocks as are resident at once (no more: the rest would only pop
+        // items once earlier blocks leave)
+        qb.ctas = (int)std::max<long long>(1, std::min<long long>((long long)B->sms * bps,
+                                                                   (long long)items.size()));
+    }
+    // the graph: reset, the one launch, the status word back to the host
+    if (rc == ST_OK) {
+        e = cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            // Hotspot source maps from the power maps' current contents, before any pass
-            cudaError_t le = cudaSuccess;
-            for (int g = 0; g < count && le == cudaSuccess; g++)
-                if (B->src[g]) {
-                    const stencil_batch_grid &q = B->grid[g];
-                    le = hot_source(static_cast<const float *>(q.power), q.nx, B->src[g], q.nx,
-                                    q.ny, q.coeffs[4], q.coeffs[3], B->stream);
-                    B->launches++;
-                }
-            if (le == cudaSuccess) le = cudaEventRecord(fork, B->stream);
-            for (int i = 0; i < ng && le == cudaSuccess; i++) le = cudaStreamWaitEvent(gs[i], fork, 0);
-            for (const LaunchRec &r : recs) {
-                if (le == cudaSuccess) le = tb2d_batch_launch(r.shape, r.bp, gs[r.group]);
-                B->launches++;
+            cudaError_t le = cudaMemsetAsync(d + o_cnt, 0, cnt_bytes, B->stream);
+            if (le == cudaSuccess && qb.total > 0) {
+                le = tb2q_launch(T, V, qb, B->stream);
+                B->launches = 1;
             }
-            for (int g = 0; g < count && le == cudaSuccess; g++) {
-                const stencil_batch_grid &q = B->grid[g];
-                const int P = B->passes[g];
-                if (P == 0 && q.grid_in != q.grid_out)
-                    le = cudaMemcpyAsync(q.grid_out, q.grid_in, (size_t)q.nx * q.ny * sizeof(float),
-                                         cudaMemcpyDeviceToDevice, B->stream);
-                else if (P > 0 && q.grid_in == q.grid_out && P % 2 == 1)
-                    le = cudaMemcpy2DAsync(q.grid_out, (size_t)q.nx * sizeof(float), B->scratch[g],
-                                           (size_t)B->ld_scratch[g] * sizeof(float),
-                                           (size_t)q.nx * sizeof(float), q.ny,
-                                           cudaMemcpyDeviceToDevice, gs[group_of[g]]);
-            }
-            for (int i = 0; i < ng; i++) {
-                cudaError_t je = cudaEventRecord(join[i], gs[i]);
-                if (je == cudaSuccess) je = cudaStreamWaitEvent(B->stream, join[i], 0);
-                if (le == cudaSuccess) le = je;
-            }
+            if (le == cudaSuccess)
+                le = cudaMemcpyAsync(B->h_status, qb.status, sizeof(int), cudaMemcpyDeviceToHost,
+                                     B->stream);
             e = cudaStreamEndCapture(B->stream, &B->graph);
             if (le != cudaSuccess) e = le;
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&B->exec, B->graph, 0);
-        for (int i = 0; i < ng; i++) {
-            if (join[i]) cudaEventDestroy(join[i]);
-            if (gs[i]) cudaStreamDestroy(gs[i]);
-        }
-        if (fork) cudaEventDestroy(fork);
         if (e != cudaSuccess) rc = status(e);
     }
     if (rc != ST_OK) {
@@ -360,11 +353,28 @@ int stencil_batch_run(stencil_batch b)
     return status(cudaGraphLaunch(b->exec, b->stream));
 }
 
+int stencil_batch_sync(stencil_batch b)
+{
+    if (!b) return ST_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return ST_ERR_CUDA;
+    return *b->h_status ? ST_ERR_TIMEOUT : ST_OK;
+}
+
+int stencil_batch_set_wait(stencil_batch b, long long wait_ns, int hold_pass)
+{
+    if (!b || !b->ctl || wait_ns < 1 || hold_pass < -1) return ST_ERR_INVALID_ARG;
+    QueueCtl ctl = {wait_ns, hold_pass, 0};
+    cudaError_t e = cudaMemcpyAsync(b->ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    return e == cudaSuccess ? ST_OK : ST_ERR_CUDA;
+}
+
 int stencil_batch_get_grid(stencil_batch b, int g, int *T, int *vec, int *passes)
 {
     if (!b || g < 0 || g >= (int)b->grid.size() || !T || !vec || !passes) return ST_ERR_INVALID_ARG;
-    *T = b->T[g];
-    *vec = b->V[g];
+    *T = b->qT;
+    *vec = b->qV;
     *passes = b->passes[g];
     return ST_OK;
 }
@@ -387,6 +397,7 @@ int stencil_batch_destroy(stencil_batch b)
     for (float *s : b->src)
         if (s) cudaFree(s);
     if (b->dev) cudaFree(b->dev);
+    if (b->h_status) cudaFreeHost(b->h_status);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
     return ST_OK;

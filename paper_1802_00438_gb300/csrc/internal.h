@@ -40,41 +40,75 @@ struct Pass2D {
 };
 
 // stor: storage format (0 float32, 1 bf16, 2 fp16) plus 4 when the kernel stages the Hotspot
-// source map p + amb*Rz instead of the power map (every contracted Hotspot plan and batch)
+// source map sdc*(p + amb*Rz) instead of the power map (every contracted Hotspot plan and batch)
 struct Shape2D { int kind, exact, T, V, W; int stor = 0; };
-enum { STOR_SRC = 4,     // Hotspot: the power rows carry amb*Rz (source map)
+enum { STOR_SRC = 4,     // Hotspot: the power rows carry sdc*(p + amb*Rz) (source map)
        STOR_ALL = 8 };    // every fused step's rows are also written (trajectory passes)
 
-// One pass over many 2D grids (contracted kernels): grids[g] describes grid g's pass (its
-// tile columns ntx, sizes, buffers, coefficients, tsteps); prefix[g] = sum of ntx*ny of the
-// grids before g (prefix[ngrids] = total_units).  Device pointers.
-struct BatchPass2D {
-    const Pass2D *grids;
-    const long long *prefix;
-    int ngrids;
-    long long total_units;
-    long long units_per_cta;
+// Many 2D grids in ONE persistent launch fed by a work queue (k_tb2f_queue).  Items are
+// popped in queue order by the launch's blocks; an item is
+//   k = -1      : grid g's Hotspot source map sdc*(p + amb*Rz) over tile tx's compute columns,
+//                 rows [seg*L, seg*L + L)
+//   0 <= k < P  : pass k of grid g over tile column tx, rows [seg*L, seg*L + L)
+//   k = P = 0   : copy of those rows from copy_from (grid_in) to copy_to (grid_out), for a grid
+//                 with no steps
+// and it waits (bounded) for what it reads and overwrites: pass k > 0 needs pass k-1 of the
+// neighbouring tiles (tx +- 1, seg +- 1) finished (RAW on the halo, WAR on the ping-pong buffer
+// it writes), pass 0 of a Hotspot grid needs the source map of tiles (tx +- 1, seg +- 1).
+// done[g][seg][tx] holds the number of passes finished, srcf[g][seg][tx] 1 once the tile's
+// source map is written.
+struct QItem { int g, k, tx, seg; };
+struct QGrid {
+    int kind, ntx, nseg, P, nx, ny;
+    int done_off, srcf_off, pass_base;
+    const float *power;       // Hotspot: the power map (dense rows of nx)
+    float *src;               // Hotspot: the source map it builds
+    float amb, rz, sdc;
+    const float *copy_from;   // k = P items
+    long long ld_copy;
+    float *copy_to;
+};
+struct QueueCtl {
+    long long wait_ns;        // a dependency wait gives up after this long (status = 1)
+    int hold_pass;            // test hook, -1 = off: items of this pass never report finished
+    int pad;
+};
+struct QueueBatch2D {
+    const QItem *items;
+    int total;
+    int L;                    // rows per item
+    const QGrid *grids;
+    const Pass2D *passes;     // grids[g].pass_base + k
+    int *done;
+    int *srcf;
+    unsigned *head;           // next item
+    int *status;              // 0, or 1 once a wait gave up (every block then leaves)
+    const QueueCtl *ctl;
     int ctas;
 };
+bool tb2q_available(int T, int V);
+cudaError_t tb2q_prepare(int T, int V, int *blocks_per_sm);
+cudaError_t tb2q_launch(int T, int V, const QueueBatch2D &q, cudaStream_t st);
 
-bool tb2d_batch_available(const Shape2D &s);
-cudaError_t tb2d_batch_prepare(const Shape2D &s, int *blocks_per_sm);
-cudaError_t tb2d_batch_launch(const Shape2D &s, const BatchPass2D &bp, cudaStream_t st);
 
 // Block codec of the 16-bit storage: one (offset, scale) per (row, tile column) of the tiling
 // with compute width cx; x = offset + scale * q, q in [-1, 1].
+// src_mul != 0: code the Hotspot source map sdc*(p + amb*Rz) of the power map src instead
+// (src_mul = sdc, src_add = amb*Rz rounded once)
 cudaError_t lp_encode(int stor, const float *src, long long ld_src, void *dst, long long ld_q,
-                      float2 *meta, int nx, int ny, int cx, cudaStream_t st);
+                      float2 *meta, int nx, int ny, int cx, cudaStream_t st, float src_add = 0.f,
+                      float src_mul = 0.f);
 cudaError_t lp_decode(int stor, const void *src, long long ld_q, const float2 *meta, float *dst,
                       long long ld_dst, int nx, int ny, int cx, cudaStream_t st);
 
 // Contracted Hotspot coefficients of the source-map kernels (STOR_SRC) from [sdc, Rx, Ry, Rz,
-// amb]: kf = [sdc, Rx', Ry', Rz, amb, fl(sdc*Ry'), -(2Rx' + 2Ry')] with 2Rx' + 2Ry' exact
+// amb]: kf = [cc, cx, cy, cz, amb, cy, 0] with cx ~ sdc*Rx, cy ~ sdc*Ry rounded so that
+// cc = 1 - 2cx - 2cy is exact, cz = sdc*Rz
 void hot_coeffs_src(const float *k, float *kf);
 
-// Hotspot source map dst = p + amb*Rz (dense rows of nx), read by the contracted kernels
+// Hotspot source map dst = sdc*(p + amb*Rz) (dense rows of nx), read by the contracted kernels
 cudaError_t hot_source(const float *p, long long ld_p, float *dst, int nx, int ny, float amb,
-                       float rz, cudaStream_t st);
+                       float rz, float sdc, cudaStream_t st);
 
 bool tb2d_available(const Shape2D &s);
 int tb2d_block_threads(const Shape2D &s);

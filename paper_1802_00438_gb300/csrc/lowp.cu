@@ -1,5 +1,5 @@
 // Block codec of the 16-bit grid storage (bf16 or fp16 with a float32 code per block), and the
-// Hotspot source map p + amb*Rz that the contracted kernels stage instead of the power map.
+// Hotspot source map sdc*(p + amb*Rz) that the contracted kernels stage instead of the power map.
 //
 // A block is the segment of one row that one tile column computes: cells
 // [b*cx, min((b+1)*cx, nx)) of row y, with cx the compute width of the plan's tiling, so the
@@ -36,11 +36,13 @@ __device__ __forceinline__ float dec(unsigned q)
 }
 
 // one warp per block (row y, block b)
+// with src_mul != 0 the values coded are the Hotspot source map sdc*(p + amb*Rz) of the power
+// map src (src_mul = sdc, src_add = amb*Rz), rounded as k_hot_source rounds them
 template <int STOR>
 __global__ void __launch_bounds__(256) k_lp_encode(const float *__restrict__ src, long long ld_src,
                                                    uint16_t *__restrict__ dst, long long ld_q,
                                                    float2 *__restrict__ meta, int nx, int ny,
-                                                   int cx, int ntx)
+                                                   int cx, int ntx, float src_add, float src_mul)
 {
     const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -49,8 +51,12 @@ __global__ void __launch_bounds__(256) k_lp_encode(const float *__restrict__ src
     const int x0 = b * cx, x1 = min(x0 + cx, nx);
     const float *row = src + (long long)y * ld_src;
     float lo = __int_as_float(0x7f800000), hi = -lo;
-    for (int x = x0 + lane; x < x1; x += 32) {
+    auto val = [&](int x) {
         const float v = row[x];
+        return src_mul != 0.f ? __fmul_rn(src_mul, __fadd_rn(v, src_add)) : v;
+    };
+    for (int x = x0 + lane; x < x1; x += 32) {
+        const float v = val(x);
         lo = fminf(lo, v);
         hi = fmaxf(hi, v);
     }
@@ -62,7 +68,7 @@ __global__ void __launch_bounds__(256) k_lp_encode(const float *__restrict__ src
     const float inv = __frcp_rn(sc);
     uint16_t *q = dst + (long long)y * ld_q;
     for (int x = x0 + lane; x < x1; x += 32)
-        q[x] = (uint16_t)enc<STOR>((row[x] - mid) * inv);   // |q| <= 1 + 3 * 2^-24: rounds to 1
+        q[x] = (uint16_t)enc<STOR>((val(x) - mid) * inv);   // |q| <= 1 + 3 * 2^-24: rounds to 1
     if (lane == 0) meta[(long long)y * ntx + b] = make_float2(mid, sc);
 }
 
@@ -79,11 +85,11 @@ __global__ void __launch_bounds__(256) k_lp_decode(const uint16_t *__restrict__ 
     dst[(long long)y * ld_dst + x] = __fmaf_rn(m.y, dec<STOR>(src[(long long)y * ld_q + x]), m.x);
 }
 
-// Hotspot source row: p + amb*Rz (the product rounded once, as the kernels round it); one
-// block row per grid row, four cells per thread (16-byte accesses when rows are aligned)
+// Hotspot source row: sdc*(p + amb*Rz), each operation rounded once; one block row per grid
+// row, four cells per thread (16-byte accesses when rows are aligned)
 __global__ void __launch_bounds__(256) k_hot_source(const float *__restrict__ p, long long ld_p,
                                                     float *__restrict__ dst, int nx, float amb,
-                                                    float rz, int vec)
+                                                    float rz, float sdc, int vec)
 {
     const int y = blockIdx.y;
     const int x = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -94,9 +100,10 @@ __global__ void __launch_bounds__(256) k_hot_source(const float *__restrict__ p,
     if (vec) {
         const float4 v = *reinterpret_cast<const float4 *>(src);
         *reinterpret_cast<float4 *>(d) =
-            make_float4(__fadd_rn(v.x, a), __fadd_rn(v.y, a), __fadd_rn(v.z, a), __fadd_rn(v.w, a));
+            make_float4(__fmul_rn(sdc, __fadd_rn(v.x, a)), __fmul_rn(sdc, __fadd_rn(v.y, a)),
+                        __fmul_rn(sdc, __fadd_rn(v.z, a)), __fmul_rn(sdc, __fadd_rn(v.w, a)));
     } else {
-        for (int j = 0; j < 4 && x + j < nx; j++) d[j] = __fadd_rn(src[j], a);
+        for (int j = 0; j < 4 && x + j < nx; j++) d[j] = __fmul_rn(sdc, __fadd_rn(src[j], a));
     }
 }
 
@@ -104,31 +111,38 @@ __global__ void __launch_bounds__(256) k_hot_source(const float *__restrict__ p,
 
 void hot_coeffs_src(const float *k, float *kf)
 {
-    // kf = [sdc, Rx', Ry', Rz, amb, fl(sdc*Ry'), -(2Rx' + 2Ry')] where Rx', Ry' are Rx, Ry with
-    // the bits below half an ulp of 2Rx + 2Ry cleared, so that 2Rx' + 2Ry' is exact in float32:
-    // the centre weight then cancels the four neighbour weights exactly on a uniform field and
-    // the folded constant moves no fixed point (Rx', Ry' differ from Rx, Ry by < 1e-7 relative)
-    const double rx = k[1], ry = k[2];
-    double ul = std::ldexp(1.0, std::ilogb((float)(2.0 * rx + 2.0 * ry)) - 23);
-    double rxq = 0, ryq = 0;
-    for (int i = 0; i < 3; i++) {
-        rxq = std::nearbyint(rx / (ul / 2)) * (ul / 2);
-        ryq = std::nearbyint(ry / (ul / 2)) * (ul / 2);
-        const double sum = 2 * rxq + 2 * ryq;
-        if ((double)(float)sum == sum) break;
-        ul *= 2;   // the sum crossed into the next binade
+    // The Hotspot update c + sdc*(p + (n+s-2c)*Ry + (e+w-2c)*Rx + (amb-c)*Rz) (Table 2) as
+    //   cc*c + cx*(e+w) + cy*(n+s) - cz*c + src,   src = sdc*(p + amb*Rz) (a per-cell map)
+    // with cx = sdc*Rx, cy = sdc*Ry, cz = sdc*Rz and cc = 1 - 2cx - 2cy.  cx and cy are sdc*Rx,
+    // sdc*Ry rounded to multiples of half an ulp of cc, so that cc is exact in float32 and
+    // cc + 2cx + 2cy = 1 holds exactly: a uniform field then loses exactly cz*c per step to the
+    // ambient term and gains src, with no drift from rounded weights (the weights move by less
+    // than 2e-7 relative).  kf = [cc, cx, cy, cz, amb, cy, 0].
+    const double sdc = k[0], rx = k[1], ry = k[2], rz = k[3];
+    const double cx0 = sdc * rx, cy0 = sdc * ry;
+    double cxq = cx0, cyq = cy0, cc = 1.0 - 2 * cx0 - 2 * cy0;
+    if (cc > 0.0) {
+        double ul = std::ldexp(1.0, std::ilogb((float)cc) - 23);
+        for (int i = 0; i < 4; i++) {
+            cxq = std::nearbyint(cx0 / (ul / 2)) * (ul / 2);
+            cyq = std::nearbyint(cy0 / (ul / 2)) * (ul / 2);
+            cc = 1.0 - 2 * cxq - 2 * cyq;
+            if ((double)(float)cc == cc && (double)(float)cxq == cxq && (double)(float)cyq == cyq)
+                break;
+            ul /= 2;   // cc fell into the binade below
+        }
     }
-    kf[0] = k[0];
-    kf[1] = (float)rxq;
-    kf[2] = (float)ryq;
-    kf[3] = k[3];
+    kf[0] = (float)cc;
+    kf[1] = (float)cxq;
+    kf[2] = (float)cyq;
+    kf[3] = (float)(sdc * rz);
     kf[4] = k[4];
-    kf[5] = kf[0] * kf[2];
-    kf[6] = -(float)(2 * rxq + 2 * ryq);
+    kf[5] = (float)cyq;
+    kf[6] = 0.f;
 }
 
 cudaError_t hot_source(const float *p, long long ld_p, float *dst, int nx, int ny, float amb,
-                       float rz, cudaStream_t st)
+                       float rz, float sdc, cudaStream_t st)
 {
     if (nx < 1 || ny < 1) return cudaErrorInvalidValue;
     const int vec = ((uintptr_t)p % 16 == 0) && ((uintptr_t)dst % 16 == 0) && (nx % 4 == 0) &&
@@ -138,7 +152,7 @@ cudaError_t hot_source(const float *p, long long ld_p, float *dst, int nx, int n
     for (long long y0 = 0; y0 < ny; y0 += 65535) {
         const unsigned rows = (unsigned)std::min<long long>(65535, ny - y0);
         k_hot_source<<<dim3(bx, rows), 256, 0, st>>>(p + y0 * ld_p, ld_p, dst + y0 * nx, nx, amb,
-                                                     rz, vec);
+                                                     rz, sdc, vec);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -146,14 +160,19 @@ cudaError_t hot_source(const float *p, long long ld_p, float *dst, int nx, int n
 }
 
 cudaError_t lp_encode(int stor, const float *src, long long ld_src, void *dst, long long ld_q,
-                      float2 *meta, int nx, int ny, int cx, cudaStream_t st)
+                      float2 *meta, int nx, int ny, int cx, cudaStream_t st, float src_add,
+                      float src_mul)
 {
     const int ntx = (nx + cx - 1) / cx;
     const long long warps = (long long)ny * ntx;
     const int blocks = (int)((warps * 32 + 255) / 256);
     uint16_t *q = static_cast<uint16_t *>(dst);
-    if (stor == 1) k_lp_encode<1><<<blocks, 256, 0, st>>>(src, ld_src, q, ld_q, meta, nx, ny, cx, ntx);
-    else k_lp_encode<2><<<blocks, 256, 0, st>>>(src, ld_src, q, ld_q, meta, nx, ny, cx, ntx);
+    if (stor == 1)
+        k_lp_encode<1><<<blocks, 256, 0, st>>>(src, ld_src, q, ld_q, meta, nx, ny, cx, ntx, src_add,
+                                               src_mul);
+    else
+        k_lp_encode<2><<<blocks, 256, 0, st>>>(src, ld_src, q, ld_q, meta, nx, ny, cx, ntx, src_add,
+                                               src_mul);
     return cudaGetLastError();
 }
 

@@ -12,14 +12,17 @@
 //   out(y-1) = P + cs * d                      (the only operation on the stage-to-stage path)
 //   P'       = Q + cc * d + cw * d_w + ce * d_e  (row y, missing only its south term)
 //   Q'       = cn * d                           (row y+1's north term)
-// Hotspot 2D uses the same split of c + sdc*(p + (n+s-2c)*Ry + (e+w-2c)*Rx + (amb-c)*Rz):
-//   out(y-1) = P + (sdc*Ry) * d
-//   P'       = d + sdc * (Q + (d_e+d_w-2d)*Rx + (amb-d)*Rz - 2Ry*d)
-//   Q'       = Ry * d + p(y+1)
+// Hotspot 2D, c + sdc*(p + (n+s-2c)*Ry + (e+w-2c)*Rx + (amb-c)*Rz), uses the same split of its
+// expansion cc*c + cx*(e+w) + cy*(n+s) - cz*c + src (cx = sdc*Rx, cy = sdc*Ry, cz = sdc*Rz,
+// cc = 1 - 2cx - 2cy exact in float32, src = sdc*(p + amb*Rz) a per-cell map built once per run):
+//   out(y-1) = P + cy * d
+//   P'       = Q + cx * (d_e + d_w) + cc * d - cz * d
+//   Q'       = cy * d + src(y+1)
 // P' accumulates on top of Q and Q' is written where P was, so the two partial rows trade
 // places every row: the row loop is unrolled twice with the roles swapped and every update is
 // in place (no register copies).  Counted work per cell is unchanged (Table 2: 9 and 15 flops,
-// issued as 5 and 9 operations).
+// issued as 5 and 6 operations; the plain-power Hotspot instances of the allocation-free entry
+// point issue 9).
 //
 // GPU mapping: one warp per block; a tile is BX = 32*V cells wide incl. halos of
 // H = roundup(T, 4) cells per side; thread = V consecutive cells; x-neighbours of a thread's
@@ -39,10 +42,10 @@
 namespace stn {
 
 enum { STOR_F32 = 0, STOR_BF16 = 1, STOR_F16 = 2 };
-// Flag added to STOR (Hotspot): the power ring holds p + amb*Rz instead of p, so each stage's
-// ambient term is one fused multiply-add (-Rz*c) instead of a subtraction and a multiply-add.
-// Float32 plans stage a precomputed copy of the power map; 16-bit plans add amb*Rz as they
-// decode a power row.
+// Flag added to STOR (Hotspot): the power ring holds the source map sdc*(p + amb*Rz) instead of
+// p, and the coefficients are the expanded weights (hot_coeffs_src), so a stage issues six
+// operations per cell instead of nine.  Float32 plans stage a map built once per run; 16-bit
+// plans code the map itself in place of the power map.
 __host__ __device__ constexpr int stor_fmt(int s) { return s & 3; }
 __host__ __device__ constexpr bool stor_src(int s) { return (s & STOR_SRC) != 0; }
 __host__ __device__ constexpr bool stor_all(int s) { return (s & STOR_ALL) != 0; }
@@ -78,7 +81,7 @@ struct TB2F {
 
 struct CoefF {
     // diffusion: cc, cw, ce, cs, cn; Hotspot: sdc, Rx, Ry, Rz, amb, sdc*Ry, -2*Ry; source-map
-    // Hotspot kernels (STOR_SRC): sdc, Rx', Ry', Rz, amb, sdc*Ry', -(2Rx' + 2Ry') (host-made)
+    // Hotspot kernels (STOR_SRC): cc, cx, cy, cz, amb, cy, 0 (host-made, hot_coeffs_src)
     float a0, a1, a2, a3, a4, a5, a6;
 };
 
@@ -203,7 +206,6 @@ struct CtxF {
     long long ld_q;        // row pitch of 16-bit grids (cells)
     int ntx, tx;           // tile columns; my tile column
     int msel;              // which of the three blocks of a loaded row my cells belong to
-    float src_add;         // amb * Rz (STOR_SRC, rounded once)
     float *st_states;      // trajectory passes (STOR_ALL): where step t's rows go
     long long st_stride;
 };
@@ -299,11 +301,9 @@ __device__ __forceinline__ void stf(const CtxF &c, const CoefF &k, int y, bool f
 #pragma unroll
         for (int j = 0; j < V; j++) {
             if (SRC) {
-                // the power row carries amb*Rz: (amb - c)*Rz + p = (p + amb*Rz) - Rz*c; and
-                // (e + w - 2c)*Rx - 2c*Ry = (e + w)*Rx' - (2Rx' + 2Ry')*c with the folded weight
-                // exact (a1 = Rx', a6 = -(2Rx' + 2Ry'))
+                // Q (cy*n + src) + cx*(e + w) + cc*c - cz*c: the expanded weights, cc exact
                 Pn[j] = __fmaf_rn(k.a1, __fadd_rn(de[j], dw[j]), Xq[j]);
-                Pn[j] = __fmaf_rn(k.a6, d[j], Pn[j]);
+                Pn[j] = __fmaf_rn(k.a0, d[j], Pn[j]);
                 Pn[j] = __fmaf_rn(-k.a3, d[j], Pn[j]);
             } else {
                 const float t2 = __fmaf_rn(-2.0f, d[j], __fadd_rn(de[j], dw[j]));
@@ -311,8 +311,8 @@ __device__ __forceinline__ void stf(const CtxF &c, const CoefF &k, int y, bool f
                 const float t3 = __fsub_rn(k.a4, d[j]);
                 Pn[j] = __fmaf_rn(t3, k.a3, Pn[j]);
                 Pn[j] = __fmaf_rn(k.a6, d[j], Pn[j]);
+                Pn[j] = __fmaf_rn(k.a0, Pn[j], d[j]);
             }
-            Pn[j] = __fmaf_rn(k.a0, Pn[j], d[j]);
         }
     }
     qf<KIND, V>(c, k, d, p_next, Qn);
@@ -389,15 +389,14 @@ __device__ __forceinline__ void tbf_iter(const CtxF &c, const CoefF &k,
             float pv[V];
             lds_row<V>(pbase - C::ROWB, c, pv);   // power of row R0-1
             if (stor_src(STOR)) {
-                // the source-map form of the Hotspot update (see stf): folded ambient term and
-                // folded centre weight
+                // the source-map form of the Hotspot update (see stf): src + cx*(e + w) +
+                // cy*(n + s) + cc*c - cz*c
 #pragma unroll
                 for (int j = 0; j < V; j++) {
                     float q = __fmaf_rn(k.a1, __fadd_rn(e[j], w[j]), pv[j]);
                     q = __fmaf_rn(k.a2, __fadd_rn(u[j], dd[j]), q);
-                    q = __fmaf_rn(k.a6, m[j], q);
-                    q = __fmaf_rn(-k.a3, m[j], q);
-                    out[j] = __fmaf_rn(k.a0, q, m[j]);
+                    q = __fmaf_rn(k.a0, m[j], q);
+                    out[j] = __fmaf_rn(-k.a3, m[j], q);
                 }
             } else {
 #pragma unroll
@@ -470,7 +469,7 @@ __device__ __forceinline__ void tbf_iter(const CtxF &c, const CoefF &k,
 
 // Decode my V cells of a staged raw row (header: codes of the blocks tx-1, tx, tx+1) into a
 // float ring row (and into its mirror when mirror != 0).
-template <int V, int STOR, bool ADD = false>
+template <int V, int STOR>
 __device__ __forceinline__ void tbf_decode(const CtxF &c, uint32_t raw, uint32_t dst, uint32_t mirror)
 {
     const uint2 cw = lds64u(raw + 8u * c.msel);
@@ -482,12 +481,6 @@ __device__ __forceinline__ void tbf_decode(const CtxF &c, uint32_t raw, uint32_t
         float x1 = __fmaf_rn(sc, q2f<STOR>(w.x >> 16), mid);
         float x2 = __fmaf_rn(sc, q2f<STOR>(w.y & 0xffffu), mid);
         float x3 = __fmaf_rn(sc, q2f<STOR>(w.y >> 16), mid);
-        if (ADD) {   // power row of a STOR_SRC kernel: p + amb*Rz
-            x0 = __fadd_rn(x0, c.src_add);
-            x1 = __fadd_rn(x1, c.src_add);
-            x2 = __fadd_rn(x2, c.src_add);
-            x3 = __fadd_rn(x3, c.src_add);
-        }
         sts128(dst + c.oq[t], x0, x1, x2, x3);
         if (mirror) sts128(mirror + c.oq[t], x0, x1, x2, x3);
     }
@@ -555,8 +548,8 @@ __device__ __forceinline__ void tbf_step(const CtxF &c, const CoefF &k,
     __syncwarp();
     if (stor_fmt(STOR) != STOR_F32) {       // decode row i into the float rings
         tbf_decode<V, STOR>(c, c.sRF + r.rr * C::RAWB, c.sF + r.rf * C::ROWB, 0u);
-        if (KIND == KTHERM)
-            tbf_decode<V, STOR, stor_src(STOR)>(c, c.sRP + r.rr * C::RAWB, c.sP + r.rp * C::ROWB,
+        if (KIND == KTHERM)   // (for STOR_SRC the coded map is the source map itself)
+            tbf_decode<V, STOR>(c, c.sRP + r.rr * C::RAWB, c.sP + r.rp * C::ROWB,
                                 r.rp < C::PW - 1 ? c.sP + (C::NBP + r.rp) * C::ROWB : 0u);
         __syncwarp();
     }
@@ -667,8 +660,7 @@ __device__ __forceinline__ void tbf_range(const Pass2D &p, long long f, const lo
     CoefF k;
     k.a0 = p.kf[0]; k.a1 = p.kf[1]; k.a2 = p.kf[2]; k.a3 = p.kf[3]; k.a4 = p.kf[4];
     k.a5 = p.kf[5];   // Hotspot: sdc * Ry
-    k.a6 = p.kf[6];   // Hotspot: -2 Ry (source-map kernels: -(2Rx' + 2Ry'))
-    c.src_add = __fmul_rn(k.a4, k.a3);   // Hotspot: amb * Rz
+    k.a6 = p.kf[6];   // Hotspot: -2 Ry (source-map kernels: unused)
     c.st_states = p.states;
     c.st_stride = p.state_stride;
 
@@ -805,34 +797,6 @@ __global__ void __launch_bounds__(32) k_tb2f(const Pass2D p)
         for (int j = 0; j < V; j++) A[s][j] = B[s][j] = 0.f;
     const long long f = (long long)blockIdx.x * p.rows_per_cta;
     tbf_range<KIND, T, V, SWAP, STOR>(p, f, min(f + p.rows_per_cta, p.total_rows), A, B, smem);
-}
-
-// Many grids in one launch: a work queue over the concatenated (tile column, row) units of all
-// grids (prefix[g] = units before grid g), split evenly over the blocks, so every block gets the
-// same number of rows whatever the grids' sizes.  Each grid carries its own sizes, buffers,
-// coefficients and step count for this pass.
-template <int KIND, int T, int V, bool SWAP>
-__global__ void __launch_bounds__(32) k_tb2f_batch(const BatchPass2D bp)
-{
-    constexpr int S = KIND == KTHERM ? STOR_SRC : STOR_F32;   // power maps carry amb*Rz
-    using C = TB2F<KIND, T, V, S>;
-    extern __shared__ __align__(16) float smem[];
-    float A[C::NS][V], B[C::NS][V];
-#pragma unroll
-    for (int s = 0; s < C::NS; s++)
-#pragma unroll
-        for (int j = 0; j < V; j++) A[s][j] = B[s][j] = 0.f;
-    long long f = (long long)blockIdx.x * bp.units_per_cta;
-    const long long fend = min(f + bp.units_per_cta, bp.total_units);
-    int g = 0;
-    while (f < fend) {
-        while (bp.prefix[g + 1] <= f) g++;
-        const Pass2D pg = bp.grids[g];
-        const long long lo = f - bp.prefix[g];
-        const long long hi = min(fend, bp.prefix[g + 1]) - bp.prefix[g];
-        tbf_range<KIND, T, V, SWAP, S>(pg, lo, hi, A, B, smem);
-        f += hi - lo;
-    }
 }
 
 }  // namespace stn

@@ -1,5 +1,7 @@
-"""Batched runs (many 2D grids of uneven sizes and step counts, one graph launch) against the
-oracle, grid by grid; graph replay; grids run in place."""
+"""Batched runs (many 2D grids of uneven sizes and step counts, one persistent kernel launch fed
+by a tile work queue, captured in a graph) against the oracle, grid by grid; graph replay; grids
+run in place; a dependency wait that runs out (a pass held back by the test hook, no fault)
+reported as ST_ERR_TIMEOUT with the batch and the context still usable."""
 import numpy as np
 import pytest
 
@@ -49,15 +51,16 @@ def test_batch_matches_oracle(eng, orc):
     ws, items = _make(eng)
     b = eng.Batch(items)
     b.run()
+    b.sync()
     torch.cuda.synchronize()
     for i, (w, it) in enumerate(zip(ws, items)):
         o = orc.run(w.kind, w.u0, w.coef, w.steps, w.power)
         g = it["grid_out"].cpu().numpy()
         assert max_rel(g, o) <= TOL, (i, w.nx, w.ny, w.steps, b.grid_info(i), max_rel(g, o))
-    assert b.launches() >= 1
+    assert b.launches() == 1                 # one persistent launch per replay
     # replay: grids not in place give the same result again; in-place ones advance further
     b.run()
-    torch.cuda.synchronize()
+    b.sync()
     for i, (w, it) in enumerate(zip(ws, items)):
         inplace = it["grid_out"].data_ptr() == it["grid_in"].data_ptr()
         steps = 2 * w.steps if inplace else w.steps
@@ -79,3 +82,30 @@ def test_batch_choices_and_errors(eng):
     bad["power"] = None                      # Hotspot without a power map
     with pytest.raises(eng.StencilError):
         eng.Batch([bad])
+
+
+def test_batch_bounded_wait_runs_out(eng, orc):
+    """The items of pass 0 are held back (they never report finished), so every pass-1 item
+    waits until the limit (20 ms) runs out: the launch leaves and sync reports ST_ERR_TIMEOUT.
+    Then the hook is removed and the same batch replays correctly (nothing was left waiting, the
+    context is intact)."""
+    import torch
+    ws, items = _make(eng, inplace_every=2)   # i % 2 == 2 never holds: no grid in place
+    b = eng.Batch(items)
+    b.set_wait(20_000_000, hold_pass=0)
+    b.run()
+    with pytest.raises(eng.StencilError) as e:
+        b.sync()
+    assert e.value.code == eng.ST_ERR_TIMEOUT
+    torch.cuda.synchronize()                 # the stream is idle: no block kept waiting
+    b.set_wait(1_000_000_000, hold_pass=-1)
+    b.run()
+    b.sync()
+    for i, (w, it) in enumerate(zip(ws, items)):
+        o = orc.run(w.kind, w.u0, w.coef, w.steps, w.power)
+        assert max_rel(it["grid_out"].cpu().numpy(), o) <= TOL, i
+    b.close()
+    with pytest.raises(eng.StencilError) as e:
+        b2 = eng.Batch(items)
+        b2.set_wait(0)                        # a limit must be positive
+    assert e.value.code == eng.ST_ERR_INVALID_ARG

@@ -146,7 +146,8 @@ def test_c5a_batch_as_configured(eng, orc):
                       "coeffs": w.coef})
     b = eng.Batch(items)
     b.run()
-    torch.cuda.synchronize()
+    b.sync()
+    assert b.launches() == 1
     for i, (w, it) in enumerate(zip(ws, items)):
         o = orc.run(w.kind, w.u0, w.coef, w.steps, w.power)
         err = max_rel(it["grid_out"].cpu().numpy(), o)
