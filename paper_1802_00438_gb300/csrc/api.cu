@@ -56,7 +56,8 @@ struct stencil_plan_s {
     double model = 0.0;   // calibrated model's prediction for this plan (1000 steps), GCell/s
     int tuned = 0;        // configuration taken from the tuning cache
     PassCfg2D traj;       // trajectory passes (stencil_run_trajectory)
-    float *src = nullptr;   // contracted float32 Hotspot 2D: the source map p + amb*Rz
+    float *src = nullptr;   // contracted float32 Hotspot 2D: the source map sdc*(p + amb*Rz)
+    long long ld_src = 0;   // its row pitch, floats
     int ntx_star = 0, nty_star = 0;   // star diffusion (rad > 1): tiles along x and y
     int nseg_star = 1, zseg_star = 0; // 3D star: z-segments per tile column, their length
     std::vector<PassCfg3D> cfg3;
@@ -401,7 +402,7 @@ int run_pass2(stencil_plan_s *p, const float *src, long long lds, float *dst, lo
     a.pw = pw;
     a.ld_in = lds;
     a.ld_out = ldd;
-    a.ld_pw = p->d.nx;
+    a.ld_pw = (p->src && pw == p->src) ? p->ld_src : p->d.nx;
     a.pw_plane = (long long)p->d.nx * p->d.ny;   // per-cell coefficient planes, dense
     a.nx = p->d.nx;
     a.ny = p->d.ny;
@@ -417,7 +418,7 @@ int run_pass2(stencil_plan_s *p, const float *src, long long lds, float *dst, lo
     a.vec_in = ((uintptr_t)src % 16 == 0) && (lds % 4 == 0);
     a.vec_out = ((uintptr_t)dst % 16 == 0) && (ldd % 4 == 0) &&
                 (!states || ((uintptr_t)states % 16 == 0 && stride % 4 == 0));
-    a.vec_pw = pw ? (((uintptr_t)pw % 16 == 0) && (p->d.nx % 4 == 0)) : 0;
+    a.vec_pw = pw ? (((uintptr_t)pw % 16 == 0) && (a.ld_pw % 4 == 0)) : 0;
     if (p->timing && p->ev_used + 2 > 2 * 1024) {
         rc = flush_timing(p);
         if (rc != ST_OK) return rc;
@@ -837,7 +838,9 @@ static int plan_create(stencil_plan *out, const stencil_desc *desc)
         if (e != cudaSuccess) rc = map_cuda(e);
     }
     if (rc == ST_OK && d.ndim == 2 && d.kind == ST_THERMAL && !d.exact && !p->stor) {
-        e = cudaMalloc(&p->src, (size_t)d.nx * d.ny * sizeof(float));
+        // rows padded to 32 cells like the scratch grid: 16-byte aligned rows for any nx
+        p->ld_src = ((long long)d.nx + 31) / 32 * 32;
+        e = cudaMalloc(&p->src, (size_t)p->ld_src * d.ny * sizeof(float));
         if (e != cudaSuccess) rc = map_cuda(e);
     }
     if (rc == ST_OK && !d.exact && !p->stor && d.rad <= 1 && d.kind != ST_DIFFUSION_VAR) {
@@ -927,7 +930,8 @@ int stencil_run(stencil_plan p, const void *grid_in, void *grid_out, const void 
     if (p->src) {
         // contracted Hotspot 2D kernels stage sdc*(p + amb*Rz) (Table 2's source and ambient
         // terms folded into one map)
-        e = hot_source(pw, d.nx, p->src, d.nx, d.ny, coeffs[4], coeffs[3], coeffs[0], p->stream);
+        e = hot_source(pw, d.nx, p->src, p->ld_src, d.nx, d.ny, coeffs[4], coeffs[3], coeffs[0],
+                       p->stream);
         if (e != cudaSuccess) return map_cuda(e);
         pw = p->src;
     }
@@ -983,8 +987,8 @@ int stencil_run_trajectory(stencil_plan p, const void *grid_in, void *states, lo
     if (p->src) {
         // contracted Hotspot kernels stage sdc*(p + amb*Rz) (Table 2's source and ambient terms
         // folded into one map)
-        const cudaError_t e = hot_source(pw, d.nx, p->src, d.nx, d.ny, coeffs[4], coeffs[3],
-                                         coeffs[0], p->stream);
+        const cudaError_t e = hot_source(pw, d.nx, p->src, p->ld_src, d.nx, d.ny, coeffs[4],
+                                         coeffs[3], coeffs[0], p->stream);
         if (e != cudaSuccess) return map_cuda(e);
         pw = p->src;
     }

@@ -163,8 +163,8 @@ int stencil_batch_create_ex(stencil_batch *out, const stencil_batch_grid *grids,
         const size_t sb = (size_t)B->ld_scratch[g] * q.ny * sizeof(float);
         if (B->passes[g] > 1) e = cudaMalloc(&B->scratch[2 * g], sb);
         if (e == cudaSuccess && B->passes[g] > 2) e = cudaMalloc(&B->scratch[2 * g + 1], sb);
-        if (e == cudaSuccess && B->passes[g] > 0 && q.kind == ST_THERMAL)
-            e = cudaMalloc(&B->src[g], (size_t)q.nx * q.ny * sizeof(float));
+        if (e == cudaSuccess && B->passes[g] > 0 && q.kind == ST_THERMAL)   // padded rows too
+            e = cudaMalloc(&B->src[g], sb);
         if (e != cudaSuccess) rc = status(e);
     }
 
@@ -190,6 +190,7 @@ int stencil_batch_create_ex(stencil_batch *out, const stencil_batch_grid *grids,
         G.pass_base = (int)desc.size();
         G.power = static_cast<const float *>(q.power);
         G.src = B->src[g];
+        G.ld_src = B->ld_scratch[g];
         G.amb = q.coeffs[4];
         G.rz = q.coeffs[3];
         G.sdc = q.coeffs[0];
@@ -205,7 +206,7 @@ int stencil_batch_create_ex(stencil_batch *out, const stencil_batch_grid *grids,
             a.out = p == P - 1 ? static_cast<float *>(q.grid_out) : B->scratch[2 * g + p % 2];
             a.ld_out = p == P - 1 ? q.nx : B->ld_scratch[g];
             a.pw = B->src[g];   // Hotspot: sdc*(p + amb*Rz), rebuilt at every replay
-            a.ld_pw = q.nx;
+            a.ld_pw = B->ld_scratch[g];
             a.nx = q.nx;
             a.ny = q.ny;
             a.tsteps = (p == P - 1) ? last : T;
@@ -217,7 +218,7 @@ int stencil_batch_create_ex(stencil_batch *out, const stencil_batch_grid *grids,
             if (q.kind == ST_THERMAL) hot_coeffs_src(q.coeffs, a.kf);   // source-map kernels
             a.vec_in = ((uintptr_t)a.in % 16 == 0) && (a.ld_in % 4 == 0);
             a.vec_out = ((uintptr_t)a.out % 16 == 0) && (a.ld_out % 4 == 0);
-            a.vec_pw = a.pw ? (((uintptr_t)a.pw % 16 == 0) && (q.nx % 4 == 0)) : 0;
+            a.vec_pw = a.pw ? (((uintptr_t)a.pw % 16 == 0) && (a.ld_pw % 4 == 0)) : 0;
             desc.push_back(a);
         }
         if (P == 0 && q.grid_in != q.grid_out) {
@@ -225,19 +226,21 @@ int stencil_batch_create_ex(stencil_batch *out, const stencil_batch_grid *grids,
             G.ld_copy = q.nx;
         }
     }
-    // Queue order.  Each grid's pass chain is placed on a common timeline of `maxp` slots so
-    // that the work per slot is level: the grids with the most work first, each at the start
-    // slot that keeps the heaviest slot it touches lightest (a grid of few passes fills in
-    // beside the long chains, which start at once: they set the launch's critical path).
-    // Items go in slot order (source-map rows first, copies last); within a slot by grid, row
-    // segment, tile column.  Every item depends only on items before it: its grid's previous
-    // pass sits in an earlier slot.
-    std::vector<int> start(count, 0);
-    {
+    // Two queues, one per kind.  Within a queue each grid's pass chain is placed on a timeline
+    // of `maxp` slots so that the work per slot is level: the grids with the most work first,
+    // each at the start slot that keeps the heaviest slot it touches lightest (a grid of few
+    // passes fills in beside the long chains, which start at once: they set the critical path).
+    // Items go in slot order (source-map tiles first, copies last); within a slot by grid, row
+    // segment, tile column.  Every item depends only on items before it in its queue: its
+    // grid's previous pass sits in an earlier slot.
+    std::vector<QItem> kitems[2];
+    double kwork[2] = {0.0, 0.0};
+    for (int kind = 0; kind < 2 && rc == ST_OK; kind++) {
+        std::vector<QItem> &its = kitems[kind];
+        std::vector<int> start(count, 0), order;
         std::vector<double> load(std::max(maxp, 1), 0.0);
-        std::vector<int> order;
         for (int g = 0; g < count; g++)
-            if (qg[g].P > 0) order.push_back(g);
+            if (qg[g].P > 0 && qg[g].kind == kind) order.push_back(g);
         std::sort(order.begin(), order.end(), [&](int a, int b) {
             const double wa = (double)qg[a].nx * qg[a].ny * qg[a].P;
             const double wb = (double)qg[b].nx * qg[b].ny * qg[b].P;
@@ -262,22 +265,29 @@ int stencil_batch_create_ex(stencil_batch *out, const stencil_batch_grid *grids,
             }
             start[g] = best_s;
             for (int k = best_s; k < best_s + P; k++) load[k] += wgt;
+            const stencil_batch_grid &q = B->grid[g];
+            kwork[kind] += (double)q.nx * q.ny * q.steps /
+                           std::max(batch_model_gcells(q.kind, q.nx, q.ny, q.steps, B->sms, T, V,
+                                                       bps, L), 1e-9);
         }
+        if (kind == ST_THERMAL)
+            for (int g : order)
+                for (int s = 0; s < qg[g].nseg; s++)
+                    for (int tx = 0; tx < qg[g].ntx; tx++) its.push_back(QItem{g, -1, tx, s});
+        for (int slot = 0; slot < maxp; slot++)
+            for (int g = 0; g < count; g++) {
+                if (qg[g].kind != kind) continue;
+                const int p = slot - start[g];
+                if (p < 0 || p >= qg[g].P) continue;
+                for (int s = 0; s < qg[g].nseg; s++)
+                    for (int tx = 0; tx < qg[g].ntx; tx++) its.push_back(QItem{g, p, tx, s});
+            }
+        for (int g = 0; g < count; g++)
+            if (qg[g].kind == kind && qg[g].copy_from)
+                for (int s = 0; s < qg[g].nseg; s++) its.push_back(QItem{g, qg[g].P, 0, s});
     }
-    for (int g = 0; g < count && rc == ST_OK; g++)
-        if (B->grid[g].kind == ST_THERMAL && qg[g].P > 0)
-            for (int s = 0; s < qg[g].nseg; s++)
-                for (int tx = 0; tx < qg[g].ntx; tx++) items.push_back(QItem{g, -1, tx, s});
-    for (int slot = 0; slot < maxp && rc == ST_OK; slot++)
-        for (int g = 0; g < count; g++) {
-            const int p = slot - start[g];
-            if (p < 0 || p >= qg[g].P) continue;
-            for (int s = 0; s < qg[g].nseg; s++)
-                for (int tx = 0; tx < qg[g].ntx; tx++) items.push_back(QItem{g, p, tx, s});
-        }
-    for (int g = 0; g < count && rc == ST_OK; g++)
-        if (qg[g].copy_from)
-            for (int s = 0; s < qg[g].nseg; s++) items.push_back(QItem{g, qg[g].P, 0, s});
+    items = kitems[0];
+    items.insert(items.end(), kitems[1].begin(), kitems[1].end());
     B->items = (long long)items.size();
 
     // device table: [items | grids | descriptors | control | counters (reset per replay)]
@@ -286,7 +296,7 @@ int stencil_batch_create_ex(stencil_batch *out, const stencil_batch_grid *grids,
     const size_t o_desc = o_grids + align256(qg.size() * sizeof(QGrid));
     const size_t o_ctl = o_desc + align256(std::max<size_t>(1, desc.size()) * sizeof(Pass2D));
     const size_t o_cnt = o_ctl + align256(sizeof(QueueCtl));
-    const size_t cnt_bytes = (size_t)(2 + ndone + nsrcf) * sizeof(int);   // head, status, counters
+    const size_t cnt_bytes = (size_t)(3 + ndone + nsrcf) * sizeof(int);   // heads, status, counters
     const size_t table = o_cnt + align256(cnt_bytes);
     if (rc == ST_OK) {
         e = cudaMalloc(&B->dev, table);
@@ -305,15 +315,20 @@ int stencil_batch_create_ex(stencil_batch *out, const stencil_batch_grid *grids,
         if (e != cudaSuccess) rc = status(e);
         B->ctl = reinterpret_cast<QueueCtl *>(d + o_ctl);
         int *cnt = reinterpret_cast<int *>(d + o_cnt);
-        qb.items = reinterpret_cast<const QItem *>(d + o_items);
-        qb.total = (int)items.size();
+        qb.items[0] = reinterpret_cast<const QItem *>(d + o_items);
+        qb.items[1] = qb.items[0] + kitems[0].size();
+        qb.total[0] = (int)kitems[0].size();
+        qb.total[1] = (int)kitems[1].size();
+        // SMs per kind in proportion to the kind's predicted time (each SM runs one kind's loop)
+        const double wsum = kwork[0] + kwork[1];
+        qb.split = wsum > 0 ? (int)std::lround(B->sms * kwork[0] / wsum) : 0;
         qb.L = L;
         qb.grids = reinterpret_cast<const QGrid *>(d + o_grids);
         qb.passes = reinterpret_cast<const Pass2D *>(d + o_desc);
         qb.head = reinterpret_cast<unsigned *>(cnt);
-        qb.status = cnt + 1;
-        qb.done = cnt + 2;
-        qb.srcf = cnt + 2 + ndone;
+        qb.status = cnt + 2;
+        qb.done = cnt + 3;
+        qb.srcf = cnt + 3 + ndone;
         qb.ctl = B->ctl;
         // as many one-warp blocks as are resident at once (no more: the rest would only pop
         // items once earlier blocks leave)
@@ -325,7 +340,7 @@ int stencil_batch_create_ex(stencil_batch *out, const stencil_batch_grid *grids,
         e = cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             cudaError_t le = cudaMemsetAsync(d + o_cnt, 0, cnt_bytes, B->stream);
-            if (le == cudaSuccess && qb.total > 0) {
+            if (le == cudaSuccess && !items.empty()) {
                 le = tb2q_launch(T, V, qb, B->stream);
                 B->launches = 1;
             }

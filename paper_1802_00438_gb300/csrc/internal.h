@@ -62,7 +62,8 @@ struct QGrid {
     int kind, ntx, nseg, P, nx, ny;
     int done_off, srcf_off, pass_base;
     const float *power;       // Hotspot: the power map (dense rows of nx)
-    float *src;               // Hotspot: the source map it builds
+    float *src;               // Hotspot: the source map it builds (rows ld_src apart)
+    long long ld_src;
     float amb, rz, sdc;
     const float *copy_from;   // k = P items
     long long ld_copy;
@@ -73,15 +74,20 @@ struct QueueCtl {
     int hold_pass;            // test hook, -1 = off: items of this pass never report finished
     int pad;
 };
+// Two queues, one per stencil kind (their items never depend on each other's): a block starts
+// on the queue of its SM (SMs below `split` take diffusion items, the others Hotspot items,
+// so each SM's instruction cache holds one kind's loop) and moves to the other queue once its
+// own is empty.
 struct QueueBatch2D {
-    const QItem *items;
-    int total;
+    const QItem *items[2];
+    int total[2];
+    int split;
     int L;                    // rows per item
     const QGrid *grids;
     const Pass2D *passes;     // grids[g].pass_base + k
     int *done;
     int *srcf;
-    unsigned *head;           // next item
+    unsigned *head;           // next item of each queue (two counters)
     int *status;              // 0, or 1 once a wait gave up (every block then leaves)
     const QueueCtl *ctl;
     int ctas;
@@ -106,9 +112,10 @@ cudaError_t lp_decode(int stor, const void *src, long long ld_q, const float2 *m
 // cc = 1 - 2cx - 2cy is exact, cz = sdc*Rz
 void hot_coeffs_src(const float *k, float *kf);
 
-// Hotspot source map dst = sdc*(p + amb*Rz) (dense rows of nx), read by the contracted kernels
-cudaError_t hot_source(const float *p, long long ld_p, float *dst, int nx, int ny, float amb,
-                       float rz, float sdc, cudaStream_t st);
+// Hotspot source map dst = sdc*(p + amb*Rz) (rows ld_d floats apart), read by the contracted
+// kernels
+cudaError_t hot_source(const float *p, long long ld_p, float *dst, long long ld_d, int nx, int ny,
+                       float amb, float rz, float sdc, cudaStream_t st);
 
 bool tb2d_available(const Shape2D &s);
 int tb2d_block_threads(const Shape2D &s);

@@ -88,15 +88,15 @@ __global__ void __launch_bounds__(256) k_lp_decode(const uint16_t *__restrict__ 
 // Hotspot source row: sdc*(p + amb*Rz), each operation rounded once; one block row per grid
 // row, four cells per thread (16-byte accesses when rows are aligned)
 __global__ void __launch_bounds__(256) k_hot_source(const float *__restrict__ p, long long ld_p,
-                                                    float *__restrict__ dst, int nx, float amb,
-                                                    float rz, float sdc, int vec)
+                                                    float *__restrict__ dst, long long ld_d, int nx,
+                                                    float amb, float rz, float sdc, int vec)
 {
     const int y = blockIdx.y;
     const int x = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (x >= nx) return;
     const float a = __fmul_rn(amb, rz);
     const float *src = p + (long long)y * ld_p + x;
-    float *d = dst + (long long)y * nx + x;
+    float *d = dst + (long long)y * ld_d + x;
     if (vec) {
         const float4 v = *reinterpret_cast<const float4 *>(src);
         *reinterpret_cast<float4 *>(d) =
@@ -141,18 +141,18 @@ void hot_coeffs_src(const float *k, float *kf)
     kf[6] = 0.f;
 }
 
-cudaError_t hot_source(const float *p, long long ld_p, float *dst, int nx, int ny, float amb,
-                       float rz, float sdc, cudaStream_t st)
+cudaError_t hot_source(const float *p, long long ld_p, float *dst, long long ld_d, int nx, int ny,
+                       float amb, float rz, float sdc, cudaStream_t st)
 {
     if (nx < 1 || ny < 1) return cudaErrorInvalidValue;
     const int vec = ((uintptr_t)p % 16 == 0) && ((uintptr_t)dst % 16 == 0) && (nx % 4 == 0) &&
-                    (ld_p % 4 == 0);
+                    (ld_p % 4 == 0) && (ld_d % 4 == 0);
     const unsigned bx = (unsigned)((nx + 1023) / 1024);
     // grid rows beyond the 65535 limit of gridDim.y go in slices
     for (long long y0 = 0; y0 < ny; y0 += 65535) {
         const unsigned rows = (unsigned)std::min<long long>(65535, ny - y0);
-        k_hot_source<<<dim3(bx, rows), 256, 0, st>>>(p + y0 * ld_p, ld_p, dst + y0 * nx, nx, amb,
-                                                     rz, sdc, vec);
+        k_hot_source<<<dim3(bx, rows), 256, 0, st>>>(p + y0 * ld_p, ld_p, dst + y0 * ld_d, ld_d, nx,
+                                                     amb, rz, sdc, vec);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

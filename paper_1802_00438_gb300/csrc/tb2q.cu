@@ -4,14 +4,15 @@
 // >= rad*T, T fused steps, redundant halo compute, only the compute block stored, the last pass
 // fusing the remainder) is split into items of one tile column x L rows.  The items of every
 // grid of a batch, all passes, sit in one queue in pass-major order (Eq. 8 gives each grid its
-// own ceil(steps/T) passes); the blocks of ONE launch pop items one after another.  A pass of a
+// own ceil(steps/T) passes); the blocks of ONE launch pop items one after another (one queue per
+// stencil kind, each SM starting on one of them: see QueueBatch2D).  A pass of a
 // grid depends on the previous pass of the same grid only where the tiles overlap, so an item
 // waits, before it reads anything, for the neighbouring tiles' previous pass (tx +- 1, seg +- 1:
 // the halo it reads and the cells it overwrites in the ping-pong buffer).
 //
 // Why no item can wait forever: items are popped in queue order and depend only on items
-// earlier in the queue, so the earliest unfinished item always has its dependencies finished and
-// is held by a running block.  Every wait is bounded all the same (a lost update would otherwise
+// earlier in the same queue, so the earliest unfinished item of each queue always has its
+// dependencies finished and is held by a running block.  Every wait is bounded all the same (a lost update would otherwise
 // hang the GPU): after QueueCtl::wait_ns a block sets the batch's status word and leaves, and
 // every other block leaves at its next poll or pop.  Waits happen before an item issues any
 // copy, so no block leaves with copies in flight.
@@ -89,12 +90,20 @@ __global__ void __launch_bounds__(32) k_tb2f_queue(const QueueBatch2D q)
 #pragma unroll
         for (int j = 0; j < V; j++) A[s][j] = B[s][j] = 0.f;
     const int lane = threadIdx.x;
-    for (;;) {
+    unsigned smid;
+    asm volatile("mov.u32 %0, %%smid;\n" : "=r"(smid));
+    int qs = (int)smid < q.split ? 0 : 1;   // this SM's queue first, then the other one
+    for (int tries = 0; tries < 2;) {
         int it = 0;
-        if (lane == 0) it = ld_relaxed(q.status) ? q.total : (int)atomicAdd(q.head, 1u);
+        if (lane == 0) it = ld_relaxed(q.status) ? q.total[qs] : (int)atomicAdd(q.head + qs, 1u);
         it = __shfl_sync(0xffffffffu, it, 0);
-        if (it >= q.total) break;
-        const QItem w = q.items[it];
+        if (it >= q.total[qs]) {
+            if (ld_relaxed(q.status)) break;
+            qs ^= 1;
+            tries++;
+            continue;
+        }
+        const QItem w = q.items[qs][it];
         // read from global memory where used: little stays live across the pass
         const QGrid &G = q.grids[w.g];
         bool ok = true;
@@ -119,11 +128,11 @@ __global__ void __launch_bounds__(32) k_tb2f_queue(const QueueBatch2D q)
             constexpr int CXQ = 32 * V - 2 * ((T + 3) / 4 * 4);
             const int x0 = w.tx * CXQ, x1 = min(G.nx, x0 + CXQ);
             const int nq = (x1 - x0 + 3) / 4;               // 4-cell chunks per row
-            const bool vec = (G.nx % 4 == 0);
+            const bool vec = (G.nx % 4 == 0);   // the source rows are padded: aligned always
             for (int c = lane; c < nq * (r1 - r0); c += 32) {
                 const int y = r0 + c / nq, x = x0 + 4 * (c % nq);
                 const float *pr = G.power + (long long)y * G.nx + x;
-                float *d = G.src + (long long)y * G.nx + x;
+                float *d = G.src + (long long)y * G.ld_src + x;
                 if (vec) {
                     const float4 v = *reinterpret_cast<const float4 *>(pr);
                     *reinterpret_cast<float4 *>(d) =
