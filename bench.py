@@ -330,7 +330,10 @@ class Gpu:
         torch.cuda.set_device(self.local)
         self.dev = torch.device("cuda", self.local)
         self.rk = Replicas("nccl", self.dev)
-        self.stream = torch.cuda.current_stream(self.dev)
+        # a stream of our own, current for the whole run (a CUDA graph cannot be captured on
+        # the legacy default stream)
+        self.stream = torch.cuda.Stream(self.dev)
+        torch.cuda.set_stream(self.stream)
         import paper_1802_00438_gb300 as st
         self.st = st
         self.sms = torch.cuda.get_device_properties(self.dev).multi_processor_count
@@ -385,16 +388,32 @@ def plan_record(g: Gpu, w, args, steps: int, warmup: int, with_cpu: bool, one_th
     def step():
         plan.run(u0, out, coef, w.steps, power=pw)
 
-    for _ in range(warmup):
+    # A run of a small grid is a few microseconds of kernels per pass: launched one by one it
+    # would measure the host's launch rate, so it is captured once in a CUDA graph (the plan
+    # launches on the stream being captured) and the timed steps replay the graph.
+    graph = None
+    if w.cells * w.steps < 2e9:
+        graph = torch.cuda.CUDAGraph()
         step()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=stream):
+            step()
+        torch.cuda.synchronize()
+    timed_step = graph.replay if graph is not None else step
+    for _ in range(warmup):
+        timed_step()
+    ms, per, clocks = g.timed(timed_step, steps, 0)
+    # kernel time per launch for the roofline: the same runs again with the library's event
+    # pair around every launch (outside the timed region)
     st.stencil_plan_set_timing(plan.h, True)
     st.stencil_plan_kernel_time(plan.h, reset=True)
-    ms, per, clocks = g.timed(step, steps, 0)
+    for _ in range(steps):
+        step()
     kern_ms, timed_launches = st.stencil_plan_kernel_time(plan.h, reset=True)
     st.stencil_plan_set_timing(plan.h, False)
     launches = timed_launches
     if w.kind == 1 and w.ndim == 2 and not args.storage and not w.var:
-        launches += steps   # the source-map kernel (p + amb*Rz) before each run's passes
+        launches += steps   # the source-map kernel (sdc*(p + amb*Rz)) before each run's passes
     cells_step = w.cells * w.steps
     value = rk.job_rate(cells_step * steps, ms) / 1e9
 
@@ -463,6 +482,7 @@ def plan_record(g: Gpu, w, args, steps: int, warmup: int, with_cpu: bool, one_th
            "gflops": value * fl, "effective_gbs": value * by,
            "config": workload_config(w),
            "plan": {"T": T, "tile": [info["bx"], info["by"]], "vec": info["vec"],
+                    "cuda_graph": graph is not None,
                     "warps": info["warps"], "ctas": info["ctas"],
                     "passes_per_step": -(-w.steps // T),
                     # the library's calibrated restatement of Eqs. 3-9 for this plan, and
@@ -685,6 +705,62 @@ def adjoint_record(g: Gpu, args, steps: int, warmup: int, with_cpu: bool, ckpt=2
     return rec
 
 
+# configurations of the model-accuracy study: 2D (T, cells per lane, variant 1 = partial rows
+# in place) and 3D (T, tile width, tile height, cells per thread), every one the library compiles
+STUDY_2D = [(1, 8, 0), (2, 8, 0), (4, 8, 0), (6, 8, 0), (8, 8, 0), (8, 8, 1),
+            (1, 4, 0), (2, 4, 0), (4, 4, 0), (8, 4, 0), (12, 4, 0), (12, 4, 1)]
+STUDY_3D = [(1, 64, 64, 8), (2, 64, 64, 8), (3, 64, 64, 8), (4, 64, 64, 8),
+            (2, 64, 64, 4), (3, 64, 64, 4), (4, 64, 64, 4),
+            (2, 128, 32, 8), (3, 128, 32, 8), (4, 128, 32, 8),
+            (2, 64, 32, 8), (3, 64, 32, 8), (4, 64, 32, 8)]
+
+
+def model_study(g: Gpu, args):
+    """Measured / predicted rate of every compiled contracted configuration on the four grid
+    configurations (the paper's Sec. 6.2 model-accuracy figure, per point): each plan timed on
+    its full step count (CUDA events, best of 3 after one warm-up) beside the calibrated
+    model's prediction for it."""
+    torch, st = g.torch, g.st
+    rows = []
+    for name in ("diffusion2d_1024", "thermal2d_16384", "diffusion3d_512", "thermal3d_512x512x256"):
+        w = WORKLOADS[name]()
+        u0 = torch.from_numpy(w.u0).to(g.dev)
+        pw = None if w.power is None else torch.from_numpy(w.power).to(g.dev)
+        out = torch.empty_like(u0)
+        confs = STUDY_2D if w.ndim == 2 else STUDY_3D
+        for cf in confs:
+            if w.ndim == 2:
+                T, vec, inplace = cf
+                kw = dict(force_T=T, force_vec=vec, force_by=1 if inplace else 0)
+            else:
+                T, bx, by, vec = cf
+                kw = dict(force_T=T, force_bx=bx, force_by=by, force_vec=vec)
+            try:
+                plan = st.Plan(w.kind, w.ndim, w.nx, w.ny, w.nz, stream=g.stream.cuda_stream, **kw)
+            except st.StencilError:
+                continue
+            info = plan.info()
+            plan.run(u0, out, w.coef, w.steps, power=pw)
+            best = 1e30
+            for _ in range(3):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(g.stream)
+                plan.run(u0, out, w.coef, w.steps, power=pw)
+                e1.record(g.stream)
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            meas = w.cells * w.steps / (best * 1e-3) / 1e9
+            model = info["model_gcells"] or None
+            rows.append({"workload": name, "config": list(cf), "measured_gcells": meas,
+                         "model_gcells": model, "accuracy": meas / model if model else None,
+                         "warps": info["warps"], "ctas": info["ctas"]})
+            plan.close()
+        del u0, pw, out
+        torch.cuda.empty_cache()
+    return rows
+
+
 def headline_line(args, world, rec, extra=None):
     """The contract's top-level keys from a measurement record."""
     line = {"metric": METRIC, "value": rec["value"], "unit": rec["unit"], "n_gpus": world,
@@ -723,6 +799,9 @@ def main():
     ap.add_argument("--ny", type=int, default=0)
     ap.add_argument("--nz", type=int, default=0)
     ap.add_argument("--time-steps", type=int, default=0, help="profiling: override time steps")
+    ap.add_argument("--model-study", action="store_true",
+                    help="measured / predicted rate of every compiled configuration (one JSON "
+                         "line), the model-accuracy study")
     ap.add_argument("--tune", type=int, default=0,
                     help="before timing, run the model's top-K configurations on the workload and "
                          "use the fastest (stencil_tune); 0 = the model's own choice")
@@ -762,6 +841,11 @@ def main():
     g = Gpu()
     rk = g.rk
     with_cpu = not args.no_cpu
+    if args.model_study:
+        rows = model_study(g, args)
+        if rk.rank == 0:
+            print(json.dumps({"model_study": rows}), flush=True)
+        return
     if name == BATCH:
         rec = batch_record(g, args, args.steps, args.warmup, with_cpu)
         if rk.rank == 0:

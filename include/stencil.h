@@ -81,7 +81,9 @@ typedef struct {
     int nx, ny, nz;  /* grid size in cells, each >= 1; nz is ignored (taken as 1) for 2D */
     int storage;     /* grid storage between passes: ST_F32, or ST_BF16 / ST_F16 (2D contracted
                         plans of ST_DIFFUSION / ST_THERMAL, rad <= 1: 16-bit codes with a
-                        float32 offset and scale per block; arithmetic stays float32) */
+                        float32 offset and scale per block; arithmetic stays float32.  Passes
+                        store each cell as its difference from its block's first cell
+                        (scale 1); fp16 differences saturate at +-65504) */
     int force_T;     /* fused steps per pass (par_time, Sec. 3.2); 0 = the plan chooses */
     int force_bx;    /* tile width in cells incl. halos (bsize_x, Sec. 3.1); 0 = choose */
     int force_by;    /* 3D: tile height in cells incl. halos (bsize_y); 0 = choose.  2D

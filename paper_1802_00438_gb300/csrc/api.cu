@@ -133,7 +133,7 @@ double model_gcells_2d(const stencil_desc &d, int sms, const Cand2D &k, int bps,
                        int seg_rows = 0)
 {
     const bool swap = k.W == 1;
-    const double fp = d.kind == ST_DIFFUSION ? 5.0 : 9.0;
+    const double fp = d.kind == ST_DIFFUSION ? 5.0 : 6.0;   // Hotspot: the expanded weights
     const double ops = fp + 4.0 / k.V + 100.0 / (k.T * k.V);
     const double code_kb = (swap ? 2.0 : 1.0) * k.T * (k.V * fp + 6.0) * 16.0 / 1024.0;
     // the launch geometry of prepare2: one-warp blocks over (tile column, row) units in
@@ -171,11 +171,15 @@ double model_gcells_2d(const stencil_desc &d, int sms, const Cand2D &k, int bps,
     return r.gcells;
 }
 
-// 3D partial-sum kernel: the same restatement, calibrated from ncu counts of the 512^3 and
-// 512^2 x 256 runs at T = 3 (2 x 4 cells per thread, 16 warps): 17.3 (Diffusion) and 19.7
-// (Hotspot) issued thread instructions per computed cell update including halos, 61 % issue
-// efficiency with one 16-warp block per SM, DRAM traffic 1.9x the algorithmic bytes (halo
-// re-reads by blocks at other z positions, so hbm_eff = 0.9 / 1.9).
+// 3D partial-sum kernel: the same restatement.  Issued work: 17.3 (Diffusion) and 19.7
+// (Hotspot) thread instructions per computed cell update including halos (ncu counts of the
+// 512^3 and 512^2 x 256 runs with 2 x 4 cells per thread at T = 4), x(0.85 + 0.6/T) for the
+// costlier first stage.  Issue efficiency 0.61 for one
+// 16-warp block per SM, x1.10 for two 8-warp blocks (they wait at fewer barriers together),
+// x0.80 for 32-warp blocks of 2 x 2 cells (twice the y exchange per cell).  Device memory: the
+// tiles read their halos again (the tile fit's read factor, ntx*bx*nty*by / (nx*ny)), at 62 %
+// of the measured copy bandwidth.  Calibrated on the 50-point sweep of bench.py --model-study
+// (measured / predicted per configuration).
 double model_gcells_3d(const stencil_desc &d, int sms, int T, int VX, int VY, int NW)
 {
     stencil_gpu_model_in m = {};
@@ -192,10 +196,16 @@ double model_gcells_3d(const stencil_desc &d, int sms, int T, int VX, int VY, in
     m.sms = sms;
     m.sm_hz = 2.07e9;
     m.hbm_gbs = 6800.0;
-    m.bytes_per_cell = d.kind == ST_DIFFUSION ? 8.0 : 12.0;
-    m.ops_per_cell = d.kind == ST_DIFFUSION ? 17.3 : 19.7;
-    m.issue_eff = 0.61;
-    m.hbm_eff = 0.9 / 1.9;
+    const double cx = m.bx - 2.0 * m.halo_x, cy = m.by - 2.0 * m.halo_y;
+    if (cx < 1 || cy < 1) return 0.0;
+    const double rf = std::ceil(d.nx / cx) * m.bx * std::ceil(d.ny / cy) * m.by / ((double)d.nx * d.ny);
+    const double alg = d.kind == ST_DIFFUSION ? 8.0 : 12.0;
+    const double read = alg - 4.0;   // field (and power) in; the field out is written once
+    m.bytes_per_cell = alg;
+    m.hbm_eff = 0.62 * alg / (read * rf + 4.0);
+    // stage 0 (three ring planes, their exchange) costs more than the partial-sum stages
+    m.ops_per_cell = (d.kind == ST_DIFFUSION ? 17.3 : 19.7) * (0.85 + 0.6 / T);
+    m.issue_eff = 0.61 * (NW <= 8 ? 1.10 : NW >= 32 ? 0.80 : 1.0);
     m.stream_overhead = 0.04;
     m.launch_s = 4e-6;
     stencil_gpu_model_out r;
@@ -807,13 +817,30 @@ static int plan_create(stencil_plan *out, const stencil_desc *desc)
         // tile width 64 (2 cells per lane) or 128 (4 cells per lane), tile height, cells per
         // thread; 64 x 64 with 16 cells per thread is the three-plane-window kernel (exact or
         // contracted), every other shape the partial-sum kernel (contracted)
-        // nothing forced, contracted: 64 x 32 tiles in 8-warp blocks, two per SM (measured on
-        // GB300 against 64 x 64 tiles in 16-warp blocks: 512^3 diffusion 950 vs 918 GCell/s,
-        // 512^2 x 256 Hotspot 784 vs 776)
         const bool free_tile = !d.exact && !d.force_bx && !d.force_by && !d.force_vec;
-        const int bx = d.force_bx ? d.force_bx : 64;
-        const int by = d.force_by ? d.force_by : (bx == 128 || free_tile ? 32 : 64);
-        const int cells = d.force_vec ? d.force_vec : (d.exact ? 16 : 8);
+        int bx = d.force_bx ? d.force_bx : 64;
+        int by = d.force_by ? d.force_by : (bx == 128 || free_tile ? 32 : 64);
+        int cells = d.force_vec ? d.force_vec : (d.exact ? 16 : 8);
+        int model_T = 0;
+        if (free_tile && !d.force_T && d.rad <= 1) {
+            // nothing forced, contracted: the compiled partial-sum (tile, T) the calibrated
+            // model rates best
+            const int shapes[][3] = {{64, 64, 8}, {64, 64, 4}, {128, 32, 8}, {64, 32, 8}};
+            double best = -1.0;
+            for (const auto &sh : shapes)
+                for (int t = 1; t <= 4; t++) {
+                    const int vx = sh[0] / 32, vy = sh[2] / vx, nw = sh[1] / vy;
+                    if (!tb3d_available(Shape3D{d.kind, 0, t, vy, nw, 1, vx})) continue;
+                    const double g = model_gcells_3d(d, p->sms, t, vx, vy, nw);
+                    if (g > best) {
+                        best = g;
+                        bx = sh[0];
+                        by = sh[1];
+                        cells = sh[2];
+                        model_T = t;
+                    }
+                }
+        }
         if (bx != 64 && bx != 128) rc = ST_ERR_UNSUPPORTED;
         p->VX3 = bx / 32;
         if (rc == ST_OK && (cells % p->VX3 != 0 || by % (cells / p->VX3) != 0))
@@ -824,9 +851,7 @@ static int plan_create(stencil_plan *out, const stencil_desc *desc)
             p->alg3 = (p->VX3 == 2 && p->VY == 8 && p->NW == 8) ? 0 : 1;
             if (p->alg3 && d.exact) rc = ST_ERR_UNSUPPORTED;
         }
-        // contracted default: T = 4 for diffusion, 3 for Hotspot (best measured with the
-        // default tiles: 512^3 diffusion T = 2, 3, 4: 838, 912, 950; Hotspot 540, 784, 764)
-        const int want = d.force_T ? d.force_T : (p->alg3 ? (d.kind == ST_DIFFUSION ? 4 : 3) : 4);
+        const int want = d.force_T ? d.force_T : (model_T ? model_T : 4);
         p->T = kernel_T_for(p, want);
         if (p->T == 0 || (d.force_T && p->T != d.force_T)) rc = ST_ERR_UNSUPPORTED;
         PassCfg3D *c = nullptr;

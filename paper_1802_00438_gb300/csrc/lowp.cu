@@ -3,11 +3,14 @@
 //
 // A block is the segment of one row that one tile column computes: cells
 // [b*cx, min((b+1)*cx, nx)) of row y, with cx the compute width of the plan's tiling, so the
-// kernel that writes a block is the only writer of its code.  Each block stores
-// (offset, scale) = (mid-range, half-range) of its cells and every cell as q = (x - offset) /
-// scale in [-1, 1] rounded to bf16 / fp16; x = offset + scale * q on load.  Precision is
-// relative to the block's spread rather than to the values' magnitude, which matters for
-// fields like temperatures (~330 K) whose bf16 ulp alone would be 2 K.
+// kernel that writes a block is the only writer of its code.  Each block stores a float32
+// (offset, scale) and every cell as q = (x - offset) / scale rounded to bf16 / fp16;
+// x = offset + scale * q on load.  The encoder here (before the first pass) takes the block's
+// mid-range and half-range, q in [-1, 1]; the passes take the block's first cell and scale 1,
+// which needs no block-wide minimum and maximum (bf16 and fp16 are floating point, so q keeps
+// its 8 or 11 significant bits at any size).  Either way the precision is relative to the
+// block's spread rather than to the values' magnitude, which matters for fields like
+// temperatures (~330 K) whose bf16 ulp alone would be 2 K.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>

@@ -158,26 +158,19 @@ __device__ __forceinline__ float q2f(unsigned q)
     return __half2float(__ushort_as_half((unsigned short)q));
 }
 
+// two codes packed in one word (first argument in the low half), each rounded to nearest even
 template <int STOR>
-__device__ __forceinline__ unsigned f2q(float x)
+__device__ __forceinline__ unsigned f2q2(float a, float b)
 {
-    if (stor_fmt(STOR) == STOR_BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(x));
-    return __half_as_ushort(__float2half_rn(x));
-}
-
-// warp-wide float min / max in one instruction (sm_100 family)
-__device__ __forceinline__ float warp_min(float v)
-{
-    float r;
-    asm volatile("redux.sync.min.f32 %0, %1, 0xffffffff;\n" : "=f"(r) : "f"(v));
-    return r;
-}
-
-__device__ __forceinline__ float warp_max(float v)
-{
-    float r;
-    asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;\n" : "=f"(r) : "f"(v));
-    return r;
+    if (stor_fmt(STOR) == STOR_BF16) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<const unsigned *>(&h);
+    }
+    // fp16 stops at 65504: a block whose cells lie further than that from its offset
+    // saturates instead of storing an infinity
+    const __half2 h = __floats2half2_rn(fminf(fmaxf(a, -65504.f), 65504.f),
+                                        fminf(fmaxf(b, -65504.f), 65504.f));
+    return *reinterpret_cast<const unsigned *>(&h);
 }
 
 struct CtxF {
@@ -432,37 +425,27 @@ __device__ __forceinline__ void tbf_iter(const CtxF &c, const CoefF &k,
                     if (j >= c.st_lo && j < c.st_hi) gO[j] = out[j];
             }
         } else {
-            // encode the row segment of this tile: offset = mid-range, scale = half-range of the
-            // stored cells, q = (x - offset) / scale in [-1, 1] rounded to the 16-bit format
-            float lo = __int_as_float(0x7f800000), hi = -lo;
+            // encode the row segment of this tile as q = x - offset with the offset the value of
+            // the block's first cell (tile column tx*CX: lane H/V, its cell 0, in the grid for
+            // every tile) and scale 1.  bf16 and fp16 are floating-point formats, so q keeps 8
+            // (11) significant bits of each cell's distance from the offset at any magnitude:
+            // the error per cell is at most half an ulp of |x - offset| <= the block's spread,
+            // and no block-wide minimum and maximum are needed
+            const float mid = __shfl_sync(0xffffffffu, out[0], C::H / V);
+            unsigned q2[V / 2];   // pairs of codes, cell 2i in the low half
 #pragma unroll
-            for (int j = 0; j < V; j++)
-                if (j >= c.st_lo && j < c.st_hi) {
-                    lo = fminf(lo, out[j]);
-                    hi = fmaxf(hi, out[j]);
-                }
-            lo = warp_min(lo);
-            hi = warp_max(hi);
-            const float mid = 0.5f * (lo + hi);
-            float sc = 0.5f * (hi - lo);
-            sc = (sc > 0.f) ? sc : 1.f;
-            const float inv = __frcp_rn(sc);
-            // |x - mid| * inv <= 1 + 3 * 2^-24 for the block's own cells, which rounds to 1 in
-            // either 16-bit format: no clamp needed
-            unsigned q[V];
-#pragma unroll
-            for (int j = 0; j < V; j++) q[j] = f2q<STOR>((out[j] - mid) * inv);
+            for (int j = 0; j < V / 2; j++) q2[j] = f2q2<STOR>(out[2 * j] - mid, out[2 * j + 1] - mid);
             if (c.st_full) {
 #pragma unroll
                 for (int t = 0; t < V / 4; t++)
-                    *reinterpret_cast<uint2 *>(r.qO + 4 * t) =
-                        make_uint2(q[4 * t] | (q[4 * t + 1] << 16), q[4 * t + 2] | (q[4 * t + 3] << 16));
+                    *reinterpret_cast<uint2 *>(r.qO + 4 * t) = make_uint2(q2[2 * t], q2[2 * t + 1]);
             } else if (c.st_any) {
 #pragma unroll
                 for (int j = 0; j < V; j++)
-                    if (j >= c.st_lo && j < c.st_hi) r.qO[j] = (uint16_t)q[j];
+                    if (j >= c.st_lo && j < c.st_hi)
+                        r.qO[j] = (uint16_t)((j & 1) ? (q2[j / 2] >> 16) : (q2[j / 2] & 0xffffu));
             }
-            if (c.lane == 0) r.mO[c.tx] = make_float2(mid, sc);
+            if (c.lane == 0) r.mO[c.tx] = make_float2(mid, 1.0f);
         }
     }
 }

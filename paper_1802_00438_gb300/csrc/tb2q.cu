@@ -79,9 +79,7 @@ template <int T, int V>
 __global__ void __launch_bounds__(32) k_tb2f_queue(const QueueBatch2D q)
 {
     using CD = TB2F<KDIFF, T, V, STOR_F32>;
-    // partial rows alternate between A and B (two-row unroll) for both kinds: with the queue's
-    // state kept in memory this fits the register file at T = 8, V = 8 (255 registers, a 4-byte
-    // spill), the in-place variant did not (92 bytes of spills)
+    // partial rows alternate between A and B (two-row unroll)
     constexpr bool SW = true;
     extern __shared__ __align__(16) float smem[];
     float A[CD::NS][V], B[CD::NS][V];
@@ -184,7 +182,7 @@ constexpr size_t q_smem()
 #define STN_TB2Q_ENTRY(T_, V_) \
     { T_, V_, reinterpret_cast<const void *>(&k_tb2f_queue<T_, V_>), q_smem<T_, V_>() }
 
-const QEntry kQueue[] = {STN_TB2Q_ENTRY(8, 8), STN_TB2Q_ENTRY(8, 4)};
+const QEntry kQueue[] = {STN_TB2Q_ENTRY(8, 4)};
 
 const QEntry *qfind(int T, int V)
 {

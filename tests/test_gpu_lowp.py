@@ -55,12 +55,14 @@ def test_lowp_configs(eng, orc, storage, bound):
 def test_lowp_edges(eng, orc, storage, kind, shape):
     # ragged sizes, one-row and one-column grids, step counts not divisible by T; the default
     # shape (T = 8, 8 cells per lane, partial rows in place) and the two-row variants
-    # Bound: the input and every pass's output are stored as q = (x - mid) / half in [-1, 1]
-    # rounded to 16 bits, an error of at most u * half per cell (u = 2^-9 bf16, 2^-12 fp16: half
-    # an ulp of |q| < 1); the update is a convex combination (plus a source), so the P + 1
-    # roundings of P passes add up to at most (P + 1) u half, half <= half the field's range
-    # (the range never grows).  Relative L2: divided by the rms of the result; never looser
-    # than the configs' 1e-2.
+    # Bound: the input is coded as (x - mid) / half with mid and half the block's mid-range and
+    # half-range, every pass's output as x - offset with the offset one cell of the block; each
+    # is rounded to 16 bits, an error of at most u times the coded magnitude (u = 2^-9 bf16,
+    # 2^-12 fp16: half an ulp), so at most u * range per cell, range the field's range; the
+    # update is a convex combination (plus a source), so the P + 1 roundings of P passes add up
+    # to at most (P + 1) u range, range the larger of the input's and the result's (diffusion
+    # never widens it, the Hotspot source can).  Relative L2 <= max error / rms of the result;
+    # the test takes the tighter of that bound (x 1.5) and the configs' 1e-2.
     T, vec, by = shape
     u = 2.0 ** -9 if storage == 1 else 2.0 ** -12
     for t, (nx, ny, steps) in enumerate([(301, 77, 17), (1, 40, 9), (57, 1, 12), (250, 250, 8),
@@ -70,9 +72,9 @@ def test_lowp_edges(eng, orc, storage, kind, shape):
         g = run(eng, w, steps, storage, T, vec, by)
         l2, _ = errs(g, ref)
         passes = -(-steps // (T or 8))
-        half = 0.5 * float(w.u0.max() - w.u0.min())
+        rng = max(float(w.u0.max() - w.u0.min()), float(ref.max() - ref.min()))
         rms = float(np.sqrt(np.mean(ref ** 2)))
-        bound = max(1e-2, (passes + 1) * u * half / rms)
+        bound = min(1e-2, 1.5 * (passes + 1) * u * rng / rms)
         assert l2 <= bound, (nx, ny, steps, storage, l2, bound)
     # zero steps copies the input exactly
     w = synth.make(kind, 2, 33, 21, seed=6100 + kind)
