@@ -380,10 +380,15 @@ def plan_record(g: Gpu, w, args, steps: int, warmup: int, with_cpu: bool, one_th
                                 top_k=args.tune, storage=args.storage, stream=stream.cuda_stream,
                                 rad=w.rad if w.rad > 1 else 0)
     plan = st.Plan(kind, w.ndim, w.nx, w.ny, w.nz, force_T=args.T, force_bx=args.bx,
-                   force_vec=args.vec, force_by=args.by, storage=args.storage,
+                   force_vec=args.vec, force_by=args.by, partial_rows=args.rows,
+                   resident=args.resident, storage=args.storage,
                    stream=stream.cuda_stream, rad=w.rad if w.rad > 1 else 0)
     info = plan.info()
     T = info["T"]
+    # resident tiles read and write the grid once per run: every step of it is fused per pass
+    # over device memory (T is then the steps between halo exchanges through L2)
+    resident = bool(info.get("resident"))
+    T_hbm = w.steps if resident else T
 
     def step():
         plan.run(u0, out, coef, w.steps, power=pw)
@@ -393,12 +398,18 @@ def plan_record(g: Gpu, w, args, steps: int, warmup: int, with_cpu: bool, one_th
     # launches on the stream being captured) and the timed steps replay the graph.
     graph = None
     if w.cells * w.steps < 2e9:
-        graph = torch.cuda.CUDAGraph()
         step()
         torch.cuda.synchronize()
-        with torch.cuda.graph(graph, stream=stream):
-            step()
-        torch.cuda.synchronize()
+        try:
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=stream):
+                step()
+            torch.cuda.synchronize()
+        except RuntimeError as e:   # a launch the capture does not support: run eagerly
+            print(f"bench: CUDA graph capture failed ({e}); timing eager launches",
+                  file=sys.stderr)
+            graph = None
+            torch.cuda.synchronize()
     timed_step = graph.replay if graph is not None else step
     for _ in range(warmup):
         timed_step()
@@ -412,7 +423,7 @@ def plan_record(g: Gpu, w, args, steps: int, warmup: int, with_cpu: bool, one_th
     kern_ms, timed_launches = st.stencil_plan_kernel_time(plan.h, reset=True)
     st.stencil_plan_set_timing(plan.h, False)
     launches = timed_launches
-    if w.kind == 1 and w.ndim == 2 and not args.storage and not w.var:
+    if w.kind == 1 and w.ndim == 2 and not args.storage and not w.var and not resident:
         launches += steps   # the source-map kernel (sdc*(p + amb*Rz)) before each run's passes
     cells_step = w.cells * w.steps
     value = rk.job_rate(cells_step * steps, ms) / 1e9
@@ -454,8 +465,8 @@ def plan_record(g: Gpu, w, args, steps: int, warmup: int, with_cpu: bool, one_th
     bytes_per_launch = w.cells * by
     tflops = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12
     gbs = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
-    cell_roof = min(alu_peak * 1e12 / fl, hbm_peak * 1e9 * T / by)      # cells/s at this T
-    alu_bound = alu_peak * 1e12 / fl <= hbm_peak * 1e9 * T / by
+    cell_roof = min(alu_peak * 1e12 / fl, hbm_peak * 1e9 * T_hbm / by)   # cells/s at this T
+    alu_bound = alu_peak * 1e12 / fl <= hbm_peak * 1e9 * T_hbm / by
     resized = bool(args.nx or args.ny or args.nz or args.time_steps)
     traffic = None if (resized or args.T or args.bx or args.vec or args.by) else \
         profiled_traffic(key, w.ndim)
@@ -482,9 +493,10 @@ def plan_record(g: Gpu, w, args, steps: int, warmup: int, with_cpu: bool, one_th
            "gflops": value * fl, "effective_gbs": value * by,
            "config": workload_config(w),
            "plan": {"T": T, "tile": [info["bx"], info["by"]], "vec": info["vec"],
-                    "cuda_graph": graph is not None,
+                    "cuda_graph": graph is not None, "resident": resident,
                     "warps": info["warps"], "ctas": info["ctas"],
-                    "passes_per_step": -(-w.steps // T),
+                    "passes_per_step": 1 if resident else -(-w.steps // T),
+                    "exchanges_per_step": (-(-w.steps // T) - 1) if resident else None,
                     # the library's calibrated restatement of Eqs. 3-9 for this plan, and
                     # measured / predicted (the paper's model-accuracy figure)
                     "model_gcells": info["model_gcells"] or None,
@@ -731,7 +743,7 @@ def model_study(g: Gpu, args):
         for cf in confs:
             if w.ndim == 2:
                 T, vec, inplace = cf
-                kw = dict(force_T=T, force_vec=vec, force_by=1 if inplace else 0)
+                kw = dict(force_T=T, force_vec=vec, partial_rows=1 if inplace else 2)
             else:
                 T, bx, by, vec = cf
                 kw = dict(force_T=T, force_bx=bx, force_by=by, force_vec=vec)
@@ -789,7 +801,11 @@ def main():
     ap.add_argument("--T", type=int, default=0, help="force the fused step count")
     ap.add_argument("--bx", type=int, default=0, help="force the 2D tile width")
     ap.add_argument("--vec", type=int, default=0, help="force cells per thread along x")
-    ap.add_argument("--by", type=int, default=0, help="force the 3D tile height (2D: kernel variant)")
+    ap.add_argument("--by", type=int, default=0, help="force the 3D tile height")
+    ap.add_argument("--rows", type=int, default=0,
+                    help="2D streaming kernels: 1 partial rows in place, 2 two-row (0: choose)")
+    ap.add_argument("--resident", type=int, default=0,
+                    help="2D: 1 resident tiles, -1 never (0: the plan chooses)")
     ap.add_argument("--storage", type=int, default=0, help="grid storage: 0 float32, 1 bf16, 2 fp16")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baselines")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")

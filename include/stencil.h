@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define ST_ABI_VERSION 3
+#define ST_ABI_VERSION 4
 
 /* status codes */
 #define ST_OK                    0
@@ -86,8 +86,8 @@ typedef struct {
                         (scale 1); fp16 differences saturate at +-65504) */
     int force_T;     /* fused steps per pass (par_time, Sec. 3.2); 0 = the plan chooses */
     int force_bx;    /* tile width in cells incl. halos (bsize_x, Sec. 3.1); 0 = choose */
-    int force_by;    /* 3D: tile height in cells incl. halos (bsize_y); 0 = choose.  2D
-                        contracted plans: 1 = the variant that updates partial rows in place */
+    int force_by;    /* 3D: tile height in cells incl. halos (bsize_y); 0 = choose.  2D: must
+                        be 0 */
     int force_vec;   /* 2D: cells per thread along x (par_vec, Sec. 3.1); 3D: cells per thread,
                         16 (2 x 8 rows, three-plane windows), 8 (2 x 4 rows) or 4 (2 x 2 rows;
                         8 and 4: partial sums along z, contracted only); 0 = choose */
@@ -98,6 +98,14 @@ typedef struct {
                         star diffusion of that radius (4*rad+1 points; ST_DIFFUSION, 2D, float32
                         storage), coefficients [cc, then per distance d = 1..rad: cw_d, ce_d,
                         cs_d, cn_d], each neighbour clamped to the grid on its axis (Sec. 5.1) */
+    int partial_rows; /* 2D contracted streaming kernels: 1 = partial sums updated in place,
+                        2 = two alternating sets of partial rows, 0 = choose */
+    int resident;    /* 2D float32 plans of ST_DIFFUSION / ST_THERMAL, rad <= 1: 1 = resident
+                        tiles (the whole grid stays on chip for the whole run: ONE cooperative
+                        launch per run, halos exchanged through L2 every T steps; ST_ERR_UNSUPPORTED
+                        when the grid does not fit), -1 = never, 0 = the plan chooses (resident
+                        when the grid fits and nothing else is forced; force_T then sets the
+                        steps per exchange and force_vec the cells per thread along x, 2 or 4) */
 } stencil_desc;
 
 /* What a plan chose (for reports and tests). */
@@ -115,6 +123,9 @@ typedef struct {
     double model_gcells;   /* the GPU restatement of Eqs. 3-9 with the library's calibration,
                               for this plan at 1000 steps, in 10^9 cell updates/s; 0 where no
                               calibration exists (exact and 16-bit plans) */
+    int resident;       /* 1: resident tiles (T = steps between halo exchanges, bx x by the
+                           tile incl. halos, ctas the co-resident blocks); 0: passes */
+    int partial_rows;   /* 2D contracted streaming kernels: 1 in place, 2 two-row; else 0 */
 } stencil_plan_info;
 
 /* Create a plan for one problem shape on the current CUDA device.  Allocates one grid-sized
@@ -157,6 +168,14 @@ int stencil_run_trajectory(stencil_plan plan, const void *grid_in, void *states,
  * ST_ERR_TIMEOUT) or ST_OK. */
 int stencil_plan_sync(stencil_plan plan);
 
+/* Bounded waits of a resident-tile plan: a block waits at most wait_ns (> 0; default 1 s) for a
+ * neighbour's halo cells, then sets the plan's error flag (stencil_plan_sync returns
+ * ST_ERR_TIMEOUT) and every block leaves; the output is then undefined.  hold_block >= 0 makes
+ * that block stop publishing its cells from exchange hold_epoch (0-based) on (a test of the
+ * timeout path: its neighbours give up); -1 = none.  Errors: ST_ERR_INVALID_ARG (no plan, wait_ns <= 0),
+ * ST_ERR_UNSUPPORTED (the plan does not run resident tiles). */
+int stencil_plan_set_wait(stencil_plan plan, long long wait_ns, int hold_block, int hold_epoch);
+
 /* Fill *info with the plan's chosen parameters. */
 int stencil_plan_get_info(stencil_plan plan, stencil_plan_info *info);
 
@@ -178,6 +197,7 @@ int stencil_plan_destroy(stencil_plan plan);
  * stencil_plan_create consults whenever its desc forces nothing. */
 typedef struct {
     int force_T, force_bx, force_by, force_vec;   /* the fastest configuration, as desc forces */
+    int partial_rows, resident;                   /* (with these two desc fields) */
     double gcells;        /* its measured rate, 10^9 cell updates/s */
     double model_gcells;  /* the model's rate for it (0 where the family has no calibration) */
     int candidates;       /* compiled configurations for the problem */
@@ -187,7 +207,8 @@ typedef struct {
 /* Rank every compiled configuration for *desc by the model, run the top_k of them
  * (top_k = 0: all) once untimed and once timed (CUDA events on desc->stream) on the caller's
  * grids, and cache the fastest.
- * desc     : as for stencil_plan_create, with every force_* field 0 (else ST_ERR_INVALID_ARG).
+ * desc     : as for stencil_plan_create, with every force_* field, partial_rows and resident
+ *            0 (else ST_ERR_INVALID_ARG).
  * grid_in, power, coeffs : as for stencil_run (device, device or NULL, host); not modified.
  * grid_out : device scratch of the grid's size, distinct from grid_in; its contents afterwards
  *            are the result of a `steps`-step run of the last configuration timed.

@@ -42,7 +42,8 @@ class stencil_desc(ctypes.Structure):
                 ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("storage", ctypes.c_int),
                 ("force_T", ctypes.c_int), ("force_bx", ctypes.c_int), ("force_by", ctypes.c_int),
                 ("force_vec", ctypes.c_int), ("exact", ctypes.c_int), ("strict", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("rad", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("rad", ctypes.c_int), ("partial_rows", ctypes.c_int),
+                ("resident", ctypes.c_int)]
 
 
 class stencil_plan_info(ctypes.Structure):
@@ -50,7 +51,8 @@ class stencil_plan_info(ctypes.Structure):
                 ("halo", ctypes.c_int), ("vec", ctypes.c_int), ("warps", ctypes.c_int),
                 ("ctas", ctypes.c_int), ("sms", ctypes.c_int),
                 ("scratch_bytes", ctypes.c_longlong), ("exact", ctypes.c_int),
-                ("kernel_id", ctypes.c_int), ("model_gcells", ctypes.c_double)]
+                ("kernel_id", ctypes.c_int), ("model_gcells", ctypes.c_double),
+                ("resident", ctypes.c_int), ("partial_rows", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -106,7 +108,8 @@ class stencil_batch_grid(ctypes.Structure):
 
 class stencil_tune_result(ctypes.Structure):
     _fields_ = [("force_T", ctypes.c_int), ("force_bx", ctypes.c_int), ("force_by", ctypes.c_int),
-                ("force_vec", ctypes.c_int), ("gcells", ctypes.c_double),
+                ("force_vec", ctypes.c_int), ("partial_rows", ctypes.c_int),
+                ("resident", ctypes.c_int), ("gcells", ctypes.c_double),
                 ("model_gcells", ctypes.c_double), ("candidates", ctypes.c_int),
                 ("timed", ctypes.c_int)]
 
@@ -123,6 +126,7 @@ SIGNATURES = {
     "stencil_plan_create": ([ctypes.POINTER(_P), ctypes.POINTER(stencil_desc)], _I),
     "stencil_run": ([_P, _P, _P, _P, ctypes.POINTER(ctypes.c_float), _I, _I, _I, _I], _I),
     "stencil_plan_sync": ([_P], _I),
+    "stencil_plan_set_wait": ([_P, ctypes.c_longlong, _I, _I], _I),
     "stencil_plan_get_info": ([_P, ctypes.POINTER(stencil_plan_info)], _I),
     "stencil_plan_set_timing": ([_P, _I], _I),
     "stencil_plan_kernel_time": ([_P, ctypes.POINTER(ctypes.c_double),
@@ -215,17 +219,18 @@ def current_stream():
 
 
 def _desc(kind, ndim, nx, ny, nz, storage, force_T, force_bx, force_by, force_vec, exact, strict,
-          stream, rad):
+          stream, rad, partial_rows=0, resident=0):
     return stencil_desc(kind, ndim, nx, ny, nz if ndim == 3 else 1, storage, force_T, force_bx,
                         force_by, force_vec, 1 if exact else 0, 1 if strict else 0,
-                        current_stream() if stream is None else stream, rad)
+                        current_stream() if stream is None else stream, rad, partial_rows,
+                        resident)
 
 
 def stencil_plan_create(kind: int, ndim: int, nx: int, ny: int, nz: int = 1, *, storage=ST_F32,
                         force_T=0, force_bx=0, force_by=0, force_vec=0, exact=False,
-                        strict=False, stream=None, rad=0):
+                        strict=False, stream=None, rad=0, partial_rows=0, resident=0):
     d = _desc(kind, ndim, nx, ny, nz, storage, force_T, force_bx, force_by, force_vec, exact,
-              strict, stream, rad)
+              strict, stream, rad, partial_rows, resident)
     h = ctypes.c_void_p()
     _check(lib.stencil_plan_create(ctypes.byref(h), ctypes.byref(d)), "stencil_plan_create")
     return h
@@ -470,6 +475,11 @@ class Plan:
 
     def sync(self):
         stencil_plan_sync(self.h)
+
+    def set_wait(self, wait_ns, hold_block=-1, hold_epoch=-1):
+        """Bounded waits of a resident-tile plan (see stencil_plan_set_wait)."""
+        _check(lib.stencil_plan_set_wait(self.h, int(wait_ns), int(hold_block), int(hold_epoch)),
+               "stencil_plan_set_wait")
 
     def info(self):
         return stencil_plan_get_info(self.h)

@@ -34,6 +34,8 @@ struct PassCfg3D {
     int ntx = 0, nty = 0;
     long long cols = 0, planes_per_cta = 0;
     int ctas = 0;
+    int zslab = 0;          // > 0: round-robin pieces of zslab planes (partial-sum kernel)
+    long long pieces = 0;
     bool ready = false;
 };
 
@@ -76,6 +78,14 @@ struct stencil_plan_s {
     float2 *qm[2] = {nullptr, nullptr};
     void *qp = nullptr;
     float2 *qpm = nullptr;
+    // resident tiles (2D): the whole grid on chip for the run, one cooperative launch
+    int res = 0, res_vx = 4, res_nw = 0, res_nbx = 0, res_nby = 0, res_cw = 0, res_ch = 0, res_hx = 0;
+    float *res_xg = nullptr;      // two exchange grids, rows of res_ld floats
+    long long res_ld = 0;
+    int *res_flags = nullptr;     // per block: epochs published (grow across runs)
+    int res_epoch = 0;            // epoch base of the next run
+    long long res_wait_ns = 1000000000LL;
+    int res_hold_block = -1, res_hold_epoch = -1;
 };
 
 namespace {
@@ -233,6 +243,112 @@ double batch_model_gcells(int kind, int nx, int ny, int steps, int sms, int T, i
 
 namespace {
 
+// ---- resident tiles (res2d.cu) ---------------------------------------------------------------
+// A 2D grid that fits the co-resident blocks is held on chip for the whole run; the chosen
+// (T, cells per thread, block rows) minimises the same kind of restated run time as Eqs. 3-9:
+//   t(steps) = steps * t_step + (epochs - 1) * t_x + t_launch + t_io,
+//   t_step   = (cells held per SM) * ops / (issue rate of an SM) + t_bar,
+// a cell held being one of a tile incl. its halos (Sec. 3.2's redundant compute), ops the issued
+// thread instructions per cell and step (the Table 2 operations, the shuffles of the lane edges,
+// the row exchange between warps, loop overhead), t_bar the per-step barrier of that exchange,
+// t_x one exchange through L2 after every T steps (publish, neighbour wait, halo reload), t_io
+// the single read and write of the grid.  Calibrated on GB300 (least squares over 93 measured
+// configurations of 512^2 and 1024^2 grids, T = 1..16, 2 and 4 cells per lane, both kinds,
+// exact and contracted; 97 % within 0.8-1.2 of measured): issue efficiency 0.53, t_x = 6.7 us.
+struct ResGeom {
+    int T = 0, vx = 0, nw = 0, nbx = 0, nby = 0, cw = 0, ch = 0, hx = 0;
+    double t = 0.0;   // predicted seconds for 1000 steps
+};
+
+double res_time(const stencil_desc &d, int sms, const ResGeom &g, int steps)
+{
+    const int VY = res2d_rows_per_thread();
+    const double per_sm = std::ceil((double)g.nbx * g.nby / sms);
+    const double cells = per_sm * g.nw * 32.0 * g.vx * VY;
+    double fp = d.kind == ST_DIFFUSION ? 5.0 : 6.0;
+    if (d.exact) fp = d.kind == ST_DIFFUSION ? 9.0 : 13.0;
+    const double ops = fp + 2.0 / g.vx + 4.0 / (g.vx * VY) + 1.0;
+    const double t_step = cells * ops / (128.0 * 0.53 * 2.07e9) + 0.1e-6;
+    const double t_x = 6.7e-6;
+    const int epochs = (steps + g.T - 1) / g.T;
+    return steps * t_step + (epochs - 1) * t_x + 5e-6 + (double)d.nx * d.ny * 8.0 / 6.8e12;
+}
+
+// The fastest resident geometry with T steps per exchange and vx cells per thread along x;
+// false when the grid does not fit the co-resident blocks of the device.
+bool res_geometry(const stencil_desc &d, int sms, int T, int vx, ResGeom *out)
+{
+    const int kind = d.kind;
+    if (T < 1 || !res2d_available(kind, d.exact, vx)) return false;
+    const int VY = res2d_rows_per_thread(), maxw = res2d_max_warps(kind, d.exact, vx);
+    const int hx = (T + vx - 1) / vx * vx, hy = T;   // x-halo a multiple of vx: x = 0 is a cell 0
+    const int cw = 32 * vx - 2 * hx;
+    if (cw < 1) return false;
+    const int nbx = (d.nx + cw - 1) / cw;
+    if (nbx > 1 && cw < hx) return false;   // a halo must not reach past the next block
+    std::vector<int> bps(maxw + 1, 0);
+    bool found = false;
+    ResGeom best;
+    for (int nby = 1; nby <= d.ny; nby++) {
+        const int ch = (d.ny + nby - 1) / nby;
+        if (nby > 1 && ch < hy) break;
+        if ((long long)(nby - 1) * ch >= d.ny) continue;   // the last block would be empty
+        const int nw = (ch + 2 * hy + VY - 1) / VY;
+        if (nw > maxw) continue;
+        if (!bps[nw]) {
+            int b = 0;
+            if (res2d_occupancy(kind, d.exact, vx, nw, &b) != cudaSuccess) {
+                (void)cudaGetLastError();
+                b = 0;
+            }
+            bps[nw] = b > 0 ? b : -1;
+        }
+        if (bps[nw] < 1 || (long long)nbx * nby > (long long)sms * bps[nw]) continue;
+        ResGeom g;
+        g.T = T;
+        g.vx = vx;
+        g.nw = nw;
+        g.nbx = nbx;
+        g.nby = nby;
+        g.cw = cw;
+        g.ch = ch;
+        g.hx = hx;
+        g.t = res_time(d, sms, g, 1000);
+        if (!found || g.t < best.t) {
+            best = g;
+            found = true;
+        }
+    }
+    if (found) *out = best;
+    return found;
+}
+
+// the best resident geometry over the compiled cells per thread and the candidate T (forced
+// values restrict the search)
+bool res_choose(const stencil_desc &d, int sms, ResGeom *out)
+{
+    bool found = false;
+    for (int vx : {2, 4}) {
+        if (d.force_vec && d.force_vec != vx) continue;
+        for (int t : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32}) {
+            if (d.force_T && t != d.force_T) continue;
+            ResGeom g;
+            if (res_geometry(d, sms, t, vx, &g) && (!found || g.t < out->t)) {
+                *out = g;
+                found = true;
+            }
+        }
+        if (d.force_T && !found) {   // a forced T outside the list above
+            ResGeom g;
+            if (res_geometry(d, sms, d.force_T, vx, &g) && (!found || g.t < out->t)) {
+                *out = g;
+                found = true;
+            }
+        }
+    }
+    return found;
+}
+
 // smallest compiled kernel T >= want for the plan's family (or the largest compiled one)
 int kernel_T_for(const stencil_plan_s *p, int want)
 {
@@ -322,6 +438,36 @@ int prepare3(stencil_plan_s *p, int Tk, PassCfg3D **out)
                                              std::max<long long>(1, total / min_planes));
         c.planes_per_cta = (total + ctas - 1) / ctas;
         c.ctas = (int)((total + c.planes_per_cta - 1) / c.planes_per_cta);
+        if (p->alg3) {
+            // or pieces (tile column, z-slab) dealt round-robin: the blocks of a round stream
+            // neighbouring tile columns through the same planes together, so the halo cells
+            // a tile reads again come from L2 (with contiguous ranges the neighbours run far
+            // apart in z and every tile reads its halos from device memory: measured on
+            // 512^2 x 256 diffusion, T = 3, DRAM bytes per pass 751 MB with ranges, 504 MB
+            // with 52-plane pieces, 537 MB algorithmic).  Taken when the rounds cost at most
+            // 6 % more plane-times per block (planes plus T of pipeline fill per segment) than
+            // the contiguous ranges (512^3 diffusion: 103-plane pieces, 945 GCell/s against
+            // 919 with ranges).
+            const long long slots = (long long)p->sms * bps;
+            const double range_cost = (double)c.planes_per_cta + Tk;
+            double best = 0.0;
+            int best_z = 0;
+            for (int S = 1; S <= std::max(1, p->d.nz / (2 * Tk)); S++) {
+                const int Z = (p->d.nz + S - 1) / S;
+                const long long pieces = c.cols * ((p->d.nz + Z - 1) / Z);
+                const long long G = std::min(slots, pieces);
+                const double cost = (double)((pieces + G - 1) / G) * (Z + Tk);
+                if (!best_z || cost < best) {
+                    best = cost;
+                    best_z = Z;
+                }
+            }
+            if (best_z > 0 && best <= 1.06 * range_cost) {
+                c.zslab = best_z;
+                c.pieces = c.cols * ((p->d.nz + best_z - 1) / best_z);
+                c.ctas = (int)std::min(slots, c.pieces);
+            }
+        }
         c.ready = true;
     }
     *out = &c;
@@ -439,6 +585,81 @@ int run_pass2(stencil_plan_s *p, const float *src, long long lds, float *dst, lo
     return map_cuda(e);
 }
 
+// a run of a resident-tile plan: one cooperative launch (after zeroing the blocks' epoch
+// counters)
+int run_resident(stencil_plan_s *p, const float *in, float *out, const float *pw, const float *k,
+                 int steps)
+{
+    const stencil_desc &d = p->d;
+    Res2D a = {};
+    a.in = in;
+    a.ld_in = d.nx;
+    a.out = out;
+    cudaError_t e = cudaSuccess;
+    const int epochs = (steps + p->T - 1) / p->T;
+    if (in == out && epochs == 1) {
+        // in place with no exchange between the blocks' first read and last write: a block
+        // could overwrite cells a neighbour has yet to read, so the run reads a copy (in the
+        // exchange grids, unused by a single epoch)
+        float *cp = p->res_xg;
+        e = cudaMemcpy2DAsync(cp, (size_t)p->res_ld * sizeof(float), in, (size_t)d.nx * sizeof(float),
+                              (size_t)d.nx * sizeof(float), d.ny, cudaMemcpyDeviceToDevice, p->stream);
+        if (e != cudaSuccess) return map_cuda(e);
+        a.in = cp;
+        a.ld_in = p->res_ld;
+    }
+    a.aux = pw;
+    a.ld_aux = d.nx;
+    a.xg = p->res_xg;
+    a.xplane = p->res_ld * d.ny;
+    a.ld_x = p->res_ld;
+    if (epochs > 1) {
+        if (p->res_epoch > 0x7fffffff - epochs) {
+            // the counters would overflow: start again from zero
+            e = cudaMemsetAsync(p->res_flags, 0, (size_t)p->res_nbx * p->res_nby * sizeof(int), p->stream);
+            if (e != cudaSuccess) return map_cuda(e);
+            p->res_epoch = 0;
+        }
+        a.epoch0 = p->res_epoch;
+        p->res_epoch += epochs;
+    }
+    a.flags = p->res_flags;
+    a.status = p->err;
+    a.wait_ns = p->res_wait_ns;
+    a.hold_block = p->res_hold_block;
+    a.hold_epoch = p->res_hold_epoch;
+    a.nx = d.nx;
+    a.ny = d.ny;
+    a.steps = steps;
+    a.T = p->T;
+    a.nbx = p->res_nbx;
+    a.nby = p->res_nby;
+    a.cw = p->res_cw;
+    a.ch = p->res_ch;
+    a.hx = p->res_hx;
+    a.hy = p->T;
+    if (d.kind == ST_THERMAL && !d.exact) {
+        // the expanded weights cc, cx, cy, cz of the contracted Hotspot kernels
+        float kf[7];
+        hot_coeffs_src(k, kf);
+        for (int i = 0; i < 4; i++) a.k[i] = kf[i];
+        a.src_sdc = k[0];
+        a.src_a = k[4] * k[3];   // amb * Rz, rounded once
+    } else {
+        for (int i = 0; i < 5; i++) a.k[i] = k[i];
+    }
+    if (p->timing && p->ev_used + 2 > 2 * 1024) {
+        const int rc = flush_timing(p);
+        if (rc != ST_OK) return rc;
+    }
+    e = record(p, true);
+    if (e == cudaSuccess)
+        e = res2d_launch(d.kind, d.exact, p->res_vx, p->res_nw, a,
+                         p->stream);
+    if (e == cudaSuccess) e = record(p, false);
+    return map_cuda(e);
+}
+
 // one pass of a 16-bit plan: coded grid q[src] -> q[dst], always the plan's T kernel (the
 // trailing stages forward when tsteps < T), so the block codes keep the plan's tiling
 int run_pass2q(stencil_plan_s *p, int src, int dst, const float *k, int tsteps)
@@ -550,6 +771,8 @@ int run_pass3(stencil_plan_s *p, const float *src, float *dst, const float *pw, 
     a.total_cols = c->cols;
     a.planes_per_cta = c->planes_per_cta;
     a.ctas = c->ctas;
+    a.zslab = c->zslab;
+    a.pieces = c->pieces;
     for (int i = 0; i < 9; i++) a.k[i] = i < ncoef(p->d) ? k[i] : 0.f;
     a.vec = ((uintptr_t)src % 16 == 0) && ((uintptr_t)dst % 16 == 0) && (p->d.nx % 4 == 0);
     a.vec_pw = pw && ((uintptr_t)pw % 16 == 0) && (p->d.nx % 4 == 0);
@@ -603,9 +826,17 @@ int stencil_plan_create(stencil_plan *out, const stencil_desc *desc)
 {
     // nothing forced and a measured choice cached for this problem: take it (an entry this
     // build cannot make falls back to the model's choice)
-    if (out && desc && !desc->force_T && !desc->force_bx && !desc->force_by && !desc->force_vec) {
+    if (out && desc && !desc->force_T && !desc->force_bx && !desc->force_by && !desc->force_vec &&
+        !desc->partial_rows && !desc->resident) {
         stencil_desc t = *desc;
-        if (tune_cache_lookup(t, &t.force_T, &t.force_bx, &t.force_by, &t.force_vec)) {
+        int f[6];
+        if (tune_cache_lookup(t, f)) {
+            t.force_T = f[0];
+            t.force_bx = f[1];
+            t.force_by = f[2];
+            t.force_vec = f[3];
+            t.partial_rows = f[4];
+            t.resident = f[5];
             const int rc = plan_create(out, &t);
             if (rc == ST_OK) {
                 (*out)->tuned = 1;
@@ -637,6 +868,14 @@ static int plan_create(stencil_plan *out, const stencil_desc *desc)
     if (d.force_T < 0 || d.force_bx < 0 || d.force_by < 0 || d.force_vec < 0)
         return ST_ERR_INVALID_ARG;
     if (d.rad < 0) return ST_ERR_INVALID_ARG;
+    if (d.partial_rows < 0 || d.partial_rows > 2 || d.resident < -1 || d.resident > 1)
+        return ST_ERR_INVALID_ARG;
+    if (d.ndim == 2 && d.rad <= 1 && d.force_by) return ST_ERR_INVALID_ARG;   // no 2D tile height
+    if (d.partial_rows && (d.ndim != 2 || d.exact || d.kind == ST_DIFFUSION_VAR || d.rad > 1))
+        return ST_ERR_UNSUPPORTED;
+    if (d.resident == 1 && (d.ndim != 2 || d.rad > 1 || d.kind == ST_DIFFUSION_VAR ||
+                            d.storage != ST_F32 || d.force_bx || d.partial_rows))
+        return ST_ERR_UNSUPPORTED;
     // per-cell coefficients: 2D float32 plans of the windowed kernel (V = 4, 128 or 512 cells
     // wide); the stability check of strict plans needs host coefficients
     if (d.kind == ST_DIFFUSION_VAR &&
@@ -727,91 +966,130 @@ static int plan_create(stencil_plan *out, const stencil_desc *desc)
             p->scratch_bytes = (size_t)d.nx * d.ny * sizeof(float);
         }
     } else if (d.ndim == 2) {
-        // Contracted plans run one-warp tiles of V = 8 cells per thread (bsize_x = 256) with
-        // partial-sum stages; exact plans run the rotating-window kernel, V = 4, with W warps
-        // per tile (bsize_x = 128 W).
-        // measured on GB300 (16384^2, T = 8): Hotspot runs best with V = 4 (its V = 8 body
-        // overflows the instruction cache), Diffusion with V = 8
-        const bool var = d.kind == ST_DIFFUSION_VAR;   // windowed kernel, exact or contracted
-        p->V = d.force_vec ? d.force_vec : ((d.exact || d.kind != ST_DIFFUSION) ? 4 : 8);
-        if (d.force_bx) {
-            if (d.force_bx % (32 * p->V)) rc = ST_ERR_UNSUPPORTED;
-            p->W = d.force_bx / (32 * p->V);
-        } else {
-            p->W = 1;
-            if (d.exact && d.nx >= 512) p->W = 4;
+        // resident tiles: when asked for, or compared below with the passes when nothing else
+        // is forced
+        ResGeom rg;
+        bool res = false;
+        if (d.resident == 1) {
+            res = res_choose(d, p->sms, &rg);
+            if (!res) rc = ST_ERR_UNSUPPORTED;
+        } else if (d.resident == 0 && !d.force_T && !d.force_vec && !d.force_bx && !d.partial_rows &&
+                   d.kind != ST_DIFFUSION_VAR && !p->stor) {
+            res = res_choose(d, p->sms, &rg);
         }
-        if (!d.exact && d.force_by == 1) p->W = 0;   // in-place partial-row variant
-        if (p->stor && !d.force_T && !d.force_vec && !d.force_bx && !d.force_by) {
-            // 16-bit storage, nothing forced: T = 8, 8 cells per lane, rows in place (measured
-            // on 16384^2: Hotspot 1990 GCell/s against 1802 for V = 4 two-row; diffusion 2720
-            // against 2380 for V = 8 two-row)
-            p->V = 8;
-            p->W = 0;
-        }
-        if (!d.exact && !var && !p->stor && !d.force_T && !d.force_vec && !d.force_bx && !d.force_by) {
-            // contracted, nothing forced: the compiled (T, V, variant) the model rates best
-            const Cand2D cands[] = {{4, 4, 1}, {8, 4, 1}, {12, 4, 1}, {4, 8, 1}, {6, 8, 1},
-                                    {8, 8, 1}, {8, 8, 0}, {12, 4, 0}};
-            double best = -1.0;
-            for (const Cand2D &k : cands) {
-                const Shape2D sh{d.kind, 0, k.T, k.V, k.W, d.kind == ST_THERMAL ? STOR_SRC : 0};
-                if (!tb2d_available(sh)) continue;
-                int bps = 0;
-                if (tb2d_prepare(sh, &bps) != cudaSuccess || bps < 1) continue;
-                const double g = model_gcells_2d(d, p->sms, k, bps, 1000);
-                if (g > best) {
-                    best = g;
-                    p->V = k.V;
-                    p->W = k.W;
-                }
+        const double res_g = res ? 1000.0 * d.nx * d.ny / rg.t / 1e9 : 0.0;
+        if (d.resident != 1) {
+            // Contracted plans run one-warp tiles of V = 8 cells per thread (bsize_x = 256) with
+            // partial-sum stages; exact plans run the rotating-window kernel, V = 4, with W warps
+            // per tile (bsize_x = 128 W).
+            // measured on GB300 (16384^2, T = 8): Hotspot runs best with V = 4 (its V = 8 body
+            // overflows the instruction cache), Diffusion with V = 8
+            const bool var = d.kind == ST_DIFFUSION_VAR;   // windowed kernel, exact or contracted
+            p->V = d.force_vec ? d.force_vec : ((d.exact || d.kind != ST_DIFFUSION) ? 4 : 8);
+            if (d.force_bx) {
+                if (d.force_bx % (32 * p->V)) rc = ST_ERR_UNSUPPORTED;
+                p->W = d.force_bx / (32 * p->V);
+            } else {
+                p->W = 1;
+                if (d.exact && d.nx >= 512) p->W = 4;
             }
+            if (!d.exact && d.partial_rows == 1) p->W = 0;   // partial rows updated in place
+            if (!d.exact && d.partial_rows == 2) p->W = 1;   // two alternating sets of partial rows
+            if (p->stor && !d.force_T && !d.force_vec && !d.force_bx && !d.partial_rows) {
+                // 16-bit storage, nothing forced: T = 8, 8 cells per lane, rows in place (measured
+                // on 16384^2: Hotspot 1990 GCell/s against 1802 for V = 4 two-row; diffusion 2720
+                // against 2380 for V = 8 two-row)
+                p->V = 8;
+                p->W = 0;
+            }
+            if (!d.exact && !var && !p->stor && !d.force_T && !d.force_vec && !d.force_bx && !d.partial_rows) {
+                // contracted, nothing forced: the compiled (T, V, variant) the model rates best
+                const Cand2D cands[] = {{4, 4, 1}, {8, 4, 1}, {12, 4, 1}, {4, 8, 1}, {6, 8, 1},
+                                        {8, 8, 1}, {8, 8, 0}, {12, 4, 0}};
+                double best = -1.0;
+                for (const Cand2D &k : cands) {
+                    const Shape2D sh{d.kind, 0, k.T, k.V, k.W, d.kind == ST_THERMAL ? STOR_SRC : 0};
+                    if (!tb2d_available(sh)) continue;
+                    int bps = 0;
+                    if (tb2d_prepare(sh, &bps) != cudaSuccess || bps < 1) continue;
+                    const double g = model_gcells_2d(d, p->sms, k, bps, 1000);
+                    if (g > best) {
+                        best = g;
+                        p->V = k.V;
+                        p->W = k.W;
+                    }
+                }
+                (void)cudaGetLastError();
+            }
+            // per-cell coefficients: every fused step keeps five more weight rows per tile column in
+            // shared memory, so deeper fusion costs resident warps; measured on 8192^2 (GB300):
+            // T = 4 with one-warp tiles 608 GCell/s, T = 8 545, four-warp tiles 532 / 451
+            const int want = d.force_T ? d.force_T : (var ? 4 : 8);
+            p->T = kernel_T_for(p, want);
+            if (!d.exact && !var && !p->stor && !d.force_T && !d.force_vec && !d.force_bx && !d.partial_rows) {
+                // and the T the model rates best within that family
+                double best = -1.0;
+                for (int t : kTcand) {
+                    const Shape2D sh{d.kind, 0, t, p->V, p->W, d.kind == ST_THERMAL ? STOR_SRC : 0};
+                    if (!tb2d_available(sh)) continue;
+                    int bps = 0;
+                    if (tb2d_prepare(sh, &bps) != cudaSuccess || bps < 1) continue;
+                    const double g = model_gcells_2d(d, p->sms, Cand2D{t, p->V, p->W}, bps, 1000);
+                    if (g > best) {
+                        best = g;
+                        p->T = t;
+                    }
+                }
+                (void)cudaGetLastError();
+            }
+            if (p->T == 0 || (d.force_T && p->T != d.force_T)) rc = ST_ERR_UNSUPPORTED;
+            PassCfg2D *c = nullptr;
+            if (rc == ST_OK) rc = prepare2(p, p->T, &c);
+            if (rc == ST_OK && p->stor) {
+                // coded grids: rows padded to 8 cells (16 bytes), codes per (row, tile column)
+                p->cx = 32 * p->V - 2 * ((p->T + 3) / 4 * 4);
+                p->ntx = (d.nx + p->cx - 1) / p->cx;
+                p->ld_q = ((long long)d.nx + 7) / 8 * 8;
+                const size_t qb = (size_t)p->ld_q * d.ny * 2, mb = (size_t)p->ntx * d.ny * sizeof(float2);
+                for (int b = 0; b < 2 && rc == ST_OK; b++) {
+                    e = cudaMalloc(&p->q[b], qb);
+                    if (e == cudaSuccess) e = cudaMalloc(&p->qm[b], mb);
+                    if (e != cudaSuccess) rc = map_cuda(e);
+                }
+                if (rc == ST_OK && d.kind == ST_THERMAL) {
+                    e = cudaMalloc(&p->qp, qb);
+                    if (e == cudaSuccess) e = cudaMalloc(&p->qpm, mb);
+                    if (e != cudaSuccess) rc = map_cuda(e);
+                }
+                p->scratch_bytes = 0;   // no float32 scratch: the coded grids take its place
+            } else if (rc == ST_OK) {
+                p->ld_scratch = ((long long)d.nx + 31) / 32 * 32;
+                p->scratch_bytes = (size_t)p->ld_scratch * d.ny * sizeof(float);
+            }
+        }
+        if (res && d.resident == 0 && rc == ST_OK && !d.exact) {
+            // contracted: resident tiles only where the model rates them above the passes
+            // (exact plans: always when the grid fits; the exact passes have no calibration)
+            int bps = 0;
+            const Shape2D sh{d.kind, 0, p->T, p->V, p->W, d.kind == ST_THERMAL ? STOR_SRC : 0};
+            if (tb2d_prepare(sh, &bps) == cudaSuccess && bps > 0 &&
+                model_gcells_2d(d, p->sms, Cand2D{p->T, p->V, p->W}, bps, 1000) >= res_g)
+                res = false;
             (void)cudaGetLastError();
         }
-        // per-cell coefficients: every fused step keeps five more weight rows per tile column in
-        // shared memory, so deeper fusion costs resident warps; measured on 8192^2 (GB300):
-        // T = 4 with one-warp tiles 608 GCell/s, T = 8 545, four-warp tiles 532 / 451
-        const int want = d.force_T ? d.force_T : (var ? 4 : 8);
-        p->T = kernel_T_for(p, want);
-        if (!d.exact && !var && !p->stor && !d.force_T && !d.force_vec && !d.force_bx && !d.force_by) {
-            // and the T the model rates best within that family
-            double best = -1.0;
-            for (int t : kTcand) {
-                const Shape2D sh{d.kind, 0, t, p->V, p->W, d.kind == ST_THERMAL ? STOR_SRC : 0};
-                if (!tb2d_available(sh)) continue;
-                int bps = 0;
-                if (tb2d_prepare(sh, &bps) != cudaSuccess || bps < 1) continue;
-                const double g = model_gcells_2d(d, p->sms, Cand2D{t, p->V, p->W}, bps, 1000);
-                if (g > best) {
-                    best = g;
-                    p->T = t;
-                }
-            }
-            (void)cudaGetLastError();
-        }
-        if (p->T == 0 || (d.force_T && p->T != d.force_T)) rc = ST_ERR_UNSUPPORTED;
-        PassCfg2D *c = nullptr;
-        if (rc == ST_OK) rc = prepare2(p, p->T, &c);
-        if (rc == ST_OK && p->stor) {
-            // coded grids: rows padded to 8 cells (16 bytes), codes per (row, tile column)
-            p->cx = 32 * p->V - 2 * ((p->T + 3) / 4 * 4);
-            p->ntx = (d.nx + p->cx - 1) / p->cx;
-            p->ld_q = ((long long)d.nx + 7) / 8 * 8;
-            const size_t qb = (size_t)p->ld_q * d.ny * 2, mb = (size_t)p->ntx * d.ny * sizeof(float2);
-            for (int b = 0; b < 2 && rc == ST_OK; b++) {
-                e = cudaMalloc(&p->q[b], qb);
-                if (e == cudaSuccess) e = cudaMalloc(&p->qm[b], mb);
-                if (e != cudaSuccess) rc = map_cuda(e);
-            }
-            if (rc == ST_OK && d.kind == ST_THERMAL) {
-                e = cudaMalloc(&p->qp, qb);
-                if (e == cudaSuccess) e = cudaMalloc(&p->qpm, mb);
-                if (e != cudaSuccess) rc = map_cuda(e);
-            }
-            p->scratch_bytes = 0;   // no float32 scratch: the coded grids take its place
-        } else if (rc == ST_OK) {
-            p->ld_scratch = ((long long)d.nx + 31) / 32 * 32;
-            p->scratch_bytes = (size_t)p->ld_scratch * d.ny * sizeof(float);
+        if (res && rc == ST_OK) {
+            p->res = 1;
+            p->T = rg.T;
+            p->res_vx = rg.vx;
+            p->res_nw = rg.nw;
+            p->res_nbx = rg.nbx;
+            p->res_nby = rg.nby;
+            p->res_cw = rg.cw;
+            p->res_ch = rg.ch;
+            p->res_hx = rg.hx;
+            p->res_ld = ((long long)d.nx + 3) / 4 * 4;
+            p->scratch_bytes = 0;   // the two exchange grids take the scratch grid's place
+            p->model = res_g;
         }
     } else {
         // tile width 64 (2 cells per lane) or 128 (4 cells per lane), tile height, cells per
@@ -868,7 +1146,14 @@ static int plan_create(stencil_plan *out, const stencil_desc *desc)
         e = cudaMalloc(&p->src, (size_t)p->ld_src * d.ny * sizeof(float));
         if (e != cudaSuccess) rc = map_cuda(e);
     }
-    if (rc == ST_OK && !d.exact && !p->stor && d.rad <= 1 && d.kind != ST_DIFFUSION_VAR) {
+    if (rc == ST_OK && p->res) {
+        const size_t fb = (size_t)p->res_nbx * p->res_nby * sizeof(int);
+        e = cudaMalloc(&p->res_xg, (size_t)2 * p->res_ld * d.ny * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&p->res_flags, fb);
+        if (e == cudaSuccess) e = cudaMemset(p->res_flags, 0, fb);
+        if (e != cudaSuccess) rc = map_cuda(e);
+    }
+    if (rc == ST_OK && !p->res && !d.exact && !p->stor && d.rad <= 1 && d.kind != ST_DIFFUSION_VAR) {
         if (d.ndim == 2) {
             int bps = 0;
             const Shape2D sh{d.kind, 0, p->T, p->V, p->W, d.kind == ST_THERMAL ? STOR_SRC : 0};
@@ -921,6 +1206,11 @@ int stencil_run(stencil_plan p, const void *grid_in, void *grid_out, const void 
         if (in == out) return ST_OK;
         e = cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, p->stream);
         return map_cuda(e);
+    }
+    if (p->res) {
+        const int rc = run_resident(p, in, out, pw, coeffs, steps);
+        if (rc != ST_OK) p->sticky = rc;
+        return rc;
     }
     const int T = p->T;
     const int passes = (steps + T - 1) / T;
@@ -1051,6 +1341,16 @@ int stencil_plan_sync(stencil_plan p)
     return p->sticky;
 }
 
+int stencil_plan_set_wait(stencil_plan p, long long wait_ns, int hold_block, int hold_epoch)
+{
+    if (!p || wait_ns <= 0 || hold_block < -1) return ST_ERR_INVALID_ARG;
+    if (!p->res) return ST_ERR_UNSUPPORTED;
+    p->res_wait_ns = wait_ns;
+    p->res_hold_block = hold_block;
+    p->res_hold_epoch = hold_block >= 0 ? hold_epoch : -1;
+    return ST_OK;
+}
+
 int stencil_plan_get_info(stencil_plan p, stencil_plan_info *info)
 {
     if (!p || !info) return ST_ERR_INVALID_ARG;
@@ -1060,6 +1360,20 @@ int stencil_plan_get_info(stencil_plan p, stencil_plan_info *info)
     info->sms = p->sms;
     info->scratch_bytes = (long long)p->scratch_bytes;
     info->exact = p->d.exact;
+    info->partial_rows = (p->d.ndim == 2 && !p->d.exact && p->d.rad <= 1 && !p->res &&
+                          p->d.kind != ST_DIFFUSION_VAR) ? (p->W == 0 ? 1 : 2) : 0;
+    if (p->res) {
+        info->resident = 1;
+        info->bx = 32 * p->res_vx;
+        info->by = p->res_nw * res2d_rows_per_thread();
+        info->halo = p->res_hx;
+        info->vec = p->res_vx;
+        info->warps = p->res_nw;
+        info->ctas = p->res_nbx * p->res_nby;
+        info->scratch_bytes = (long long)2 * p->res_ld * p->d.ny * sizeof(float);
+        info->kernel_id = 7;
+        return ST_OK;
+    }
     if (p->d.rad > 1 && p->d.ndim == 3) {
         int cx = 0, cy = 0;
         star3d_tile(p->d.rad, p->T, &cx, &cy);
@@ -1140,6 +1454,8 @@ int stencil_plan_destroy(stencil_plan p)
     if (p->qpm) cudaFree(p->qpm);
     if (p->err) cudaFree(p->err);
     if (p->src) cudaFree(p->src);
+    if (p->res_xg) cudaFree(p->res_xg);
+    if (p->res_flags) cudaFree(p->res_flags);
     delete p;
     return ST_OK;
 }

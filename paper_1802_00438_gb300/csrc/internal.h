@@ -177,6 +177,8 @@ struct Pass3D {
     long long total_cols;  // ntx * nty tile columns (each streamed along z)
     long long planes_per_cta;
     int ctas;
+    int zslab;             // partial-sum kernel: > 0 = pieces of zslab planes, round-robin
+    long long pieces;      // total_cols * ceil(nz / zslab)
     float k[9];
     int vec;               // 1: rows start on 16-byte boundaries
     int vec_pw;            // 1: the power map's rows start on 16-byte boundaries
@@ -203,7 +205,37 @@ cudaError_t tb3d_launch(const Shape3D &s, const Pass3D &p, const Tma3D &t, cudaS
 // driver entry point or the encoding is unavailable
 bool tma3d_encode(CUtensorMap *m, const float *base, int nx, int ny, int nz, int bx, int by);
 
-// tuning cache (tune.cu): the measured configuration for the desc's problem key, if any
-bool tune_cache_lookup(const stencil_desc &d, int *T, int *bx, int *by, int *vec);
+// Resident tiles (res2d.cu): the whole 2D grid held on chip by nbx x nby co-resident blocks
+// for a run of `steps` steps, halos exchanged through L2 every T steps (an epoch).
+struct Res2D {
+    const float *in;       // grid_in, rows of ld_in floats
+    long long ld_in;
+    float *out;            // grid_out, dense rows of nx
+    const float *aux;      // Hotspot: the power map, rows of ld_aux floats
+    long long ld_aux;
+    float src_sdc, src_a;  // contracted Hotspot: the source map sdc*(p + amb*Rz), a = amb*Rz
+    float *xg;             // two exchange grids (epoch parity), rows of ld_x floats
+    long long xplane, ld_x;
+    int *flags;            // per block: epochs published, as epoch0 + e + 1 (never reset)
+    int epoch0;
+    int *status;           // set to 1 by a wait that gave up
+    long long wait_ns;     // bound of every wait
+    int hold_block, hold_epoch;   // test hook: that block publishes no exchange >= hold_epoch
+    int nx, ny, steps, T;
+    int nbx, nby, cw, ch, hx, hy;   // blocks, compute block size, halo widths
+    float k[5];            // Diffusion: cc cw ce cs cn; Hotspot exact: sdc Rx Ry Rz amb;
+                           // Hotspot contracted: cc cx cy cz (expanded weights)
+};
+
+int res2d_rows_per_thread();
+int res2d_max_warps(int kind, int exact, int vx);
+size_t res2d_smem(int vx, int nw);
+bool res2d_available(int kind, int exact, int vx);
+cudaError_t res2d_occupancy(int kind, int exact, int vx, int nw, int *blocks_per_sm);
+cudaError_t res2d_launch(int kind, int exact, int vx, int nw, const Res2D &a, cudaStream_t st);
+
+// tuning cache (tune.cu): the measured configuration for the desc's problem key, if any, as
+// desc fields (force_T, force_bx, force_by, force_vec, partial_rows, resident)
+bool tune_cache_lookup(const stencil_desc &d, int *f6);
 
 }  // namespace stn

@@ -565,14 +565,30 @@ __global__ void __launch_bounds__(32 * NW, (TB3F<KIND, T, VX, VY, NW>::MINB))
 #pragma unroll
             for (int j = 0; j < VX; j++) PA[s][k][j] = QA[s][k][j] = PB[s][k][j] = QB[s][k][j] = 0.f;
 
-    long long f = (long long)blockIdx.x * p.planes_per_cta;
+    // segments: zslab > 0 -- pieces (tile column, z-slab), taken round-robin, so that the
+    // blocks of one round stream neighbouring tile columns through the same z-planes together
+    // and the halo one of them re-reads is still in L2; else a contiguous range of
+    // (tile column, plane) units per block
+    long long f = (long long)blockIdx.x * p.planes_per_cta, pc = blockIdx.x;
     const long long total = p.total_cols * p.nz;
     const long long fend = min(f + p.planes_per_cta, total);
-    while (f < fend) {
-        const long long col = f / p.nz;
-        const int z0 = (int)(f - col * p.nz);
-        const int z1 = (int)min((long long)p.nz, (long long)z0 + (fend - f));
-        f += z1 - z0;
+    for (;;) {
+        long long col;
+        int z0, z1;
+        if (p.zslab > 0) {
+            if (pc >= p.pieces) break;
+            const long long sl = pc / p.total_cols;
+            col = pc - sl * p.total_cols;
+            z0 = (int)(sl * p.zslab);
+            z1 = min(p.nz, z0 + p.zslab);
+            pc += gridDim.x;
+        } else {
+            if (f >= fend) break;
+            col = f / p.nz;
+            z0 = (int)(f - col * p.nz);
+            z1 = (int)min((long long)p.nz, (long long)z0 + (fend - f));
+            f += z1 - z0;
+        }
         const int ty = (int)(col / p.ntx), tx = (int)(col - (long long)ty * p.ntx);
 
         c.z0 = z0;

@@ -22,7 +22,7 @@ namespace {
 using Key = std::tuple<int, int, int, int, int, int, int, int>;
 
 struct Choice {
-    int T, bx, by, vec;
+    std::array<int, 6> f;   // force_T, force_bx, force_by, force_vec, partial_rows, resident
     double gcells;
 };
 
@@ -35,31 +35,45 @@ Key key_of(const stencil_desc &d)
                d.rad > 1 ? d.rad : 0};
 }
 
-// Every configuration a plan can be forced to, as (force_T, force_bx, force_by, force_vec);
-// those not compiled into the library are refused by stencil_plan_create and skipped.
-std::vector<std::array<int, 4>> candidates(const stencil_desc &d)
+// Every configuration a plan can be forced to, as (force_T, force_bx, force_by, force_vec,
+// partial_rows, resident); those not compiled into the library, or resident tiles of a grid
+// that does not fit, are refused by stencil_plan_create and skipped.
+std::vector<std::array<int, 6>> candidates(const stencil_desc &d)
 {
-    std::vector<std::array<int, 4>> c;
+    std::vector<std::array<int, 6>> c;
     const int Ts[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16};
     if (d.rad > 1) {
-        for (int T : Ts) c.push_back({T, 0, 0, 0});
+        for (int T : Ts) c.push_back({T, 0, 0, 0, 0, -1});
     } else if (d.ndim == 2) {
         for (int V : {4, 8})
             for (int T : Ts) {
                 if (d.exact || d.kind == ST_DIFFUSION_VAR) {   // the windowed kernel
                     if (V != 4) continue;
-                    for (int bx : {128, 512}) c.push_back({T, bx, 0, 4});
+                    for (int bx : {128, 512}) c.push_back({T, bx, 0, 4, 0, -1});
                 } else {
-                    c.push_back({T, 0, 0, V});
-                    c.push_back({T, 0, 1, V});   // in-place rows
+                    c.push_back({T, 0, 0, V, 2, -1});   // two alternating partial rows
+                    c.push_back({T, 0, 0, V, 1, -1});   // partial rows in place
                 }
             }
+        if (d.kind != ST_DIFFUSION_VAR && d.storage == ST_F32)
+            for (int V : {2, 4})
+                for (int T : Ts) c.push_back({T, 0, 0, V, 0, 1});   // resident tiles
     } else {
         const int shapes[][3] = {{64, 64, 16}, {64, 64, 8}, {64, 64, 4}, {128, 32, 8}, {64, 32, 8}};
         for (const auto &s : shapes)
-            for (int T : Ts) c.push_back({T, s[0], s[1], s[2]});
+            for (int T : Ts) c.push_back({T, s[0], s[1], s[2], 0, 0});
     }
     return c;
+}
+
+void apply_config(stencil_desc &d, const std::array<int, 6> &f)
+{
+    d.force_T = f[0];
+    d.force_bx = f[1];
+    d.force_by = f[2];
+    d.force_vec = f[3];
+    d.partial_rows = f[4];
+    d.resident = f[5];
 }
 
 struct Events {
@@ -81,15 +95,12 @@ int status(cudaError_t e)
 
 namespace stn {
 
-bool tune_cache_lookup(const stencil_desc &d, int *T, int *bx, int *by, int *vec)
+bool tune_cache_lookup(const stencil_desc &d, int *f6)
 {
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_cache.find(key_of(d));
     if (it == g_cache.end()) return false;
-    *T = it->second.T;
-    *bx = it->second.bx;
-    *by = it->second.by;
-    *vec = it->second.vec;
+    for (int i = 0; i < 6; i++) f6[i] = it->second.f[i];
     return true;
 }
 
@@ -103,7 +114,8 @@ int stencil_tune(const stencil_desc *desc, const void *grid_in, void *grid_out, 
     if (!desc || !grid_in || !grid_out || !coeffs || !result || steps < 1 || top_k < 0 ||
         grid_in == grid_out)   // the timed runs must leave the input as it was
         return ST_ERR_INVALID_ARG;
-    if (desc->force_T || desc->force_bx || desc->force_by || desc->force_vec)
+    if (desc->force_T || desc->force_bx || desc->force_by || desc->force_vec ||
+        desc->partial_rows || desc->resident)
         return ST_ERR_INVALID_ARG;   // the tuner chooses these
     if (desc->ndim != 2 && desc->ndim != 3) return ST_ERR_INVALID_ARG;
     const stencil_desc base = *desc;
@@ -112,16 +124,13 @@ int stencil_tune(const stencil_desc *desc, const void *grid_in, void *grid_out, 
     // rank the compiled configurations by the model (stable: build order breaks ties, and
     // families without a calibration keep it)
     struct Cand {
-        std::array<int, 4> f;
+        std::array<int, 6> f;
         double model;
     };
     std::vector<Cand> ranked;
     for (const auto &f : candidates(base)) {
         stencil_desc d = base;
-        d.force_T = f[0];
-        d.force_bx = f[1];
-        d.force_by = f[2];
-        d.force_vec = f[3];
+        apply_config(d, f);
         stencil_plan p = nullptr;
         const int rc = stencil_plan_create(&p, &d);
         if (rc == ST_ERR_UNSUPPORTED) continue;
@@ -148,10 +157,7 @@ int stencil_tune(const stencil_desc *desc, const void *grid_in, void *grid_out, 
     double best_ms = 0.0;
     for (size_t i = 0; i < n; i++) {
         stencil_desc d = base;
-        d.force_T = ranked[i].f[0];
-        d.force_bx = ranked[i].f[1];
-        d.force_by = ranked[i].f[2];
-        d.force_vec = ranked[i].f[3];
+        apply_config(d, ranked[i].f);
         stencil_plan p = nullptr;
         int rc = stencil_plan_create(&p, &d);
         if (rc != ST_OK) return rc;
@@ -174,12 +180,14 @@ int stencil_tune(const stencil_desc *desc, const void *grid_in, void *grid_out, 
     result->force_bx = w.f[1];
     result->force_by = w.f[2];
     result->force_vec = w.f[3];
+    result->partial_rows = w.f[4];
+    result->resident = w.f[5];
     result->gcells = updates / (best_ms * 1e-3) / 1e9;
     result->model_gcells = w.model;
     result->candidates = (int)ranked.size();
     result->timed = (int)n;
     std::lock_guard<std::mutex> lk(g_mu);
-    g_cache[key_of(base)] = Choice{w.f[0], w.f[1], w.f[2], w.f[3], result->gcells};
+    g_cache[key_of(base)] = Choice{w.f, result->gcells};
     return ST_OK;
 }
 
@@ -196,7 +204,8 @@ int stencil_tune_cache_size(void)
     return (int)g_cache.size();
 }
 
-// One line per entry: kind ndim nx ny nz storage exact rad T bx by vec gcells
+// One line per entry: kind ndim nx ny nz storage exact rad T bx by vec partial_rows resident
+// gcells
 int stencil_tune_cache_save(const char *path)
 {
     if (!path) return ST_ERR_INVALID_ARG;
@@ -206,10 +215,10 @@ int stencil_tune_cache_save(const char *path)
     for (const auto &kv : g_cache) {
         const Key &k = kv.first;
         const Choice &c = kv.second;
-        std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %.6g\n", std::get<0>(k),
+        std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %.6g\n", std::get<0>(k),
                      std::get<1>(k), std::get<2>(k), std::get<3>(k), std::get<4>(k),
-                     std::get<5>(k), std::get<6>(k), std::get<7>(k), c.T, c.bx, c.by, c.vec,
-                     c.gcells);
+                     std::get<5>(k), std::get<6>(k), std::get<7>(k), c.f[0], c.f[1], c.f[2],
+                     c.f[3], c.f[4], c.f[5], c.gcells);
     }
     const bool ok = std::fclose(f) == 0;
     return ok ? ST_OK : ST_ERR_INVALID_ARG;
@@ -226,27 +235,28 @@ int stencil_tune_cache_load(const char *path)
     char line[512];
     bool ok = true;
     while (ok && std::fgets(line, sizeof(line), f)) {
-        int v[12];
+        int v[14];
         double g = 0.0;
         int used = 0;
-        const int n = std::sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %d %lf %n", &v[0],
+        const int n = std::sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %lf %n", &v[0],
                                   &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7], &v[8], &v[9],
-                                  &v[10], &v[11], &g, &used);
+                                  &v[10], &v[11], &v[12], &v[13], &g, &used);
         if (n == EOF) continue;   // blank line
-        if (n != 13 || line[used] != '\0') {
+        if (n != 15 || line[used] != '\0') {
             ok = false;
             break;
         }
         const bool valid = (v[0] == ST_DIFFUSION || v[0] == ST_THERMAL) && (v[1] == 2 || v[1] == 3) &&
                            v[2] >= 1 && v[3] >= 1 && v[4] >= 1 && (v[1] == 3 || v[4] == 1) &&
                            v[5] >= ST_F32 && v[5] <= ST_F16 && (v[6] == 0 || v[6] == 1) &&
-                           v[7] >= 0 && v[8] >= 1 && v[9] >= 0 && v[10] >= 0 && v[11] >= 0;
+                           v[7] >= 0 && v[8] >= 1 && v[9] >= 0 && v[10] >= 0 && v[11] >= 0 &&
+                           v[12] >= 0 && v[12] <= 2 && v[13] >= -1 && v[13] <= 1;
         if (!valid) {
             ok = false;
             break;
         }
         got.push_back({Key{v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7]},
-                       Choice{v[8], v[9], v[10], v[11], g}});
+                       Choice{{v[8], v[9], v[10], v[11], v[12], v[13]}, g}});
     }
     std::fclose(f);
     if (!ok) return ST_ERR_INVALID_ARG;

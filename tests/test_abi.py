@@ -41,9 +41,57 @@ def test_binding_covers_header(lib_path):
     assert names == set(st.SIGNATURES), names ^ set(st.SIGNATURES)
 
 
+_CTYPES = {"int": ctypes.c_int, "long long": ctypes.c_longlong, "double": ctypes.c_double,
+           "float": ctypes.c_float, "void *": ctypes.c_void_p, "size_t": ctypes.c_size_t}
+
+
+def _structs(header):
+    """{typedef name: [(field, C type, array length)]} of the header's plain structs."""
+    src = open(os.path.join(ROOT, "include", header)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct\s*\{(.*?)\}\s*(\w+)\s*;", src, re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            m = re.match(r"(long long|unsigned int|int|double|float|size_t|void \*|const \w+ \*)\s*(.*)", decl)
+            assert m, decl
+            ctype = m.group(1)
+            for item in m.group(2).split(","):
+                item = item.strip()
+                star = item.startswith("*")
+                item = item.lstrip("*").strip()
+                am = re.match(r"(\w+)(?:\[(\d+)\])?$", item)
+                assert am, item
+                fields.append((am.group(1), "void *" if star else ctype,
+                               int(am.group(2)) if am.group(2) else 0))
+        out[name] = fields
+    return out
+
+
+def test_binding_structs_match_header(lib_path):
+    # every struct of the header has a ctypes twin with the same fields, in order, of the same
+    # types: a field added on one side only would shift everything after it
+    import paper_1802_00438_gb300 as st
+    structs = _structs("stencil.h")
+    assert {"stencil_desc", "stencil_plan_info", "stencil_tune_result"} <= set(structs)
+    for name, fields in structs.items():
+        twin = getattr(st, name)
+        got = [(f, t) for f, t in twin._fields_]
+        assert [f for f, _ in got] == [f for f, _, _ in fields], name
+        for (f, t), (_, ctype, n) in zip(got, fields):
+            want = _CTYPES.get(ctype, ctypes.c_void_p)
+            if n:
+                assert t._type_ is want and t._length_ == n, (name, f)
+            else:
+                assert ctypes.sizeof(t) == ctypes.sizeof(want), (name, f)
+
+
 def test_host_only_calls(lib_path):
     import paper_1802_00438_gb300 as st
-    assert st.lib.stencil_abi_version() == 3
+    assert st.lib.stencil_abi_version() == 4
     assert st.strerror(0) == "ok"
     assert "dimensions" in st.strerror(st.ST_ERR_DIMS_MISMATCH)
     assert st.strerror(12345) == "unknown status"

@@ -23,7 +23,7 @@ def run(st, w, steps, storage, T=0, vec=0, by=0):
     u = torch.from_numpy(w.u0).cuda()
     p = None if w.power is None else torch.from_numpy(w.power).cuda()
     out = torch.full_like(u, float("nan"))
-    plan = st.Plan(w.kind, 2, w.nx, w.ny, storage=storage, force_T=T, force_vec=vec, force_by=by)
+    plan = st.Plan(w.kind, 2, w.nx, w.ny, storage=storage, force_T=T, force_vec=vec, partial_rows=by)
     plan.run(u, out, w.coef, steps, power=p)
     plan.sync()
     plan.close()

@@ -31,13 +31,13 @@ def max_rel(g, o):
     return float(np.max(np.abs(g - o) / np.maximum(np.abs(o), floor)))
 
 
-def gpu_run(st, w, steps, exact=False, T=0, bx=0, inplace=False, vec=0, by=0):
+def gpu_run(st, w, steps, exact=False, T=0, bx=0, inplace=False, vec=0, by=0, rows=0, resident=0):
     import torch
     u = torch.from_numpy(np.ascontiguousarray(w.u0)).cuda()
     p = None if w.power is None else torch.from_numpy(np.ascontiguousarray(w.power)).cuda()
     out = u if inplace else torch.full_like(u, float("nan"))
     plan = st.Plan(w.kind, w.ndim, w.nx, w.ny, w.nz, exact=exact, force_T=T, force_bx=bx,
-                   force_vec=vec, force_by=by)
+                   force_vec=vec, force_by=by, partial_rows=rows, resident=resident)
     plan.run(u, out, w.coef, steps, power=p)
     plan.sync()
     info = plan.info()
@@ -92,13 +92,13 @@ def test_contracted_2d_in_place_rows(eng, orc, kind):
     for t, (nx, ny) in enumerate(SIZES_2D + [(700, 300), (1500, 97)]):
         w = synth.make(kind, 2, nx, ny, seed=3500 + 43 * t + kind)
         for steps in (1, 7, 9, 27):
-            g, info = gpu_run(eng, w, steps, T=8, vec=8, by=1)
+            g, info = gpu_run(eng, w, steps, T=8, vec=8, rows=1)
             assert info["T"] == 8 and info["warps"] == 1
             o = orc.run(kind, w.u0, w.coef, steps, w.power)
             assert max_rel(g, o) <= TOL, (nx, ny, steps, max_rel(g, o))
         if nx * ny > 1000:
             for steps in (16, 25):
-                g, _ = gpu_run(eng, w, steps, T=8, vec=8, by=1, inplace=True)
+                g, _ = gpu_run(eng, w, steps, T=8, vec=8, rows=1, inplace=True)
                 o = orc.run(kind, w.u0, w.coef, steps, w.power)
                 assert max_rel(g, o) <= TOL, (nx, ny, steps, "in place")
 
