@@ -178,9 +178,11 @@ def reference_rank_gate() -> bool:
     return int(os.environ.get("RANK", "0")) == 0
 
 
-def kernel_source_hash(ndim: int) -> str:
-    """Hash of the sources of the benchmarked kernel family (2D contracted or 3D)."""
-    files = (("tb2f_kernel.cuh", "tb2d_kernel.cuh", "common.cuh") if ndim == 2
+def kernel_source_hash(ndim: int, resident: bool = False) -> str:
+    """Hash of the sources of the benchmarked kernel family (2D streaming, 2D resident tiles
+    or 3D)."""
+    files = (("res2d.cu", "common.cuh") if resident else
+             ("tb2f_kernel.cuh", "tb2d_kernel.cuh", "common.cuh") if ndim == 2
              else ("tb3f_kernel.cuh", "tb3d_kernel.cuh", "common.cuh"))
     h = hashlib.sha1()
     for f in files:
@@ -188,7 +190,7 @@ def kernel_source_hash(ndim: int) -> str:
     return h.hexdigest()[:12]
 
 
-def profiled_traffic(workload: str, ndim: int):
+def profiled_traffic(workload: str, ndim: int, resident: bool = False):
     """DRAM bytes per launch recorded from an ncu capture of the current kernel source
     (profiles/traffic.txt); None when the kernel changed since it was captured."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
@@ -197,7 +199,7 @@ def profiled_traffic(workload: str, ndim: int):
     for line in open(p):
         f = line.split()
         if len(f) >= 3 and not line.startswith("#") and f[0] == workload:
-            return float(f[2]) if f[1] == kernel_source_hash(ndim) else None
+            return float(f[2]) if f[1] == kernel_source_hash(ndim, resident) else None
     return None
 
 
@@ -445,9 +447,10 @@ def plan_record(g: Gpu, w, args, steps: int, warmup: int, with_cpu: bool, one_th
             st.stencil_run(plan.h, d_u, d_o, d_p, coef, w.nx, w.ny, w.nz, w.steps)
             h_o.copy_(d_o, non_blocking=True)
 
-        ems, _, _ = g.timed(e2e_step, steps, 1)
+        e2e_steps = min(steps, 100)   # each call copies the grids both ways: fewer calls
+        ems, _, _ = g.timed(e2e_step, e2e_steps, 1)
         nb = w.u0.nbytes
-        e2e = {"value": rk.job_rate(cells_step * steps, ems) / 1e9, "unit": "GCell/s",
+        e2e = {"value": rk.job_rate(cells_step * e2e_steps, ems) / 1e9, "unit": "GCell/s",
                "h2d_bytes_per_step": nb + (0 if h_pin is None else h_pin.nbytes),
                "d2h_bytes_per_step": nb}
         del h_u, h_p, h_o, d_u, d_p, d_o
@@ -469,7 +472,7 @@ def plan_record(g: Gpu, w, args, steps: int, warmup: int, with_cpu: bool, one_th
     alu_bound = alu_peak * 1e12 / fl <= hbm_peak * 1e9 * T_hbm / by
     resized = bool(args.nx or args.ny or args.nz or args.time_steps)
     traffic = None if (resized or args.T or args.bx or args.vec or args.by) else \
-        profiled_traffic(key, w.ndim)
+        profiled_traffic(key, w.ndim, resident)
     if alu_bound:
         roof = {"bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": tflops / alu_peak,
@@ -721,6 +724,8 @@ def adjoint_record(g: Gpu, args, steps: int, warmup: int, with_cpu: bool, ckpt=2
 # in place) and 3D (T, tile width, tile height, cells per thread), every one the library compiles
 STUDY_2D = [(1, 8, 0), (2, 8, 0), (4, 8, 0), (6, 8, 0), (8, 8, 0), (8, 8, 1),
             (1, 4, 0), (2, 4, 0), (4, 4, 0), (8, 4, 0), (12, 4, 0), (12, 4, 1)]
+# resident tiles (small 2D grids): (T, cells per lane)
+STUDY_RES = [(T, v) for v in (2, 4) for T in (2, 4, 8, 12, 16)]
 STUDY_3D = [(1, 64, 64, 8), (2, 64, 64, 8), (3, 64, 64, 8), (4, 64, 64, 8),
             (2, 64, 64, 4), (3, 64, 64, 4), (4, 64, 64, 4),
             (2, 128, 32, 8), (3, 128, 32, 8), (4, 128, 32, 8),
@@ -740,8 +745,12 @@ def model_study(g: Gpu, args):
         pw = None if w.power is None else torch.from_numpy(w.power).to(g.dev)
         out = torch.empty_like(u0)
         confs = STUDY_2D if w.ndim == 2 else STUDY_3D
+        if name == "diffusion2d_1024":
+            confs = confs + [("resident",) + c for c in STUDY_RES]
         for cf in confs:
-            if w.ndim == 2:
+            if cf[0] == "resident":
+                kw = dict(force_T=cf[1], force_vec=cf[2], resident=1)
+            elif w.ndim == 2:
                 T, vec, inplace = cf
                 kw = dict(force_T=T, force_vec=vec, partial_rows=1 if inplace else 2)
             else:
@@ -911,8 +920,10 @@ def main():
                     r = adjoint_record(g, args, k, 3, with_cpu)
                 else:
                     cw = WORKLOADS[cname]()
-                    # the 1024^2 grid runs in well under a millisecond: more calls per sample
-                    kk = 10 * k if cw.cells * cw.steps < 1e9 else k
+                    # the 1024^2 grid runs in well under a millisecond: enough calls that the
+                    # timed region lasts about half a second, so that nvidia-smi (200 ms
+                    # period) samples its clocks
+                    kk = 4000 if cw.cells * cw.steps < 1e9 else k
                     r = plan_record(g, cw, args, kk, 3, with_cpu,
                                     one_thread=(cname == "diffusion2d_1024"), key=cname)
                     r["_plan"].close()

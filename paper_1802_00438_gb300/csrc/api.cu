@@ -26,8 +26,63 @@ struct PassCfg2D {
     int ntx = 0;
     long long total = 0, rows_per_cta = 0;
     int ctas = 0;
+    long long *starts = nullptr;   // device: cost-balanced ranges (contracted kernel), or none
     bool ready = false;
 };
+
+// Ranges of (tile column, row) pairs, one per block, balanced by cost rather than by rows: a
+// segment streams 2T rows of pipeline fill besides its own (Sec. 3.2), so a block whose range
+// crosses a tile column pays the fill twice, and the slowest block sets the pass time.  Greedy
+// cut at the mean cost (rows + fill per segment).  Returns the ranges' largest cost and fills
+// starts (ctas + 1 entries).
+long long balanced_ranges(long long ntx, long long ny, int ctas, int fill, std::vector<long long> &st)
+{
+    const long long total = ntx * ny;
+    const double target = (double)(total + (long long)fill * (ctas + ntx - 1)) / ctas;
+    st.assign(ctas + 1, total);
+    long long u = 0, worst = 0;
+    for (int b = 0; b < ctas; b++) {
+        st[b] = u;
+        double cost = 0.0;
+        while (u < total) {
+            const long long col_end = (u / ny + 1) * ny;
+            const double room = target - cost - fill;
+            if (room < 1.0 && cost > 0.0) break;
+            const long long take = std::min<long long>(col_end - u, std::max<long long>(1, (long long)std::ceil(room)));
+            cost += fill + (double)take;
+            u += take;
+            if (cost >= target) break;
+        }
+    }
+    for (int b = 0; b < ctas; b++) {   // the last block also takes whatever is left
+        long long c = 0;
+        for (long long x = st[b]; x < st[b + 1];) {
+            const long long e = std::min(st[b + 1], (x / ny + 1) * ny);
+            c += fill + (e - x);
+            x = e;
+        }
+        worst = std::max(worst, c);
+    }
+    return worst;
+}
+
+// the largest cost of the equal-row ranges
+long long even_ranges_cost(long long ntx, long long ny, long long per, int fill)
+{
+    const long long total = ntx * ny;
+    long long worst = 0;
+    for (long long a = 0; a < total; a += per) {
+        const long long e = std::min(total, a + per);
+        long long c = 0;
+        for (long long x = a; x < e;) {
+            const long long f = std::min(e, (x / ny + 1) * ny);
+            c += fill + (f - x);
+            x = f;
+        }
+        worst = std::max(worst, c);
+    }
+    return worst;
+}
 
 struct PassCfg3D {
     Shape3D shape;
@@ -190,6 +245,35 @@ double model_gcells_2d(const stencil_desc &d, int sms, const Cand2D &k, int bps,
 // tiles read their halos again (the tile fit's read factor, ntx*bx*nty*by / (nx*ny)), at 62 %
 // of the measured copy bandwidth.  Calibrated on the 50-point sweep of bench.py --model-study
 // (measured / predicted per configuration).
+// 3D segments (tb3f): the z-slab length Z of round-robin (tile column, z-slab) pieces, or 0 for
+// contiguous (tile column, plane) ranges.  Pieces are taken when their rounds cost at most 6 %
+// more plane-times per block (planes plus T of pipeline fill per segment) than the ranges;
+// *cost receives the chosen mode's plane-times per block.
+int zslab_pick(long long cols, int nz, long long slots, int T, double *cost)
+{
+    const long long total = cols * nz;
+    const long long ctas = std::min(slots, std::max<long long>(1, total / std::max(16, 8 * T)));
+    const double range_cost = (double)((total + ctas - 1) / ctas) + T;
+    double best = 0.0;
+    int best_z = 0;
+    for (int S = 1; S <= std::max(1, nz / (2 * T)); S++) {
+        const int Z = (nz + S - 1) / S;
+        const long long pieces = cols * ((nz + Z - 1) / Z);
+        const long long G = std::min(slots, pieces);
+        const double c = (double)((pieces + G - 1) / G) * (Z + T);
+        if (!best_z || c < best) {
+            best = c;
+            best_z = Z;
+        }
+    }
+    if (best_z > 0 && best <= 1.06 * range_cost) {
+        if (cost) *cost = best;
+        return best_z;
+    }
+    if (cost) *cost = range_cost;
+    return 0;
+}
+
 double model_gcells_3d(const stencil_desc &d, int sms, int T, int VX, int VY, int NW)
 {
     stencil_gpu_model_in m = {};
@@ -208,7 +292,13 @@ double model_gcells_3d(const stencil_desc &d, int sms, int T, int VX, int VY, in
     m.hbm_gbs = 6800.0;
     const double cx = m.bx - 2.0 * m.halo_x, cy = m.by - 2.0 * m.halo_y;
     if (cx < 1 || cy < 1) return 0.0;
-    const double rf = std::ceil(d.nx / cx) * m.bx * std::ceil(d.ny / cy) * m.by / ((double)d.nx * d.ny);
+    const long long cols = (long long)std::ceil(d.nx / cx) * (long long)std::ceil(d.ny / cy);
+    double rf = std::ceil(d.nx / cx) * m.bx * std::ceil(d.ny / cy) * m.by / ((double)d.nx * d.ny);
+    // the segments prepare3 will take: z-slab pieces read their halos again from L2, not DRAM
+    const long long slots = (long long)sms * (NW <= 8 ? 2 : 1);
+    double seg_cost = 0.0;
+    const bool pieces = zslab_pick(cols, d.nz, slots, T, &seg_cost) > 0;
+    if (pieces) rf = 1.0;
     const double alg = d.kind == ST_DIFFUSION ? 8.0 : 12.0;
     const double read = alg - 4.0;   // field (and power) in; the field out is written once
     m.bytes_per_cell = alg;
@@ -216,7 +306,8 @@ double model_gcells_3d(const stencil_desc &d, int sms, int T, int VX, int VY, in
     // stage 0 (three ring planes, their exchange) costs more than the partial-sum stages
     m.ops_per_cell = (d.kind == ST_DIFFUSION ? 17.3 : 19.7) * (0.85 + 0.6 / T);
     m.issue_eff = 0.61 * (NW <= 8 ? 1.10 : NW >= 32 ? 0.80 : 1.0);
-    m.stream_overhead = 0.04;
+    // plane-times per block beyond an even share of the planes (fill, round quantisation)
+    m.stream_overhead = pieces ? std::max(0.0, seg_cost * slots / ((double)cols * d.nz) - 1.0) : 0.04;
     m.launch_s = 4e-6;
     stencil_gpu_model_out r;
     if (stencil_model_gpu(&m, &r) != ST_OK) return 0.0;
@@ -382,6 +473,23 @@ int prepare2(stencil_plan_s *p, int Tk, PassCfg2D **out)
                                              std::max<long long>(1, c.total / min_rows));
         c.rows_per_cta = (c.total + ctas - 1) / ctas;
         c.ctas = (int)((c.total + c.rows_per_cta - 1) / c.rows_per_cta);
+        if (!c.shape.exact && c.shape.kind != ST_DIFFUSION_VAR) {
+            // contracted kernel: cost-balanced ranges where they shorten the longest block
+            std::vector<long long> st;
+            const int fill = 2 * Tk;
+            if (balanced_ranges(c.ntx, p->d.ny, (int)ctas, fill, st) <
+                even_ranges_cost(c.ntx, p->d.ny, c.rows_per_cta, fill)) {
+                e = cudaMalloc(&c.starts, st.size() * sizeof(long long));
+                if (e == cudaSuccess)
+                    e = cudaMemcpy(c.starts, st.data(), st.size() * sizeof(long long), cudaMemcpyHostToDevice);
+                if (e != cudaSuccess) {
+                    if (c.starts) cudaFree(c.starts);
+                    c.starts = nullptr;
+                    return map_cuda(e);
+                }
+                c.ctas = (int)ctas;
+            }
+        }
         c.ready = true;
     }
     *out = &c;
@@ -439,30 +547,16 @@ int prepare3(stencil_plan_s *p, int Tk, PassCfg3D **out)
         c.planes_per_cta = (total + ctas - 1) / ctas;
         c.ctas = (int)((total + c.planes_per_cta - 1) / c.planes_per_cta);
         if (p->alg3) {
-            // or pieces (tile column, z-slab) dealt round-robin: the blocks of a round stream
-            // neighbouring tile columns through the same planes together, so the halo cells
-            // a tile reads again come from L2 (with contiguous ranges the neighbours run far
-            // apart in z and every tile reads its halos from device memory: measured on
-            // 512^2 x 256 diffusion, T = 3, DRAM bytes per pass 751 MB with ranges, 504 MB
-            // with 52-plane pieces, 537 MB algorithmic).  Taken when the rounds cost at most
-            // 6 % more plane-times per block (planes plus T of pipeline fill per segment) than
-            // the contiguous ranges (512^3 diffusion: 103-plane pieces, 945 GCell/s against
-            // 919 with ranges).
+            // or pieces (tile column, z-slab) dealt round-robin (zslab_pick): the blocks of a
+            // round stream neighbouring tile columns through the same planes together, so the
+            // halo cells a tile reads again come from L2 (with contiguous ranges the neighbours
+            // run far apart in z and every tile reads its halos from device memory: measured
+            // on 512^2 x 256 diffusion, T = 3, DRAM bytes per pass 751 MB with ranges, 504 MB
+            // with 52-plane pieces, 537 MB algorithmic; 512^3 diffusion: 103-plane pieces,
+            // 945 GCell/s against 919 with ranges).
             const long long slots = (long long)p->sms * bps;
-            const double range_cost = (double)c.planes_per_cta + Tk;
-            double best = 0.0;
-            int best_z = 0;
-            for (int S = 1; S <= std::max(1, p->d.nz / (2 * Tk)); S++) {
-                const int Z = (p->d.nz + S - 1) / S;
-                const long long pieces = c.cols * ((p->d.nz + Z - 1) / Z);
-                const long long G = std::min(slots, pieces);
-                const double cost = (double)((pieces + G - 1) / G) * (Z + Tk);
-                if (!best_z || cost < best) {
-                    best = cost;
-                    best_z = Z;
-                }
-            }
-            if (best_z > 0 && best <= 1.06 * range_cost) {
+            const int best_z = zslab_pick(c.cols, p->d.nz, slots, Tk, nullptr);
+            if (best_z > 0) {
                 c.zslab = best_z;
                 c.pieces = c.cols * ((p->d.nz + best_z - 1) / best_z);
                 c.ctas = (int)std::min(slots, c.pieces);
@@ -566,6 +660,7 @@ int run_pass2(stencil_plan_s *p, const float *src, long long lds, float *dst, lo
     a.ntx = c->ntx;
     a.total_rows = c->total;
     a.rows_per_cta = c->rows_per_cta;
+    a.starts = c->starts;
     a.ctas = c->ctas;
     for (int i = 0; i < 5; i++) a.k[i] = a.kf[i] = k[i];
     a.kf[5] = k[0] * k[2];    // Hotspot: sdc * Ry, rounded once (float32)
@@ -674,6 +769,7 @@ int run_pass2q(stencil_plan_s *p, int src, int dst, const float *k, int tsteps)
     a.ntx = c->ntx;
     a.total_rows = c->total;
     a.rows_per_cta = c->rows_per_cta;
+    a.starts = c->starts;
     a.ctas = c->ctas;
     for (int i = 0; i < 5; i++) a.k[i] = a.kf[i] = k[i];
     a.kf[5] = k[0] * k[2];
@@ -1456,6 +1552,8 @@ int stencil_plan_destroy(stencil_plan p)
     if (p->src) cudaFree(p->src);
     if (p->res_xg) cudaFree(p->res_xg);
     if (p->res_flags) cudaFree(p->res_flags);
+    for (PassCfg2D &c : p->cfg2)
+        if (c.starts) cudaFree(c.starts);
     delete p;
     return ST_OK;
 }

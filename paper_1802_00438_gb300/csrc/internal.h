@@ -19,6 +19,8 @@ struct Pass2D {
     int ntx;               // tiles along x
     long long total_rows;  // ntx * ny: the (tile column, row) pairs of the pass
     long long rows_per_cta;
+    const long long *starts;   // contracted kernel: block b takes pairs [starts[b], starts[b+1])
+                               // (nullptr: rows_per_cta pairs each)
     int ctas;
     float k[5];
     // contracted kernel's coefficients, derived on the host from k: diffusion cc, cw, ce, cs, cn;

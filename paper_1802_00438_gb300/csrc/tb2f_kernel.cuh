@@ -778,8 +778,15 @@ __global__ void __launch_bounds__(32) k_tb2f(const Pass2D p)
     for (int s = 0; s < C::NS; s++)
 #pragma unroll
         for (int j = 0; j < V; j++) A[s][j] = B[s][j] = 0.f;
-    const long long f = (long long)blockIdx.x * p.rows_per_cta;
-    tbf_range<KIND, T, V, SWAP, STOR>(p, f, min(f + p.rows_per_cta, p.total_rows), A, B, smem);
+    long long f, fend;
+    if (p.starts) {
+        f = __ldg(p.starts + blockIdx.x);
+        fend = __ldg(p.starts + blockIdx.x + 1);
+    } else {
+        f = (long long)blockIdx.x * p.rows_per_cta;
+        fend = min(f + p.rows_per_cta, p.total_rows);
+    }
+    tbf_range<KIND, T, V, SWAP, STOR>(p, f, fend, A, B, smem);
 }
 
 }  // namespace stn
