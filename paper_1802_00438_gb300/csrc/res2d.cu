@@ -268,11 +268,13 @@ __global__ void __launch_bounds__(res_max_threads(KIND, VX, EXACT)) k_res2d(cons
     const int E = (p.steps + p.T - 1) / p.T;
     for (int e = 0; e < E; e++) {
         const int ts = (e == E - 1) ? p.steps - p.T * (E - 1) : p.T;
+        // unrolled so that the rows updated in place need no register moves at the loop edge
+        // (measured: 4 steps per iteration +7-9 % over 1)
         if (xe) {
-#pragma unroll 1
+#pragma unroll 4
             for (int t = 0; t < ts; t++) rstep<KIND, VX, VY, EXACT, true>(u, q, k, xs, par, nw, w, lane, g);
         } else {
-#pragma unroll 1
+#pragma unroll 4
             for (int t = 0; t < ts; t++) rstep<KIND, VX, VY, EXACT, false>(u, q, k, xs, par, nw, w, lane, g);
         }
         if (e == E - 1) break;
@@ -284,12 +286,18 @@ __global__ void __launch_bounds__(res_max_threads(KIND, VX, EXACT)) k_res2d(cons
         int ox = gx0, oy = gy0;
         unsigned pb = pub, rl = rld;
         asm volatile("" : "+r"(ox), "+r"(oy), "+r"(pb), "+r"(rl));
+        constexpr unsigned ALL = (1u << VX) - 1u;
 #pragma unroll
         for (int r = 0; r < VY; r++) {
             float *row = X + (long long)(oy + r) * p.ld_x + ox;
+            const unsigned bits = (pb >> (r * VX)) & ALL;
+            if (bits == ALL) {   // the lane's cells of this row whole: one aligned vector store
+                st_row<VX>(row, u[r]);
+            } else if (bits) {
 #pragma unroll
-            for (int j = 0; j < VX; j++)
-                if ((pb >> (r * VX + j)) & 1u) row[j] = u[r][j];
+                for (int j = 0; j < VX; j++)
+                    if ((bits >> j) & 1u) row[j] = u[r][j];
+            }
         }
         // the block's stores, then one release store of its counter (cumulative over the
         // stores the barrier ordered before it); counters only grow, across runs too
@@ -321,12 +329,25 @@ __global__ void __launch_bounds__(res_max_threads(KIND, VX, EXACT)) k_res2d(cons
         if (__syncthreads_or(failed)) return;   // block-uniform; no copy in flight
         // reload the halos (clamped: ghost cells take the edge cells' new values), from L2
         asm volatile("" : "+r"(ox), "+r"(oy), "+r"(rl));
+        const bool xin = ox >= 0 && ox + VX <= p.nx;   // my columns need no clamp
 #pragma unroll
         for (int r = 0; r < VY; r++) {
-            const float *row = X + (long long)min(max(oy + r, 0), p.ny - 1) * p.ld_x;
+            const int y = oy + r;
+            const float *row = X + (long long)min(max(y, 0), p.ny - 1) * p.ld_x;
+            const unsigned bits = (rl >> (r * VX)) & ALL;
+            if (bits == ALL && xin && y >= 0 && y < p.ny) {   // one aligned vector load
+                if (VX == 4) {
+                    const float4 v = __ldcg(reinterpret_cast<const float4 *>(row + ox));
+                    u[r][0] = v.x; u[r][1] = v.y; u[r][VX > 2 ? 2 : 0] = v.z; u[r][VX > 3 ? 3 : 0] = v.w;
+                } else {
+                    const float2 v = __ldcg(reinterpret_cast<const float2 *>(row + ox));
+                    u[r][0] = v.x; u[r][1] = v.y;
+                }
+            } else if (bits) {
 #pragma unroll
-            for (int j = 0; j < VX; j++)
-                if ((rl >> (r * VX + j)) & 1u) u[r][j] = __ldcg(row + min(max(ox + j, 0), p.nx - 1));
+                for (int j = 0; j < VX; j++)
+                    if ((bits >> j) & 1u) u[r][j] = __ldcg(row + min(max(ox + j, 0), p.nx - 1));
+            }
         }
     }
 #pragma unroll
