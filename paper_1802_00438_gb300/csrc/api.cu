@@ -32,33 +32,39 @@ struct PassCfg2D {
 
 // Ranges of (tile column, row) pairs, one per block, balanced by cost rather than by rows: a
 // segment streams 2T rows of pipeline fill besides its own (Sec. 3.2), so a block whose range
-// crosses a tile column pays the fill twice, and the slowest block sets the pass time.  Greedy
-// cut at the mean cost (rows + fill per segment).  Returns the ranges' largest cost and fills
-// starts (ctas + 1 entries).
-long long balanced_ranges(long long ntx, long long ny, int ctas, int fill, std::vector<long long> &st)
+// crosses a tile column pays the fill twice, and the slowest block sets the pass time; rows of
+// the two edge tile columns cost edge_w (their warps apply the clamps).  Greedy cut at the mean
+// cost.  Returns the ranges' largest cost and fills starts (ctas + 1 entries).
+double balanced_ranges(long long ntx, long long ny, int ctas, int fill, double edge_w,
+                       std::vector<long long> &st)
 {
     const long long total = ntx * ny;
-    const double target = (double)(total + (long long)fill * (ctas + ntx - 1)) / ctas;
+    auto w_of = [&](long long col) { return (col == 0 || col == ntx - 1) ? edge_w : 1.0; };
+    double weighted = 0.0;
+    for (long long c = 0; c < ntx; c++) weighted += w_of(c) * ny;
+    const double target = (weighted + (double)fill * (ctas + ntx - 1)) / ctas;
     st.assign(ctas + 1, total);
-    long long u = 0, worst = 0;
+    long long u = 0;
     for (int b = 0; b < ctas; b++) {
         st[b] = u;
         double cost = 0.0;
         while (u < total) {
-            const long long col_end = (u / ny + 1) * ny;
+            const long long col = u / ny, col_end = (col + 1) * ny;
+            const double w = w_of(col);
             const double room = target - cost - fill;
-            if (room < 1.0 && cost > 0.0) break;
-            const long long take = std::min<long long>(col_end - u, std::max<long long>(1, (long long)std::ceil(room)));
-            cost += fill + (double)take;
+            if (room < w && cost > 0.0) break;
+            const long long take = std::min<long long>(col_end - u, std::max<long long>(1, (long long)std::ceil(room / w)));
+            cost += fill + w * (double)take;
             u += take;
             if (cost >= target) break;
         }
     }
+    double worst = 0.0;
     for (int b = 0; b < ctas; b++) {   // the last block also takes whatever is left
-        long long c = 0;
+        double c = 0.0;
         for (long long x = st[b]; x < st[b + 1];) {
             const long long e = std::min(st[b + 1], (x / ny + 1) * ny);
-            c += fill + (e - x);
+            c += fill + w_of(x / ny) * (double)(e - x);
             x = e;
         }
         worst = std::max(worst, c);
@@ -66,17 +72,18 @@ long long balanced_ranges(long long ntx, long long ny, int ctas, int fill, std::
     return worst;
 }
 
-// the largest cost of the equal-row ranges
-long long even_ranges_cost(long long ntx, long long ny, long long per, int fill)
+// the largest cost of the equal-row ranges (same costs)
+double even_ranges_cost(long long ntx, long long ny, long long per, int fill, double edge_w)
 {
     const long long total = ntx * ny;
-    long long worst = 0;
+    double worst = 0.0;
     for (long long a = 0; a < total; a += per) {
         const long long e = std::min(total, a + per);
-        long long c = 0;
+        double c = 0.0;
         for (long long x = a; x < e;) {
             const long long f = std::min(e, (x / ny + 1) * ny);
-            c += fill + (f - x);
+            const long long col = x / ny;
+            c += fill + ((col == 0 || col == ntx - 1) ? edge_w : 1.0) * (double)(f - x);
             x = f;
         }
         worst = std::max(worst, c);
@@ -477,8 +484,12 @@ int prepare2(stencil_plan_s *p, int Tk, PassCfg2D **out)
             // contracted kernel: cost-balanced ranges where they shorten the longest block
             std::vector<long long> st;
             const int fill = 2 * Tk;
-            if (balanced_ranges(c.ntx, p->d.ny, (int)ctas, fill, st) <
-                even_ranges_cost(c.ntx, p->d.ny, c.rows_per_cta, fill)) {
+            // a row of an edge tile column costs 1.25: its warps run the clamp selects
+            // (measured on GB300 with the edge weight swept 1.0-1.4: 16384^2 Hotspot 2684 ->
+            // 2948 GCell/s, diffusion 3337 -> 3753, flat between 1.2 and 1.4)
+            const double edge_w = 1.25;
+            if (balanced_ranges(c.ntx, p->d.ny, (int)ctas, fill, edge_w, st) <
+                even_ranges_cost(c.ntx, p->d.ny, c.rows_per_cta, fill, edge_w)) {
                 e = cudaMalloc(&c.starts, st.size() * sizeof(long long));
                 if (e == cudaSuccess)
                     e = cudaMemcpy(c.starts, st.data(), st.size() * sizeof(long long), cudaMemcpyHostToDevice);
