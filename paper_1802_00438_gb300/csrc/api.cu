@@ -30,31 +30,30 @@ struct PassCfg2D {
     bool ready = false;
 };
 
-// Ranges of (tile column, row) pairs, one per block, balanced by cost rather than by rows: a
-// segment streams 2T rows of pipeline fill besides its own (Sec. 3.2), so a block whose range
-// crosses a tile column pays the fill twice, and the slowest block sets the pass time; rows of
-// the two edge tile columns cost edge_w (their warps apply the clamps).  Greedy cut at the mean
-// cost.  Returns the ranges' largest cost and fills starts (ctas + 1 entries).
-double balanced_ranges(long long ntx, long long ny, int ctas, int fill, double edge_w,
+// Ranges of (tile column, row or plane) units, one per block, balanced by cost rather than by
+// count: a segment streams 2T rows (planes) of pipeline fill besides its own (Sec. 3.2), so a
+// block whose range crosses a tile column pays the fill twice, and a unit of an edge tile column
+// costs more (its warps run the clamp selects): w[col] per unit.  The slowest block sets the
+// pass time.  Greedy cut at the mean cost.  Returns the ranges' largest cost and fills starts
+// (ctas + 1 entries).
+double balanced_ranges(long long len, int ctas, int fill, const std::vector<double> &w,
                        std::vector<long long> &st)
 {
-    const long long total = ntx * ny;
-    auto w_of = [&](long long col) { return (col == 0 || col == ntx - 1) ? edge_w : 1.0; };
+    const long long ncol = (long long)w.size(), total = ncol * len;
     double weighted = 0.0;
-    for (long long c = 0; c < ntx; c++) weighted += w_of(c) * ny;
-    const double target = (weighted + (double)fill * (ctas + ntx - 1)) / ctas;
+    for (double x : w) weighted += x * len;
+    const double target = (weighted + (double)fill * (ctas + ncol - 1)) / ctas;
     st.assign(ctas + 1, total);
     long long u = 0;
     for (int b = 0; b < ctas; b++) {
         st[b] = u;
         double cost = 0.0;
         while (u < total) {
-            const long long col = u / ny, col_end = (col + 1) * ny;
-            const double w = w_of(col);
+            const long long col = u / len, col_end = (col + 1) * len;
             const double room = target - cost - fill;
-            if (room < w && cost > 0.0) break;
-            const long long take = std::min<long long>(col_end - u, std::max<long long>(1, (long long)std::ceil(room / w)));
-            cost += fill + w * (double)take;
+            if (room < w[col] && cost > 0.0) break;
+            const long long take = std::min<long long>(col_end - u, std::max<long long>(1, (long long)std::ceil(room / w[col])));
+            cost += fill + w[col] * (double)take;
             u += take;
             if (cost >= target) break;
         }
@@ -63,8 +62,8 @@ double balanced_ranges(long long ntx, long long ny, int ctas, int fill, double e
     for (int b = 0; b < ctas; b++) {   // the last block also takes whatever is left
         double c = 0.0;
         for (long long x = st[b]; x < st[b + 1];) {
-            const long long e = std::min(st[b + 1], (x / ny + 1) * ny);
-            c += fill + w_of(x / ny) * (double)(e - x);
+            const long long e = std::min(st[b + 1], (x / len + 1) * len);
+            c += fill + w[x / len] * (double)(e - x);
             x = e;
         }
         worst = std::max(worst, c);
@@ -72,18 +71,17 @@ double balanced_ranges(long long ntx, long long ny, int ctas, int fill, double e
     return worst;
 }
 
-// the largest cost of the equal-row ranges (same costs)
-double even_ranges_cost(long long ntx, long long ny, long long per, int fill, double edge_w)
+// the largest cost of ranges of `per` units each (same costs)
+double even_ranges_cost(long long len, long long per, int fill, const std::vector<double> &w)
 {
-    const long long total = ntx * ny;
+    const long long total = (long long)w.size() * len;
     double worst = 0.0;
     for (long long a = 0; a < total; a += per) {
         const long long e = std::min(total, a + per);
         double c = 0.0;
         for (long long x = a; x < e;) {
-            const long long f = std::min(e, (x / ny + 1) * ny);
-            const long long col = x / ny;
-            c += fill + ((col == 0 || col == ntx - 1) ? edge_w : 1.0) * (double)(f - x);
+            const long long f = std::min(e, (x / len + 1) * len);
+            c += fill + w[x / len] * (double)(f - x);
             x = f;
         }
         worst = std::max(worst, c);
@@ -98,6 +96,7 @@ struct PassCfg3D {
     int ctas = 0;
     int zslab = 0;          // > 0: round-robin pieces of zslab planes (partial-sum kernel)
     long long pieces = 0;
+    long long *starts = nullptr;   // device: cost-balanced ranges (zslab = 0), or none
     bool ready = false;
 };
 
@@ -253,9 +252,13 @@ double model_gcells_2d(const stencil_desc &d, int sms, const Cand2D &k, int bps,
 // of the measured copy bandwidth.  Calibrated on the 50-point sweep of bench.py --model-study
 // (measured / predicted per configuration).
 // 3D segments (tb3f): the z-slab length Z of round-robin (tile column, z-slab) pieces, or 0 for
-// contiguous (tile column, plane) ranges.  Pieces are taken when their rounds cost at most 6 %
-// more plane-times per block (planes plus T of pipeline fill per segment) than the ranges;
-// *cost receives the chosen mode's plane-times per block.
+// contiguous (tile column, plane) ranges.  Pieces read the tiles' halo planes from L2 and cut
+// the pass's DRAM traffic to about the algorithmic bytes (ranges: 1.4-1.6x), which pays only
+// where the pass is memory-bound: measured on GB300, T = 1 (512^3 diffusion: 578 GCell/s with
+// pieces, 431 with ranges); from T = 2 on the kernel is issue-bound and the cost-balanced
+// ranges are faster (T = 3: 963 against 935).  So pieces for T = 1, when their rounds cost at
+// most 6 % more plane-times per block (planes plus T of pipeline fill per segment) than the
+// ranges; *cost receives the chosen mode's plane-times per block.
 int zslab_pick(long long cols, int nz, long long slots, int T, double *cost)
 {
     const long long total = cols * nz;
@@ -273,7 +276,7 @@ int zslab_pick(long long cols, int nz, long long slots, int T, double *cost)
             best_z = Z;
         }
     }
-    if (best_z > 0 && best <= 1.06 * range_cost) {
+    if (T == 1 && best_z > 0 && best <= 1.06 * range_cost) {
         if (cost) *cost = best;
         return best_z;
     }
@@ -487,9 +490,10 @@ int prepare2(stencil_plan_s *p, int Tk, PassCfg2D **out)
             // a row of an edge tile column costs 1.25: its warps run the clamp selects
             // (measured on GB300 with the edge weight swept 1.0-1.4: 16384^2 Hotspot 2684 ->
             // 2948 GCell/s, diffusion 3337 -> 3753, flat between 1.2 and 1.4)
-            const double edge_w = 1.25;
-            if (balanced_ranges(c.ntx, p->d.ny, (int)ctas, fill, edge_w, st) <
-                even_ranges_cost(c.ntx, p->d.ny, c.rows_per_cta, fill, edge_w)) {
+            std::vector<double> w(c.ntx, 1.0);
+            w.front() = w.back() = 1.25;
+            if (balanced_ranges(p->d.ny, (int)ctas, fill, w, st) <
+                even_ranges_cost(p->d.ny, c.rows_per_cta, fill, w)) {
                 e = cudaMalloc(&c.starts, st.size() * sizeof(long long));
                 if (e == cudaSuccess)
                     e = cudaMemcpy(c.starts, st.data(), st.size() * sizeof(long long), cudaMemcpyHostToDevice);
@@ -563,14 +567,38 @@ int prepare3(stencil_plan_s *p, int Tk, PassCfg3D **out)
             // halo cells a tile reads again come from L2 (with contiguous ranges the neighbours
             // run far apart in z and every tile reads its halos from device memory: measured
             // on 512^2 x 256 diffusion, T = 3, DRAM bytes per pass 751 MB with ranges, 504 MB
-            // with 52-plane pieces, 537 MB algorithmic; 512^3 diffusion: 103-plane pieces,
-            // 945 GCell/s against 919 with ranges).
+            // with 52-plane pieces, 537 MB algorithmic).
             const long long slots = (long long)p->sms * bps;
             const int best_z = zslab_pick(c.cols, p->d.nz, slots, Tk, nullptr);
+            // a plane of a tile column at the x edge costs 1.1, at the y edge 1.05 (their
+            // warps run the clamp selects; measured on GB300, weights swept 1.0-1.5: 512^2 x
+            // 256 Hotspot 750 -> 804 GCell/s, 512^3 diffusion 931 -> 963)
+            const double wx = 1.1, wy = 1.05;
+            std::vector<double> w(c.cols, 1.0);
+            for (long long col = 0; col < c.cols; col++) {
+                const long long ty = col / c.ntx, tx = col - ty * c.ntx;
+                if (tx == 0 || tx == c.ntx - 1) w[col] *= wx;
+                if (ty == 0 || ty == c.nty - 1) w[col] *= wy;
+            }
             if (best_z > 0) {
                 c.zslab = best_z;
                 c.pieces = c.cols * ((p->d.nz + best_z - 1) / best_z);
                 c.ctas = (int)std::min(slots, c.pieces);
+            } else {
+                // contiguous ranges balanced by cost: edge tile columns weigh more
+                std::vector<long long> st;
+                if (balanced_ranges(p->d.nz, (int)ctas, Tk, w, st) <
+                    even_ranges_cost(p->d.nz, c.planes_per_cta, Tk, w)) {
+                    e = cudaMalloc(&c.starts, st.size() * sizeof(long long));
+                    if (e == cudaSuccess)
+                        e = cudaMemcpy(c.starts, st.data(), st.size() * sizeof(long long), cudaMemcpyHostToDevice);
+                    if (e != cudaSuccess) {
+                        if (c.starts) cudaFree(c.starts);
+                        c.starts = nullptr;
+                        return map_cuda(e);
+                    }
+                    c.ctas = (int)ctas;
+                }
             }
         }
         c.ready = true;
@@ -880,6 +908,7 @@ int run_pass3(stencil_plan_s *p, const float *src, float *dst, const float *pw, 
     a.ctas = c->ctas;
     a.zslab = c->zslab;
     a.pieces = c->pieces;
+    a.starts = c->starts;
     for (int i = 0; i < 9; i++) a.k[i] = i < ncoef(p->d) ? k[i] : 0.f;
     a.vec = ((uintptr_t)src % 16 == 0) && ((uintptr_t)dst % 16 == 0) && (p->d.nx % 4 == 0);
     a.vec_pw = pw && ((uintptr_t)pw % 16 == 0) && (p->d.nx % 4 == 0);
@@ -1564,6 +1593,8 @@ int stencil_plan_destroy(stencil_plan p)
     if (p->res_xg) cudaFree(p->res_xg);
     if (p->res_flags) cudaFree(p->res_flags);
     for (PassCfg2D &c : p->cfg2)
+        if (c.starts) cudaFree(c.starts);
+    for (PassCfg3D &c : p->cfg3)
         if (c.starts) cudaFree(c.starts);
     delete p;
     return ST_OK;

@@ -181,6 +181,8 @@ struct Pass3D {
     int ctas;
     int zslab;             // partial-sum kernel: > 0 = pieces of zslab planes, round-robin
     long long pieces;      // total_cols * ceil(nz / zslab)
+    const long long *starts;   // partial-sum kernel, zslab = 0: block b takes units
+                               // [starts[b], starts[b+1]) (nullptr: planes_per_cta each)
     float k[9];
     int vec;               // 1: rows start on 16-byte boundaries
     int vec_pw;            // 1: the power map's rows start on 16-byte boundaries

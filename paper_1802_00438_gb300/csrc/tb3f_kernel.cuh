@@ -568,10 +568,14 @@ __global__ void __launch_bounds__(32 * NW, (TB3F<KIND, T, VX, VY, NW>::MINB))
     // segments: zslab > 0 -- pieces (tile column, z-slab), taken round-robin, so that the
     // blocks of one round stream neighbouring tile columns through the same z-planes together
     // and the halo one of them re-reads is still in L2; else a contiguous range of
-    // (tile column, plane) units per block
+    // (tile column, plane) units per block, balanced by cost on the host
     long long f = (long long)blockIdx.x * p.planes_per_cta, pc = blockIdx.x;
     const long long total = p.total_cols * p.nz;
-    const long long fend = min(f + p.planes_per_cta, total);
+    long long fend = min(f + p.planes_per_cta, total);
+    if (p.starts) {   // cost-balanced ranges
+        f = __ldg(p.starts + blockIdx.x);
+        fend = __ldg(p.starts + blockIdx.x + 1);
+    }
     for (;;) {
         long long col;
         int z0, z1;
