@@ -58,15 +58,15 @@ __device__ bool q_wait(const int *flags, int row, int x0, int x1, int y0, int y1
             const int *f = flags + (long long)y * row + x;
             unsigned ns = 32;
             while (__shfl_sync(0xffffffffu, ld_relaxed(f) < need ? 1 : 0, 0)) {
-                int verdict = 0;   // 1: another block gave up, 2: our deadline passed
+                int outcome = 0;   // 1: another block gave up, 2: our deadline passed
                 if (lane == 0) {
-                    if (ld_relaxed(status) != 0) verdict = 1;
+                    if (ld_relaxed(status) != 0) outcome = 1;
                     else if (gtimer() > deadline) {
                         atomicCAS(status, 0, 1);
-                        verdict = 2;
+                        outcome = 2;
                     }
                 }
-                if (__shfl_sync(0xffffffffu, verdict, 0)) return false;
+                if (__shfl_sync(0xffffffffu, outcome, 0)) return false;
                 __nanosleep(ns);
                 ns = ns < 1024 ? 2 * ns : ns;
             }
