@@ -127,26 +127,14 @@ struct Edges {
     int k0, k1;  // rows of y = 0 and y = ny-1 among my VY rows (outside [0, VY): none)
 };
 
-// Contracted diffusion folds the x clamps into the weights of a lane's first and last cell:
-// at x = 0 the west neighbour is the cell itself, so cc*c + cw*c = (cc + cw)*c with the west
-// weight 0 (the shuffled-in value, finite, then adds exactly 0); likewise at x = nx-1 for the
-// east weight.  The x-edge blocks then run the same instructions as the others instead of two
-// selects per row (measured: those selects made the edge blocks the slowest, and every block
-// waits for its neighbours at each exchange).  Exact plans keep the selects (Table 2 order).
-struct Fold {
-    float cc0, cw0;   // cell 0: centre and west weights
-    float ccL, ceL;   // cell VX-1: centre and east weights
-};
-
 // One Jacobi step of the thread's VX x VY cells, in place.  xs: the block's row-exchange
 // buffers [2][NW][2][32*VX] (parity, warp, top/bottom row); XE: the block touches x = 0 or
-// x = nx-1 (folded diffusion: only an east edge inside a lane).
+// x = nx-1.
 template <int KIND, int VX, int VY, bool EXACT, bool XE>
 __device__ __forceinline__ void rstep(float (&u)[VY][VX], const float (&q)[VY][VX],
-                                      const float (&k)[5], const Fold &fo, float *xs, int &par,
-                                      int nw, int w, int lane, const Edges &g)
+                                      const float (&k)[5], float *xs, int &par, int nw, int w,
+                                      int lane, const Edges &g)
 {
-    constexpr bool FOLD = KIND == KDIFF && !EXACT;
     constexpr int RW = 32 * VX;
     float *mine = xs + ((par * nw + w) * 2) * RW + lane * VX;
     st_row<VX>(mine, u[0]);
@@ -179,7 +167,7 @@ __device__ __forceinline__ void rstep(float (&u)[VY][VX], const float (&q)[VY][V
         for (int j = 0; j < VX; j++) c[j] = u[r][j];
         float win = __shfl_up_sync(0xffffffffu, c[VX - 1], 1);
         float ein = __shfl_down_sync(0xffffffffu, c[0], 1);
-        if (XE && !FOLD) {
+        if (XE) {
             win = g.wsel ? c[0] : win;
             ein = g.esel ? c[VX - 1] : ein;
         }
@@ -188,12 +176,7 @@ __device__ __forceinline__ void rstep(float (&u)[VY][VX], const float (&q)[VY][V
             const float wv = j > 0 ? c[j - 1] : win;
             const float ev = j < VX - 1 ? c[j + 1] : ein;
             const float sv = r < VY - 1 ? u[r + 1][j] : sin[j];
-            if (FOLD && j == 0)
-                u[r][j] = diff5<false>(c[j], wv, ev, sv, prev[j], fo.cc0, fo.cw0, k[2], k[3], k[4]);
-            else if (FOLD && j == VX - 1)
-                u[r][j] = diff5<false>(c[j], wv, ev, sv, prev[j], fo.ccL, k[1], fo.ceL, k[3], k[4]);
-            else
-                u[r][j] = rcell<KIND, EXACT>(c[j], wv, ev, sv, prev[j], q[r][j], k);
+            u[r][j] = rcell<KIND, EXACT>(c[j], wv, ev, sv, prev[j], q[r][j], k);
         }
 #pragma unroll
         for (int j = 0; j < VX; j++) prev[j] = c[j];
@@ -262,13 +245,7 @@ __global__ void __launch_bounds__(res_max_threads(KIND, VX, EXACT)) k_res2d(cons
     g.efix = (r1 >= 0 && r1 < VX - 1) ? r1 : -1;
     g.k0 = -gy0;
     g.k1 = p.ny - 1 - gy0;
-    constexpr bool FOLD = KIND == KDIFF && !EXACT;
-    Fold fo;
-    fo.cc0 = g.wsel ? k[0] + k[1] : k[0];
-    fo.cw0 = g.wsel ? 0.f : k[1];
-    fo.ccL = g.esel ? k[0] + k[2] : k[0];
-    fo.ceL = g.esel ? 0.f : k[2];
-    const bool xe = __syncthreads_or(FOLD ? g.efix >= 0 : (g.wsel || g.esel || g.efix >= 0)) != 0;
+    const bool xe = __syncthreads_or(g.wsel || g.esel || g.efix >= 0) != 0;
 
     // the tile at time 0 (coordinates clamped: ghost cells start equal to the edge cells)
     float u[VY][VX], q[VY][VX];
@@ -295,10 +272,10 @@ __global__ void __launch_bounds__(res_max_threads(KIND, VX, EXACT)) k_res2d(cons
         // (measured: 4 steps per iteration +7-9 % over 1)
         if (xe) {
 #pragma unroll 4
-            for (int t = 0; t < ts; t++) rstep<KIND, VX, VY, EXACT, true>(u, q, k, fo, xs, par, nw, w, lane, g);
+            for (int t = 0; t < ts; t++) rstep<KIND, VX, VY, EXACT, true>(u, q, k, xs, par, nw, w, lane, g);
         } else {
 #pragma unroll 4
-            for (int t = 0; t < ts; t++) rstep<KIND, VX, VY, EXACT, false>(u, q, k, fo, xs, par, nw, w, lane, g);
+            for (int t = 0; t < ts; t++) rstep<KIND, VX, VY, EXACT, false>(u, q, k, xs, par, nw, w, lane, g);
         }
         if (e == E - 1) break;
 
