@@ -127,10 +127,20 @@ struct Edges {
     int k0, k1;  // rows of y = 0 and y = ny-1 among my VY rows (outside [0, VY): none)
 };
 
+// Clamp work of a block at the x edges, one bit each, so that a block compiles and runs only
+// what its own edges need (measured: with one edge path for both edges and the ghost-column
+// fix-up, the x-edge blocks took ~15 % more cycles per step than the others, and every block
+// waits for its neighbours at each exchange).
+enum : int {
+    XW = 1,   // x = 0 in the block: its west input is itself
+    XS = 2,   // x = nx-1 is a lane's last cell: its east input is itself
+    XF = 4,   // x = nx-1 inside a lane: the ghost cell after it copies it after each step
+};
+
 // One Jacobi step of the thread's VX x VY cells, in place.  xs: the block's row-exchange
-// buffers [2][NW][2][32*VX] (parity, warp, top/bottom row); XE: the block touches x = 0 or
-// x = nx-1.
-template <int KIND, int VX, int VY, bool EXACT, bool XE>
+// buffers [2][NW][2][32*VX] (parity, warp, top/bottom row); XM: the block's clamp work at the
+// x edges (XW | XS | XF).
+template <int KIND, int VX, int VY, bool EXACT, int XM>
 __device__ __forceinline__ void rstep(float (&u)[VY][VX], const float (&q)[VY][VX],
                                       const float (&k)[5], float *xs, int &par, int nw, int w,
                                       int lane, const Edges &g)
@@ -167,10 +177,8 @@ __device__ __forceinline__ void rstep(float (&u)[VY][VX], const float (&q)[VY][V
         for (int j = 0; j < VX; j++) c[j] = u[r][j];
         float win = __shfl_up_sync(0xffffffffu, c[VX - 1], 1);
         float ein = __shfl_down_sync(0xffffffffu, c[0], 1);
-        if (XE) {
-            win = g.wsel ? c[0] : win;
-            ein = g.esel ? c[VX - 1] : ein;
-        }
+        if (XM & XW) win = g.wsel ? c[0] : win;
+        if (XM & XS) ein = g.esel ? c[VX - 1] : ein;
 #pragma unroll
         for (int j = 0; j < VX; j++) {
             const float wv = j > 0 ? c[j - 1] : win;
@@ -196,7 +204,7 @@ __device__ __forceinline__ void rstep(float (&u)[VY][VX], const float (&q)[VY][V
 #pragma unroll
                 for (int j = 0; j < VX; j++) u[r + 1][j] = u[r][j];
     }
-    if (XE && g.efix >= 0) {
+    if ((XM & XF) && g.efix >= 0) {
 #pragma unroll
         for (int j = 0; j < VX - 1; j++)
             if (g.efix == j)
@@ -245,7 +253,8 @@ __global__ void __launch_bounds__(res_max_threads(KIND, VX, EXACT)) k_res2d(cons
     g.efix = (r1 >= 0 && r1 < VX - 1) ? r1 : -1;
     g.k0 = -gy0;
     g.k1 = p.ny - 1 - gy0;
-    const bool xe = __syncthreads_or(g.wsel || g.esel || g.efix >= 0) != 0;
+    const int xm = (__syncthreads_or(g.wsel) ? XW : 0) | (__syncthreads_or(g.esel) ? XS : 0) |
+                   (__syncthreads_or(g.efix >= 0) ? XF : 0);
 
     // the tile at time 0 (coordinates clamped: ghost cells start equal to the edge cells)
     float u[VY][VX], q[VY][VX];
@@ -270,12 +279,23 @@ __global__ void __launch_bounds__(res_max_threads(KIND, VX, EXACT)) k_res2d(cons
         const int ts = (e == E - 1) ? p.steps - p.T * (E - 1) : p.T;
         // unrolled so that the rows updated in place need no register moves at the loop edge
         // (measured: 4 steps per iteration +7-9 % over 1)
-        if (xe) {
+        // interior blocks, blocks on one x edge, and the rest (a grid one block wide)
+        if (xm == 0) {
 #pragma unroll 4
-            for (int t = 0; t < ts; t++) rstep<KIND, VX, VY, EXACT, true>(u, q, k, xs, par, nw, w, lane, g);
+            for (int t = 0; t < ts; t++) rstep<KIND, VX, VY, EXACT, 0>(u, q, k, xs, par, nw, w, lane, g);
+        } else if (xm == XW) {
+#pragma unroll 4
+            for (int t = 0; t < ts; t++) rstep<KIND, VX, VY, EXACT, XW>(u, q, k, xs, par, nw, w, lane, g);
+        } else if (xm == XS) {
+#pragma unroll 4
+            for (int t = 0; t < ts; t++) rstep<KIND, VX, VY, EXACT, XS>(u, q, k, xs, par, nw, w, lane, g);
+        } else if (xm == XF) {
+#pragma unroll 4
+            for (int t = 0; t < ts; t++) rstep<KIND, VX, VY, EXACT, XF>(u, q, k, xs, par, nw, w, lane, g);
         } else {
 #pragma unroll 4
-            for (int t = 0; t < ts; t++) rstep<KIND, VX, VY, EXACT, false>(u, q, k, xs, par, nw, w, lane, g);
+            for (int t = 0; t < ts; t++)
+                rstep<KIND, VX, VY, EXACT, XW | XS | XF>(u, q, k, xs, par, nw, w, lane, g);
         }
         if (e == E - 1) break;
 
