@@ -279,7 +279,9 @@ __global__ void __launch_bounds__(res_max_threads(KIND, VX, EXACT)) k_res2d(cons
         const int ts = (e == E - 1) ? p.steps - p.T * (E - 1) : p.T;
         // unrolled so that the rows updated in place need no register moves at the loop edge
         // (measured: 4 steps per iteration +7-9 % over 1)
-        // interior blocks, blocks on one x edge, and the rest (a grid one block wide)
+        // interior blocks and blocks on one x edge (x = nx-1 on a lane's last cell), unrolled;
+        // the rest (x = nx-1 inside a lane, a grid one block wide) in one general loop
+        // (measured: more unrolled variants slowed the interior blocks' loop by ~2 %)
         if (xm == 0) {
 #pragma unroll 4
             for (int t = 0; t < ts; t++) rstep<KIND, VX, VY, EXACT, 0>(u, q, k, xs, par, nw, w, lane, g);
@@ -289,11 +291,8 @@ __global__ void __launch_bounds__(res_max_threads(KIND, VX, EXACT)) k_res2d(cons
         } else if (xm == XS) {
 #pragma unroll 4
             for (int t = 0; t < ts; t++) rstep<KIND, VX, VY, EXACT, XS>(u, q, k, xs, par, nw, w, lane, g);
-        } else if (xm == XF) {
-#pragma unroll 4
-            for (int t = 0; t < ts; t++) rstep<KIND, VX, VY, EXACT, XF>(u, q, k, xs, par, nw, w, lane, g);
         } else {
-#pragma unroll 4
+#pragma unroll 1
             for (int t = 0; t < ts; t++)
                 rstep<KIND, VX, VY, EXACT, XW | XS | XF>(u, q, k, xs, par, nw, w, lane, g);
         }
