@@ -570,10 +570,11 @@ int prepare3(stencil_plan_s *p, int Tk, PassCfg3D **out)
             // with 52-plane pieces, 537 MB algorithmic).
             const long long slots = (long long)p->sms * bps;
             const int best_z = zslab_pick(c.cols, p->d.nz, slots, Tk, nullptr);
-            // a plane of a tile column at the x edge costs 1.1, at the y edge 1.05 (their
-            // warps run the clamp selects; measured on GB300, weights swept 1.0-1.5: 512^2 x
-            // 256 Hotspot 750 -> 804 GCell/s, 512^3 diffusion 931 -> 963)
-            const double wx = 1.1, wy = 1.05;
+            // a plane of a tile column at the x edge costs 1.2, at the y edge 1.1 (only those
+            // columns run the kernel instance with the clamp fix-ups; measured on GB300,
+            // weights swept 1.0-1.45, T = 3: 512^3 diffusion 923 -> 1027 GCell/s, 512^2 x 256
+            // Hotspot 752 -> 838)
+            const double wx = 1.2, wy = 1.1;
             std::vector<double> w(c.cols, 1.0);
             for (long long col = 0; col < c.cols; col++) {
                 const long long ty = col / c.ntx, tx = col - ty * c.ntx;

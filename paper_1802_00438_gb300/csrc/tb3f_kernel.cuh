@@ -26,6 +26,7 @@
 //   Ring slots advance with the z iteration as rolling indices (no integer division in the
 //   steady state); shared memory is addressed with 32-bit shared-window addresses.
 #pragma once
+#include <type_traits>
 #include "common.cuh"
 #include "internal.h"
 
@@ -219,7 +220,7 @@ __device__ __forceinline__ void tbf3_load(const CtxF3 &c, const float *src, int 
 // never used) takes the edge cell's value, inside my cells (m, in place) or in the value that
 // arrives from another lane or warp (wl, er, nt, sb).  The neighbour arrays stay pure renames of
 // m, so the common path keeps no second copy of them.
-template <int VX, int VY>
+template <int VX, int VY, bool EDGE>
 __device__ __forceinline__ void nbf3(const CtxF3 &c, float (&m)[VY][VX], float (&nt)[VX],
                                      float (&sb)[VX], float (&w)[VY][VX], float (&e)[VY][VX],
                                      float (&n)[VY][VX], float (&s)[VY][VX])
@@ -230,7 +231,7 @@ __device__ __forceinline__ void nbf3(const CtxF3 &c, float (&m)[VY][VX], float (
         wl[k] = __shfl_sync(0xffffffffu, m[k][VX - 1], (c.lane + 31) & 31);
         er[k] = __shfl_sync(0xffffffffu, m[k][0], (c.lane + 1) & 31);
     }
-    if (c.edge_y) {
+    if (EDGE && c.edge_y) {
         // y = 0 at my row k: ghost row k-1 (or the row above, nt) := row k; likewise below
 #pragma unroll
         for (int j = 0; j < VX; j++) {
@@ -246,7 +247,7 @@ __device__ __forceinline__ void nbf3(const CtxF3 &c, float (&m)[VY][VX], float (
 #pragma unroll
             for (int j = 0; j < VX; j++) m[k + 1][j] = ((c.ymn >> k) & 1u) ? m[k][j] : m[k + 1][j];
     }
-    if (c.edge_x) {
+    if (EDGE && c.edge_x) {
         // x = 0 is always my cell 0 (tile origins are multiples of 4); x = nx-1 is my cell j
 #pragma unroll
         for (int k = 0; k < VY; k++) {
@@ -332,7 +333,7 @@ __device__ __forceinline__ float upd3f(const CtxF3 &c, float m, float w, float e
     else return hot3<false>(m, w, e, s, n, b, a, p, c.k, c.ca_amb);
 }
 
-template <int KIND, int T, int VX, int VY, int NW, bool SPECIAL>
+template <int KIND, int T, int VX, int VY, int NW, bool SPECIAL, bool EDGE>
 __device__ __forceinline__ void tbf3_iter(const CtxF3 &c, uint32_t sring, uint32_t spw,
                                           uint32_t sxch, const Slots3 &sl,
                                           const float (&P)[TB3F<KIND, T, VX, VY, NW>::NS][VY][VX],
@@ -390,7 +391,7 @@ __device__ __forceinline__ void tbf3_iter(const CtxF3 &c, uint32_t sring, uint32
                 sb[j] = y.v[j];
             }
         }
-        nbf3<VX, VY>(c, m, nt, sb, w, e, n, s);
+        nbf3<VX, VY, EDGE>(c, m, nt, sb, w, e, n, s);
         if (KIND == KTHERM) {
             const uint32_t ap = spw + pm * C::PLANE_B + own;
 #pragma unroll
@@ -445,7 +446,7 @@ __device__ __forceinline__ void tbf3_iter(const CtxF3 &c, uint32_t sring, uint32
                     }
                 }
                 float w[VY][VX], e[VY][VX], n[VY][VX], s[VY][VX], p[VY][VX];
-                nbf3<VX, VY>(c, d, nt, sb, w, e, n, s);
+                nbf3<VX, VY, EDGE>(c, d, nt, sb, w, e, n, s);
                 if (KIND == KTHERM) {
                     int ps;
                     if (SPECIAL)
@@ -718,34 +719,40 @@ __global__ void __launch_bounds__(32 * NW, (TB3F<KIND, T, VX, VY, NW>::MINB))
         };
         // The partial sums alternate between two register sets (A -> B, then B -> A) so that
         // no iteration copies them; the rare special iterations run A -> B and copy back.
-        int i = 0;
+        // Tile columns away from the x and y domain edges run an instance without the clamp
+        // fix-ups: their in-place updates of the plane otherwise cost register copies on every
+        // path.  Returns false when a wait gave up.
+        auto run = [&](auto edge_tag) -> bool {
+            constexpr bool EDGE = decltype(edge_tag)::value;
+            int i = 0;
 #pragma unroll 1
-        while (i < n_it) {
-            if (!prologue(i)) {
-                bail();
-                return;
-            }
-            if (special(i)) {
-                tbf3_iter<KIND, T, VX, VY, NW, true>(c, sring, spw, sxch, sl, PA, QA, PB, QB, i);
-                advance();
-                copy_back();
-                ++i;
-                continue;
-            }
-            tbf3_iter<KIND, T, VX, VY, NW, false>(c, sring, spw, sxch, sl, PA, QA, PB, QB, i);
-            advance();
-            ++i;
-            if (i < n_it && !special(i)) {
-                if (!prologue(i)) {
-                    bail();
-                    return;
+            while (i < n_it) {
+                if (!prologue(i)) return false;
+                if (special(i)) {
+                    tbf3_iter<KIND, T, VX, VY, NW, true, EDGE>(c, sring, spw, sxch, sl, PA, QA, PB, QB, i);
+                    advance();
+                    copy_back();
+                    ++i;
+                    continue;
                 }
-                tbf3_iter<KIND, T, VX, VY, NW, false>(c, sring, spw, sxch, sl, PB, QB, PA, QA, i);
+                tbf3_iter<KIND, T, VX, VY, NW, false, EDGE>(c, sring, spw, sxch, sl, PA, QA, PB, QB, i);
                 advance();
                 ++i;
-            } else {
-                copy_back();
+                if (i < n_it && !special(i)) {
+                    if (!prologue(i)) return false;
+                    tbf3_iter<KIND, T, VX, VY, NW, false, EDGE>(c, sring, spw, sxch, sl, PB, QB, PA, QA, i);
+                    advance();
+                    ++i;
+                } else {
+                    copy_back();
+                }
             }
+            return true;
+        };
+        const bool edge = __syncthreads_or(c.edge_x || c.edge_y) != 0;
+        if (!(edge ? run(std::true_type{}) : run(std::false_type{}))) {
+            bail();
+            return;
         }
         if (!tma) cp_async_wait<0>();
         __syncthreads();
