@@ -252,7 +252,7 @@ typedef struct {
  * Sec. 3.2) with its own ping-pong scratch (Sec. 2.1); one (T, cells per thread) for the whole
  * batch comes from the GPU restatement of the paper's model (Eqs. 3-9), the compiled choice with
  * the least predicted total time.  The passes of all grids are cut into items of one tile column
- * (Sec. 3.1's overlapped tile) by 128 rows and queued pass by pass; ONE persistent kernel launch,
+ * (Sec. 3.1's overlapped tile) by 192 rows and queued pass by pass; ONE persistent kernel launch,
  * one warp per block and as many blocks as the device holds at once, pops the items in order,
  * and an item waits for the neighbouring tiles of its grid's previous pass (the halo it reads and
  * the cells of the ping-pong buffer it overwrites) before it starts.  Each such wait is bounded

@@ -49,10 +49,14 @@ struct stencil_batch_s {
 
 namespace {
 
-constexpr int kRows = 128;                        // rows per queue item (L), by default
+// rows per queue item (L), by default: each item streams 2T rows more than it stores, and
+// fewer, longer items leave more blocks waiting for their neighbours (measured on the 64-grid
+// workload, T = 8: 1921 / 1973 / 1980 / 1978 / 1961 GCell/s for L = 128 / 160 / 192 / 224 / 256)
+constexpr int kRows = 192;
 constexpr long long kWaitNs = 1000LL * 1000 * 1000;   // 1 s: a wait of a healthy batch is far shorter
 // (T, V) of the compiled queue kernel: 4 cells per lane (with 8, the launch ran at half the
-// rate on the 64-grid workload: 816 against 1713 GCell/s, one 255-register block per SMSP pair)
+// rate on the 64-grid workload: 816 against 1713 GCell/s, one 255-register block per SMSP pair;
+// T = 12 with 4 cells, 255 registers, 1763 against 1980 for T = 8)
 const int kCand[][2] = {{8, 4}};
 
 int status(cudaError_t e)
