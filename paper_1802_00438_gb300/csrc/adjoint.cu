@@ -45,7 +45,10 @@ namespace {
 constexpr int AX = 128, AY = 32, ANT = 256, ACPT = AX * AY / ANT;   // tile, threads, cells/thread
 static_assert(AX == 4 * 32 && AY == 4 * (ANT / 32), "a lane owns 4 x 4 cells of the tile");
 constexpr int ATA = 4;                                                // fused adjoint steps
-constexpr int ACX = AX - 2 * ATA, ACY = AY - 2 * ATA;                // compute block
+// halos: ATA rows in y; in x at least ATA cells and a multiple of 4, so that every tile origin
+// (a tensor-map copy's innermost coordinate) stays on a 16-byte boundary
+constexpr int AHX = (ATA + 3) / 4 * 4;
+constexpr int ACX = AX - 2 * AHX, ACY = AY - 2 * ATA;                // compute block
 constexpr int NG = 5;                                                 // coefficients
 constexpr int NPART = 3 * NG;                                         // (hi, lo, |.|) x 5
 
@@ -242,7 +245,7 @@ __device__ __forceinline__ void adj_block(const AdjPass &a, int lane, int ly0, i
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 const int lx = lx0 + j, gx = x0 + lx;
-                if (lx < ATA || lx >= ATA + ACX) continue;
+                if (lx < AHX || lx >= AHX + ACX) continue;
                 if (EDGE && gx >= a.nx) continue;
                 const float uc = U[r + 1][j];
                 float uwj = j > 0 ? U[r + 1][j - 1] : uw[r];
@@ -284,7 +287,7 @@ __global__ void __launch_bounds__(ANT, 2) k_adj2d(const AdjPass a, const __grid_
     __shared__ __align__(8) uint64_t bars[2 + ATA];   // lambda, power, state tiles 0 .. ATA-1
     const int tid = threadIdx.x;
     const int tx = blockIdx.x % a.ntx, ty = blockIdx.x / a.ntx;
-    const int x0 = tx * ACX - ATA, y0 = ty * ACY - ATA;
+    const int x0 = tx * ACX - AHX, y0 = ty * ACY - ATA;
     const bool tma = a.use_tma != 0;
     const uint32_t b0 = sm32(&bars[0]);
     // block-uniform: the whole tile is in the grid and no cell of it lies on the grid's edge
@@ -382,7 +385,7 @@ __global__ void __launch_bounds__(ANT, 2) k_adj2d(const AdjPass a, const __grid_
                 r = __fmaf_rn(a.ws, ln, r);
                 r = __fmaf_rn(a.wn, ls, r);
                 nxt[idx] = in ? r : 0.f;
-                const bool own = in && lx >= ATA && lx < ATA + ACX && ly >= ATA && ly < ATA + ACY;
+                const bool own = in && lx >= AHX && lx < AHX + ACX && ly >= ATA && ly < ATA + ACY;
                 if (own) {
                     float g[NG];
                     if (tma) {
@@ -420,7 +423,7 @@ __global__ void __launch_bounds__(ANT, 2) k_adj2d(const AdjPass a, const __grid_
     for (int c = 0; c < ACPT; c++) {
         const int lx = lx0 + (c & 3), ly = ly0 + (c >> 2), idx = ly * AX + lx;
         const int gx = x0 + lx, gy = y0 + ly;
-        const bool own = gx < a.nx && gy < a.ny && lx >= ATA && lx < ATA + ACX && ly >= ATA &&
+        const bool own = gx < a.nx && gy < a.ny && lx >= AHX && lx < AHX + ACX && ly >= ATA &&
                          ly < ATA + ACY;
         if (own) {
             const long long o = (long long)gy * a.nx + gx;
