@@ -782,7 +782,7 @@ def adjoint_record(g: Gpu, args, steps: int, warmup: int, with_cpu: bool, ckpt=2
 STUDY_2D = [(1, 8, 0), (2, 8, 0), (4, 8, 0), (6, 8, 0), (8, 8, 0), (8, 8, 1),
             (1, 4, 0), (2, 4, 0), (4, 4, 0), (8, 4, 0), (12, 4, 0), (12, 4, 1)]
 # resident tiles (small 2D grids): (T, cells per lane)
-STUDY_RES = [(T, v) for v in (2, 4) for T in (2, 4, 8, 12, 16)]
+STUDY_RES = [(T, v) for v in (2, 4) for T in (2, 4, 8, 12, 16, 20)]
 STUDY_3D = [(1, 64, 64, 8), (2, 64, 64, 8), (3, 64, 64, 8), (4, 64, 64, 8),
             (2, 64, 64, 4), (3, 64, 64, 4), (4, 64, 64, 4),
             (2, 128, 32, 8), (3, 128, 32, 8), (4, 128, 32, 8),

@@ -355,9 +355,12 @@ namespace {
 // thread instructions per cell and step (the Table 2 operations, the shuffles of the lane edges,
 // the row exchange between warps, loop overhead), t_bar the per-step barrier of that exchange,
 // t_x one exchange through L2 after every T steps (publish, neighbour wait, halo reload), t_io
-// the single read and write of the grid.  Calibrated on GB300 (least squares over 93 measured
-// configurations of 512^2 and 1024^2 grids, T = 1..16, 2 and 4 cells per lane, both kinds,
-// exact and contracted; 97 % within 0.8-1.2 of measured): issue efficiency 0.53, t_x = 6.7 us.
+// the single read and write of the grid.  Calibrated on GB300: first by least squares over 93
+// measured configurations of 512^2 and 1024^2 grids (T = 1..16, 2 and 4 cells per lane, both
+// kinds, exact and contracted); then, after the step loop was unrolled and the x-edge work split
+// by edge, on the step loops' clock64 cycles and the run times of 1024^2 at T = 12..20 (both
+// kinds, exact and contracted, within 0.9-1.05): issue efficiency 0.73, t_x = 7.8 us, and two
+// more operations per cell for exact plans (Table 2 order, no fused multiply-adds).
 struct ResGeom {
     int T = 0, vx = 0, nw = 0, nbx = 0, nby = 0, cw = 0, ch = 0, hx = 0;
     double t = 0.0;   // predicted seconds for 1000 steps
@@ -369,10 +372,10 @@ double res_time(const stencil_desc &d, int sms, const ResGeom &g, int steps)
     const double per_sm = std::ceil((double)g.nbx * g.nby / sms);
     const double cells = per_sm * g.nw * 32.0 * g.vx * VY;
     double fp = d.kind == ST_DIFFUSION ? 5.0 : 6.0;
-    if (d.exact) fp = d.kind == ST_DIFFUSION ? 9.0 : 13.0;
+    if (d.exact) fp = d.kind == ST_DIFFUSION ? 11.0 : 15.0;
     const double ops = fp + 2.0 / g.vx + 4.0 / (g.vx * VY) + 1.0;
-    const double t_step = cells * ops / (128.0 * 0.53 * 2.07e9) + 0.1e-6;
-    const double t_x = 6.7e-6;
+    const double t_step = cells * ops / (128.0 * 0.73 * 2.07e9) + 0.1e-6;
+    const double t_x = 7.8e-6;
     const int epochs = (steps + g.T - 1) / g.T;
     return steps * t_step + (epochs - 1) * t_x + 5e-6 + (double)d.nx * d.ny * 8.0 / 6.8e12;
 }
@@ -433,7 +436,7 @@ bool res_choose(const stencil_desc &d, int sms, ResGeom *out)
     bool found = false;
     for (int vx : {2, 4}) {
         if (d.force_vec && d.force_vec != vx) continue;
-        for (int t : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32}) {
+        for (int t : {1, 2, 3, 4, 6, 8, 12, 16, 20, 24, 32}) {
             if (d.force_T && t != d.force_T) continue;
             ResGeom g;
             if (res_geometry(d, sms, t, vx, &g) && (!found || g.t < out->t)) {
