@@ -460,6 +460,18 @@ int stencil_run_noalloc(int kind, const void *grid_in, void *grid_out, const voi
  * nothing.  Errors: ST_ERR_INVALID_ARG (NULL tflops), ST_ERR_CUDA. */
 int stencil_fp32_peak(double *tflops, void *stream);
 
+/* Allocation-failure injection and allocation accounting (test hooks; no paper counterpart).
+ * Every device allocation the library makes (plans, batches, adjoints, tuning) and its pinned
+ * host allocations go through one allocator.  stencil_debug_fail_alloc(n), n > 0: the n-th such
+ * allocation from now on fails as if the device were out of memory, without touching the
+ * device; the call that makes it releases what it had allocated and returns ST_ERR_OOM.  The
+ * hook then disarms itself; n = 0 disarms it at once.  Process-wide, not synchronised with
+ * calls running on other threads.  Errors: ST_ERR_INVALID_ARG (n < 0).
+ * stencil_debug_live_allocs(): the allocations the library holds now (a leak shows as a count
+ * that does not return to its earlier value once the objects are destroyed). */
+int stencil_debug_fail_alloc(int n);
+long long stencil_debug_live_allocs(void);
+
 /* Static description of a status code. */
 const char *stencil_strerror(int code);
 

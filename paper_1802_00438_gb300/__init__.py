@@ -122,6 +122,8 @@ _P = ctypes.c_void_p
 _I = ctypes.c_int
 SIGNATURES = {
     "stencil_abi_version": ([], _I),
+    "stencil_debug_fail_alloc": ([_I], _I),
+    "stencil_debug_live_allocs": ([], ctypes.c_longlong),
     "stencil_strerror": ([_I], ctypes.c_char_p),
     "stencil_plan_create": ([ctypes.POINTER(_P), ctypes.POINTER(stencil_desc)], _I),
     "stencil_run": ([_P, _P, _P, _P, ctypes.POINTER(ctypes.c_float), _I, _I, _I, _I], _I),

@@ -602,14 +602,14 @@ int stencil_adjoint_create(stencil_adjoint *out, int kind, int nx, int ny, int s
     const size_t n = (size_t)nx * ny * sizeof(float);
     cudaError_t e = cudaSuccess;
     if (rc == ST_OK && a->nseg > 0) {
-        e = cudaMalloc(&a->ck, n * a->nseg);
-        if (e == cudaSuccess) e = cudaMalloc(&a->seg, n * a->ckpt);
-        if (e == cudaSuccess) e = cudaMalloc(&a->lam[0], n);
-        if (e == cudaSuccess) e = cudaMalloc(&a->lam[1], n);
+        e = stn::dev_malloc(&a->ck, n * a->nseg);
+        if (e == cudaSuccess) e = stn::dev_malloc(&a->seg, n * a->ckpt);
+        if (e == cudaSuccess) e = stn::dev_malloc(&a->lam[0], n);
+        if (e == cudaSuccess) e = stn::dev_malloc(&a->lam[1], n);
         if (e == cudaSuccess)
-            e = cudaMalloc(&a->partials, sizeof(float) * NPART *
+            e = stn::dev_malloc(&a->partials, sizeof(float) * NPART *
                                              (size_t)(a->blocks * a->passes + ADJ_SUM_BLOCKS));
-        if (e == cudaSuccess) e = cudaMalloc(&a->err, sizeof(int));
+        if (e == cudaSuccess) e = stn::dev_malloc(&a->err, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(a->err, 0, sizeof(int));
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_adj2d<ST_DIFFUSION, false>,
@@ -804,12 +804,12 @@ int stencil_adjoint_destroy(stencil_adjoint a)
     if (a->stream) cudaStreamSynchronize(a->stream);
     else cudaDeviceSynchronize();
     if (a->fwd) stencil_plan_destroy(a->fwd);
-    if (a->ck) cudaFree(a->ck);
-    if (a->seg) cudaFree(a->seg);
+    if (a->ck) stn::dev_free(a->ck);
+    if (a->seg) stn::dev_free(a->seg);
     for (float *l : a->lam)
-        if (l) cudaFree(l);
-    if (a->partials) cudaFree(a->partials);
-    if (a->err) cudaFree(a->err);
+        if (l) stn::dev_free(l);
+    if (a->partials) stn::dev_free(a->partials);
+    if (a->err) stn::dev_free(a->err);
     delete a;
     return ST_OK;
 }

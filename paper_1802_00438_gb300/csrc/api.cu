@@ -499,11 +499,11 @@ int prepare2(stencil_plan_s *p, int Tk, PassCfg2D **out)
             w.front() = w.back() = 1.25;
             if (balanced_ranges(p->d.ny, (int)ctas, fill, w, st) <
                 even_ranges_cost(p->d.ny, c.rows_per_cta, fill, w)) {
-                e = cudaMalloc(&c.starts, st.size() * sizeof(long long));
+                e = stn::dev_malloc(&c.starts, st.size() * sizeof(long long));
                 if (e == cudaSuccess)
                     e = cudaMemcpy(c.starts, st.data(), st.size() * sizeof(long long), cudaMemcpyHostToDevice);
                 if (e != cudaSuccess) {
-                    if (c.starts) cudaFree(c.starts);
+                    if (c.starts) stn::dev_free(c.starts);
                     c.starts = nullptr;
                     return map_cuda(e);
                 }
@@ -595,11 +595,11 @@ int prepare3(stencil_plan_s *p, int Tk, PassCfg3D **out)
                 std::vector<long long> st;
                 if (balanced_ranges(p->d.nz, (int)ctas, Tk, w, st) <
                     even_ranges_cost(p->d.nz, c.planes_per_cta, Tk, w)) {
-                    e = cudaMalloc(&c.starts, st.size() * sizeof(long long));
+                    e = stn::dev_malloc(&c.starts, st.size() * sizeof(long long));
                     if (e == cudaSuccess)
                         e = cudaMemcpy(c.starts, st.data(), st.size() * sizeof(long long), cudaMemcpyHostToDevice);
                     if (e != cudaSuccess) {
-                        if (c.starts) cudaFree(c.starts);
+                        if (c.starts) stn::dev_free(c.starts);
                         c.starts = nullptr;
                         return map_cuda(e);
                     }
@@ -1194,13 +1194,13 @@ static int plan_create(stencil_plan *out, const stencil_desc *desc)
                 p->ld_q = ((long long)d.nx + 7) / 8 * 8;
                 const size_t qb = (size_t)p->ld_q * d.ny * 2, mb = (size_t)p->ntx * d.ny * sizeof(float2);
                 for (int b = 0; b < 2 && rc == ST_OK; b++) {
-                    e = cudaMalloc(&p->q[b], qb);
-                    if (e == cudaSuccess) e = cudaMalloc(&p->qm[b], mb);
+                    e = stn::dev_malloc(&p->q[b], qb);
+                    if (e == cudaSuccess) e = stn::dev_malloc(&p->qm[b], mb);
                     if (e != cudaSuccess) rc = map_cuda(e);
                 }
                 if (rc == ST_OK && d.kind == ST_THERMAL) {
-                    e = cudaMalloc(&p->qp, qb);
-                    if (e == cudaSuccess) e = cudaMalloc(&p->qpm, mb);
+                    e = stn::dev_malloc(&p->qp, qb);
+                    if (e == cudaSuccess) e = stn::dev_malloc(&p->qpm, mb);
                     if (e != cudaSuccess) rc = map_cuda(e);
                 }
                 p->scratch_bytes = 0;   // no float32 scratch: the coded grids take its place
@@ -1279,19 +1279,19 @@ static int plan_create(stencil_plan *out, const stencil_desc *desc)
         p->scratch_bytes = (size_t)cells_of(d) * sizeof(float);
     }
     if (rc == ST_OK && p->scratch_bytes) {
-        e = cudaMalloc(&p->scratch, p->scratch_bytes);
+        e = stn::dev_malloc(&p->scratch, p->scratch_bytes);
         if (e != cudaSuccess) rc = map_cuda(e);
     }
     if (rc == ST_OK && d.ndim == 2 && d.kind == ST_THERMAL && !d.exact && !p->stor) {
         // rows padded to 32 cells like the scratch grid: 16-byte aligned rows for any nx
         p->ld_src = ((long long)d.nx + 31) / 32 * 32;
-        e = cudaMalloc(&p->src, (size_t)p->ld_src * d.ny * sizeof(float));
+        e = stn::dev_malloc(&p->src, (size_t)p->ld_src * d.ny * sizeof(float));
         if (e != cudaSuccess) rc = map_cuda(e);
     }
     if (rc == ST_OK && p->res) {
         const size_t fb = (size_t)p->res_nbx * p->res_nby * sizeof(int);
-        e = cudaMalloc(&p->res_xg, (size_t)2 * p->res_ld * d.ny * sizeof(float));
-        if (e == cudaSuccess) e = cudaMalloc(&p->res_flags, fb);
+        e = stn::dev_malloc(&p->res_xg, (size_t)2 * p->res_ld * d.ny * sizeof(float));
+        if (e == cudaSuccess) e = stn::dev_malloc(&p->res_flags, fb);
         if (e == cudaSuccess) e = cudaMemset(p->res_flags, 0, fb);
         if (e != cudaSuccess) rc = map_cuda(e);
     }
@@ -1307,7 +1307,7 @@ static int plan_create(stencil_plan *out, const stencil_desc *desc)
         }
     }
     if (rc == ST_OK) {
-        e = cudaMalloc(&p->err, sizeof(int));
+        e = stn::dev_malloc(&p->err, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(p->err, 0, sizeof(int));
         if (e != cudaSuccess) rc = map_cuda(e);
     }
@@ -1587,21 +1587,21 @@ int stencil_plan_destroy(stencil_plan p)
     if (!p) return ST_OK;
     if (p->ev_used) cudaStreamSynchronize(p->stream);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
-    if (p->scratch) cudaFree(p->scratch);
+    if (p->scratch) stn::dev_free(p->scratch);
     for (int b = 0; b < 2; b++) {
-        if (p->q[b]) cudaFree(p->q[b]);
-        if (p->qm[b]) cudaFree(p->qm[b]);
+        if (p->q[b]) stn::dev_free(p->q[b]);
+        if (p->qm[b]) stn::dev_free(p->qm[b]);
     }
-    if (p->qp) cudaFree(p->qp);
-    if (p->qpm) cudaFree(p->qpm);
-    if (p->err) cudaFree(p->err);
-    if (p->src) cudaFree(p->src);
-    if (p->res_xg) cudaFree(p->res_xg);
-    if (p->res_flags) cudaFree(p->res_flags);
+    if (p->qp) stn::dev_free(p->qp);
+    if (p->qpm) stn::dev_free(p->qpm);
+    if (p->err) stn::dev_free(p->err);
+    if (p->src) stn::dev_free(p->src);
+    if (p->res_xg) stn::dev_free(p->res_xg);
+    if (p->res_flags) stn::dev_free(p->res_flags);
     for (PassCfg2D &c : p->cfg2)
-        if (c.starts) cudaFree(c.starts);
+        if (c.starts) stn::dev_free(c.starts);
     for (PassCfg3D &c : p->cfg3)
-        if (c.starts) cudaFree(c.starts);
+        if (c.starts) stn::dev_free(c.starts);
     delete p;
     return ST_OK;
 }

@@ -116,7 +116,7 @@ int stencil_batch_create_ex(stencil_batch *out, const stencil_batch_grid *grids,
     int dev = 0, rc = ST_OK;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&B->sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaMallocHost(&B->h_status, sizeof(int));
+    if (e == cudaSuccess) e = stn::host_malloc(&B->h_status, sizeof(int));
     if (e != cudaSuccess) {
         stencil_batch_destroy(B);
         return status(e);
@@ -167,10 +167,10 @@ int stencil_batch_create_ex(stencil_batch *out, const stencil_batch_grid *grids,
         B->passes[g] = q.steps > 0 ? (q.steps + T - 1) / T : 0;
         B->ld_scratch[g] = ((long long)q.nx + 31) / 32 * 32;
         const size_t sb = (size_t)B->ld_scratch[g] * q.ny * sizeof(float);
-        if (B->passes[g] > 1) e = cudaMalloc(&B->scratch[2 * g], sb);
-        if (e == cudaSuccess && B->passes[g] > 2) e = cudaMalloc(&B->scratch[2 * g + 1], sb);
+        if (B->passes[g] > 1) e = stn::dev_malloc(&B->scratch[2 * g], sb);
+        if (e == cudaSuccess && B->passes[g] > 2) e = stn::dev_malloc(&B->scratch[2 * g + 1], sb);
         if (e == cudaSuccess && B->passes[g] > 0 && q.kind == ST_THERMAL)   // padded rows too
-            e = cudaMalloc(&B->src[g], sb);
+            e = stn::dev_malloc(&B->src[g], sb);
         if (e != cudaSuccess) rc = status(e);
     }
 
@@ -305,7 +305,7 @@ int stencil_batch_create_ex(stencil_batch *out, const stencil_batch_grid *grids,
     const size_t cnt_bytes = (size_t)(3 + ndone + nsrcf) * sizeof(int);   // heads, status, counters
     const size_t table = o_cnt + align256(cnt_bytes);
     if (rc == ST_OK) {
-        e = cudaMalloc(&B->dev, table);
+        e = stn::dev_malloc(&B->dev, table);
         if (e != cudaSuccess) rc = status(e);
     }
     char *d = static_cast<char *>(B->dev);
@@ -414,11 +414,11 @@ int stencil_batch_destroy(stencil_batch b)
     }
     if (b->graph) cudaGraphDestroy(b->graph);
     for (float *s : b->scratch)
-        if (s) cudaFree(s);
+        if (s) stn::dev_free(s);
     for (float *s : b->src)
-        if (s) cudaFree(s);
-    if (b->dev) cudaFree(b->dev);
-    if (b->h_status) cudaFreeHost(b->h_status);
+        if (s) stn::dev_free(s);
+    if (b->dev) stn::dev_free(b->dev);
+    if (b->h_status) stn::host_free(b->h_status);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
     return ST_OK;

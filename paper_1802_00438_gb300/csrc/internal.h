@@ -231,6 +231,23 @@ struct Res2D {
                            // Hotspot contracted: cc cx cy cz (expanded weights)
 };
 
+// Device and pinned-host allocations of the library (alloc.cu): failure injection and live
+// accounting for tests (stencil_debug_fail_alloc, stencil_debug_live_allocs).
+cudaError_t dev_malloc(void **p, size_t bytes);
+void dev_free(void *p);
+cudaError_t host_malloc(void **p, size_t bytes);
+void host_free(void *p);
+template <class T>
+cudaError_t dev_malloc(T **p, size_t bytes)
+{
+    return dev_malloc(reinterpret_cast<void **>(p), bytes);
+}
+template <class T>
+cudaError_t host_malloc(T **p, size_t bytes)
+{
+    return host_malloc(reinterpret_cast<void **>(p), bytes);
+}
+
 int res2d_rows_per_thread();
 int res2d_max_warps(int kind, int exact, int vx);
 size_t res2d_smem(int vx, int nw);

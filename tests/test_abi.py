@@ -106,6 +106,10 @@ def test_host_only_calls(lib_path):
     assert st.lib.stencil_plan_create(ctypes.byref(h), ctypes.byref(bad)) == st.ST_ERR_INVALID_ARG
     assert st.lib.stencil_run(None, None, None, None, None, 1, 1, 1, 1) == st.ST_ERR_INVALID_ARG
     assert st.lib.stencil_plan_destroy(None) == st.ST_OK
+    # allocation-failure hook: argument checks and the live count need no device
+    assert st.lib.stencil_debug_fail_alloc(-1) == st.ST_ERR_INVALID_ARG
+    assert st.lib.stencil_debug_fail_alloc(0) == st.ST_OK
+    assert st.lib.stencil_debug_live_allocs() >= 0
 
 
 def test_no_oracle_in_product():
