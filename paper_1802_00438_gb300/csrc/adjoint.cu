@@ -643,6 +643,7 @@ int stencil_adjoint_forward(stencil_adjoint a, const float *u0, const float *pow
     if (!a || !u0 || !coeffs || !u_out) return ST_ERR_INVALID_ARG;
     if (a->kind == ST_THERMAL && !power) return ST_ERR_INVALID_ARG;
     if (a->kind == ST_DIFFUSION && power) return ST_ERR_INVALID_ARG;
+    const stn::NvtxRange r("stencil_adjoint_forward");
     const size_t n = (size_t)a->nx * a->ny * sizeof(float);
     for (int i = 0; i < 5; i++) a->coef[i] = coeffs[i];
     a->have_forward = false;
@@ -676,6 +677,7 @@ int stencil_adjoint_backward(stencil_adjoint a, const float *grad_out, const flo
     if (!a->have_forward) return ST_ERR_INVALID_ARG;
     if (a->kind == ST_THERMAL && (!power || !grad_power)) return ST_ERR_INVALID_ARG;
     if (a->kind == ST_DIFFUSION && (power || grad_power)) return ST_ERR_INVALID_ARG;
+    const stn::NvtxRange r("stencil_adjoint_backward");
     const long long cells = (long long)a->nx * a->ny;
     const size_t n = (size_t)cells * sizeof(float);
     cudaError_t e = cudaSuccess;

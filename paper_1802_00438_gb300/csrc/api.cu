@@ -1339,6 +1339,7 @@ int stencil_run(stencil_plan p, const void *grid_in, void *grid_out, const void 
     if (power && ranges_overlap2(power, pw_bytes, grid_out, bytes)) return ST_ERR_INVALID_ARG;
     if (d.strict && !stable(d, coeffs)) return ST_ERR_UNSTABLE_COEFFS;
     if (p->sticky != ST_OK) return p->sticky;
+    const stn::NvtxRange r_run("stencil_run");
 
     const float *in = static_cast<const float *>(grid_in);
     float *out = static_cast<float *>(grid_out);
@@ -1368,6 +1369,7 @@ int stencil_run(stencil_plan p, const void *grid_in, void *grid_out, const void 
         if (e != cudaSuccess) return map_cuda(e);
         int cur = 0;
         for (int i = 0; i < passes; i++) {
+            const stn::NvtxRange r_pass("pass");
             const int rc = run_pass2q(p, cur, 1 - cur, coeffs, (i == passes - 1) ? last : T);
             if (rc != ST_OK) {
                 p->sticky = rc;
@@ -1395,6 +1397,7 @@ int stencil_run(stencil_plan p, const void *grid_in, void *grid_out, const void 
     const float *src = in;
     long long lds = d.nx;
     for (int i = 0; i < passes; i++) {
+        const stn::NvtxRange r_pass("pass");
         const int ts = (i == passes - 1) ? last : T;
         const bool to_out = shift ? ((passes - i) % 2 == 0) : ((passes - 1 - i) % 2 == 0);
         float *dst = to_out ? out : p->scratch;

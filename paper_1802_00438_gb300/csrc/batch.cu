@@ -371,6 +371,7 @@ int stencil_batch_create_ex(stencil_batch *out, const stencil_batch_grid *grids,
 int stencil_batch_run(stencil_batch b)
 {
     if (!b || !b->exec) return ST_ERR_INVALID_ARG;
+    const stn::NvtxRange r("stencil_batch_run");
     return status(cudaGraphLaunch(b->exec, b->stream));
 }
 

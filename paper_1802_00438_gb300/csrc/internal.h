@@ -1,5 +1,6 @@
 // Interface between the host runtime (api.cu) and the kernel translation units.
 #pragma once
+#include <nvtx3/nvToolsExt.h>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -229,6 +230,15 @@ struct Res2D {
     int nbx, nby, cw, ch, hx, hy;   // blocks, compute block size, halo widths
     float k[5];            // Diffusion: cc cw ce cs cn; Hotspot exact: sdc Rx Ry Rz amb;
                            // Hotspot contracted: cc cx cy cz (expanded weights)
+};
+
+// A named range on the host timeline for tools (ncu --nvtx, Nsight Systems): NVTX3, header
+// only; without a tool attached a push or pop returns at once.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
 // Device and pinned-host allocations of the library (alloc.cu): failure injection and live

@@ -176,6 +176,7 @@ extern "C" int stencil_run_noalloc(int kind, const void *grid_in, void *grid_out
         const uintptr_t pp = (uintptr_t)power;
         if (pp < po + bytes && po < pp + bytes) return ST_ERR_INVALID_ARG;
     }
+    const stn::NvtxRange r("stencil_run_noalloc");
     DeviceSlot *dv = nullptr;
     int rc = device_slot(&dv);
     if (rc != ST_OK) return rc;
