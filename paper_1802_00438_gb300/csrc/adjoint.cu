@@ -49,6 +49,9 @@ constexpr int ATA = 4;                                                // fused a
 // (a tensor-map copy's innermost coordinate) stays on a 16-byte boundary
 constexpr int AHX = (ATA + 3) / 4 * 4;
 constexpr int ACX = AX - 2 * AHX, ACY = AY - 2 * ATA;                // compute block
+// tile origin x = tx * ACX - AHX: a multiple of 4 floats for every tile (an unaligned innermost
+// coordinate of a tensor-map copy is an illegal instruction)
+static_assert(AHX % 4 == 0 && ACX % 4 == 0 && AHX >= ATA, "tile origins on 16-byte boundaries");
 constexpr int NG = 5;                                                 // coefficients
 constexpr int NPART = 3 * NG;                                         // (hi, lo, |.|) x 5
 
